@@ -1,0 +1,240 @@
+"""Python handle on the CPU oracle (``liboracle.so``).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's
+``cpu_baseline`` / ``--impl reference`` legs import this; the CUDA product path
+never does.  Every function marshals numpy arrays into the C library, which is
+a plain FP64 restatement of the method (see oracle.h for the passages it
+follows).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_dp = ct.POINTER(ct.c_double)
+_ip = ct.POINTER(ct.c_int32)
+
+
+class Opts(ct.Structure):
+    _fields_ = [("method", ct.c_int), ("rtol", ct.c_double), ("atol_Y", ct.c_double),
+                ("atol_T", ct.c_double), ("max_newton", ct.c_int), ("ramp", ct.c_int)]
+
+
+class Grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int), ("dx", ct.c_double),
+                ("u", ct.c_double * 3), ("D", ct.c_double), ("order", ct.c_int)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.SO
+        if not os.path.exists(path):
+            path = _build.build()
+        L = ct.CDLL(path)
+        L.orc_mech_load.restype = ct.c_void_p
+        L.orc_mech_load.argtypes = [ct.c_char_p, ct.c_size_t]
+        L.orc_mech_free.argtypes = [ct.c_void_p]
+        for name in ("orc_thermo", "orc_rate_coeffs", "orc_progress", "orc_rhs", "orc_jac", "orc_jac_cs",
+                     "orc_stage_fast", "orc_mri_step", "orc_single_rate", "orc_mech_info"):
+            getattr(L, name).argtypes = None
+        L.orc_thermo.argtypes = [ct.c_void_p, ct.c_double, _dp, _dp, _dp, _dp]
+        L.orc_rate_coeffs.argtypes = [ct.c_void_p, ct.c_double, _dp, _dp, _dp, _dp]
+        L.orc_progress.argtypes = [ct.c_void_p, ct.c_double, _dp, _dp, _dp]
+        L.orc_rhs.argtypes = [ct.c_void_p, _dp, ct.c_double, _dp]
+        L.orc_jac.argtypes = [ct.c_void_p, _dp, ct.c_double, _dp]
+        L.orc_jac_cs.argtypes = [ct.c_void_p, _dp, ct.c_double, _dp]
+        L.orc_mech_info.argtypes = [ct.c_void_p, _ip, _ip]
+        L.orc_lu_solve.argtypes = [ct.c_int, _dp, _ip, _dp]
+        L.orc_sdirk_tableau.argtypes = [ct.c_int, _dp, _dp, _dp, _ip]
+        L.orc_mri_tableau.argtypes = [_dp, _dp, _ip]
+        L.orc_mri_coupling.argtypes = [_dp, _ip]
+        L.orc_stage_fast.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, _dp, ct.c_int, ct.c_double, ct.c_double,
+                                     ct.POINTER(Opts), _ip, _ip, ct.c_int]
+        L.orc_slow_rhs.argtypes = [_dp, _dp, ct.c_int, ct.POINTER(Grid)]
+        L.orc_mri_step.argtypes = [ct.c_void_p, _dp, _dp, ct.POINTER(Grid), ct.c_double, ct.c_double,
+                                   ct.POINTER(Opts), _ip, _ip, ct.c_int]
+        L.orc_single_rate.argtypes = [ct.c_void_p, _dp, _dp, ct.POINTER(Grid), ct.c_double, ct.c_int,
+                                      ct.POINTER(Opts)]
+        L.orc_sdirk_scalar.argtypes = [ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_double, ct.c_int,
+                                       ct.c_double, _dp]
+        L.orc_kpr_mri.argtypes = [ct.c_int, ct.c_double, ct.c_double, ct.c_double, ct.c_double, ct.c_double,
+                                  ct.c_int, ct.c_int, _dp, _dp]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def opts(method=3, rtol=1e-10, atol_Y=1e-20, atol_T=1e-10, max_newton=10, ramp=0) -> Opts:
+    return Opts(method, rtol, atol_Y, atol_T, max_newton, ramp)
+
+
+def grid(g: dict) -> Grid:
+    return Grid(g["nx"], g["ny"], g["nz"], g["dx"], (ct.c_double * 3)(*g["u"]), g["D"], g["order"])
+
+
+def default_threads() -> int:
+    return os.cpu_count() or 1
+
+
+class Mech:
+    """An oracle-side mechanism parsed from a mechgen blob."""
+
+    def __init__(self, mechanism):
+        blob = mechanism.to_blob() if hasattr(mechanism, "to_blob") else bytes(mechanism)
+        self._blob = blob
+        self.ptr = lib().orc_mech_load(blob, len(blob))
+        if not self.ptr:
+            raise ValueError("oracle rejected the mechanism blob")
+        ns, nr = ct.c_int32(), ct.c_int32()
+        lib().orc_mech_info(self.ptr, ct.byref(ns), ct.byref(nr))
+        self.Ns, self.R = ns.value, nr.value
+        self.n = self.Ns + 1
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.orc_mech_free(self.ptr)
+            self.ptr = None
+
+    def thermo(self, T):
+        out = [np.zeros(self.Ns) for _ in range(4)]
+        rc = lib().orc_thermo(self.ptr, float(T), *[_d(o) for o in out])
+        assert rc == 0
+        return tuple(out)   # cp/R, h/RT, s/R, g/RT
+
+    def rate_coeffs(self, T, C):
+        kf, kr, Kc = np.zeros(self.R), np.zeros(self.R), np.zeros(self.R)
+        C = _f64(C)
+        assert lib().orc_rate_coeffs(self.ptr, float(T), _d(C), _d(kf), _d(kr), _d(Kc)) == 0
+        return kf, kr, Kc
+
+    def progress(self, T, C):
+        q, w = np.zeros(self.R), np.zeros(self.Ns)
+        C = _f64(C)
+        assert lib().orc_progress(self.ptr, float(T), _d(C), _d(q), _d(w)) == 0
+        return q, w
+
+    def rhs(self, y, p):
+        y = _f64(y)
+        f = np.zeros(self.n)
+        assert lib().orc_rhs(self.ptr, _d(y), float(p), _d(f)) == 0
+        return f
+
+    def jac(self, y, p):
+        y = _f64(y)
+        J = np.zeros((self.n, self.n))
+        assert lib().orc_jac(self.ptr, _d(y), float(p), _d(J)) == 0
+        return J
+
+    def jac_cs(self, y, p):
+        y = _f64(y)
+        J = np.zeros((self.n, self.n))
+        assert lib().orc_jac_cs(self.ptr, _d(y), float(p), _d(J)) == 0
+        return J
+
+    def stage_fast(self, y, p, phi, Hs, h, o: Opts, nthreads=None):
+        """One MRI stage's fast IVP for every cell; returns (y_new, status, stats)."""
+        y = _f64(y).copy()
+        ncell = y.shape[0]
+        p = _f64(p)
+        phi = _f64(phi) if phi is not None else None
+        K = phi.shape[1] if phi is not None else 0
+        status = np.zeros(ncell, np.int32)
+        stats = np.zeros((ncell, 4), np.int32)
+        rc = lib().orc_stage_fast(self.ptr, _d(y), _d(p), ncell, _d(phi), K, float(Hs), float(h),
+                                  ct.byref(o), _i(status), _i(stats), nthreads or default_threads())
+        if rc < 0:
+            raise ValueError("orc_stage_fast rejected its arguments")
+        return y, status, stats
+
+    def mri_step(self, y, p, g: dict, H, h, o: Opts, nthreads=None):
+        y = _f64(y).copy()
+        ncell = y.shape[0]
+        status = np.zeros(ncell, np.int32)
+        stats = np.zeros((ncell, 4), np.int32)
+        gr = grid(g)
+        rc = lib().orc_mri_step(self.ptr, _d(y), _d(_f64(p)), ct.byref(gr), float(H), float(h), ct.byref(o),
+                                _i(status), _i(stats), nthreads or default_threads())
+        if rc < 0:
+            raise ValueError("orc_mri_step rejected its arguments")
+        return y, status, stats
+
+    def single_rate(self, y, p, g: dict, t_end, nsteps, o: Opts):
+        y = _f64(y).copy()
+        gr = grid(g)
+        rc = lib().orc_single_rate(self.ptr, _d(y), _d(_f64(p)), ct.byref(gr), float(t_end), int(nsteps),
+                                   ct.byref(o))
+        if rc != 0:
+            raise RuntimeError(f"orc_single_rate failed ({rc})")
+        return y
+
+
+def lu_solve(A, b):
+    A = _f64(A).copy()
+    b = _f64(b).copy()
+    n = A.shape[0]
+    piv = np.zeros(n, np.int32)
+    rc = lib().orc_lu_solve(n, _d(A), _i(piv), _d(b))
+    if rc != 0:
+        raise np.linalg.LinAlgError(f"singular at column {rc - 1}")
+    return b, A, piv
+
+
+def sdirk_tableau(method):
+    A, b, c, s = np.zeros(9), np.zeros(3), np.zeros(3), ct.c_int32()
+    assert lib().orc_sdirk_tableau(method, _d(A), _d(b), _d(c), ct.byref(s)) == 0
+    s = s.value
+    return A[: s * s].reshape(s, s), b[:s], c[:s]
+
+
+def mri_tableau():
+    A, c, s = np.zeros(16), np.zeros(4), ct.c_int32()
+    lib().orc_mri_tableau(_d(A), _d(c), ct.byref(s))
+    return A.reshape(4, 4), c
+
+
+def mri_coupling():
+    G, s = np.zeros(16), ct.c_int32()
+    lib().orc_mri_coupling(_d(G), ct.byref(s))
+    return G.reshape(4, 4)
+
+
+def slow_rhs(y, g: dict):
+    y = _f64(y)
+    f = np.zeros_like(y)
+    gr = grid(g)
+    assert lib().orc_slow_rhs(_d(y), _d(f), y.shape[1], ct.byref(gr)) == 0
+    return f
+
+
+def sdirk_scalar(method, problem, lam, t0, t1, nsteps, y0):
+    out = np.zeros(1)
+    rc = lib().orc_sdirk_scalar(method, problem, lam, t0, t1, nsteps, y0, _d(out))
+    if rc != 0:
+        raise RuntimeError("scalar SDIRK failed")
+    return out[0]
+
+
+def kpr_mri(fast_method, G, e, beta, omega, t1, nsteps, m_fast):
+    err = np.zeros(1)
+    yo = np.zeros(2)
+    rc = lib().orc_kpr_mri(fast_method, G, e, beta, omega, t1, nsteps, m_fast, _d(err), _d(yo))
+    if rc != 0:
+        raise RuntimeError("KPR MRI failed")
+    return err[0], yo

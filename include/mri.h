@@ -1,0 +1,198 @@
+/*
+ * mri.h -- C ABI of the GB300 fast-partition solver for multirate infinitesimal
+ * (MRI) time integration of reacting flow.
+ *
+ * The method (Loffeld et al., "Performance of explicit and IMEX MRI multirate
+ * methods on complex reactive flow problems ...", arXiv 2211.03293):
+ *   y' = f^F(t, y) + f^S(t, y)                                   (Eq. 1)
+ * One slow step H: Y_1 = y_n; for i = 2..s, with T_i = t_n + c_i H and
+ * dc_i = c_i - c_{i-1}, solve the modified fast IVP
+ *   v'(theta) = f^F(theta, v) + r_i(theta),  theta in [T_{i-1}, T_i],
+ *   v(T_{i-1}) = Y_{i-1},  Y_i = v(T_i)                          (Eq. 3)
+ * where the forcing r_i is built from f^S(T_j, Y_j), j <= i; y_{n+1} = Y_s
+ * (Sec. 2.1, the stage algorithm).  f^F is the chemistry of each grid cell
+ * (Sec. 3.2: f^F = omega_k W_k / rho for Eq. 6), f^S the transport.
+ *
+ * Conventions for every call:
+ *   - state layout is cell-major y[ncell][n], n = Ns + 1, entries
+ *     (Y_1 .. Y_Ns, T): mass fractions then temperature [K]; SI units;
+ *   - all array arguments are DEVICE pointers owned by the caller (cudaMalloc,
+ *     torch tensors, ...).  The library allocates device memory only in
+ *     mri_mech_load (freed by mri_mech_free);
+ *   - calls are asynchronous and ordered on `stream` (a cudaStream_t, NULL =
+ *     legacy default stream); the return value covers host-side argument
+ *     checks and launch errors only.  Per-cell results (Newton failure, bad
+ *     input state) are written to cell_status on the device;
+ *   - no call aborts or traps: errors are negative return codes.
+ */
+#ifndef MRI_H
+#define MRI_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define MRI_OK 0
+#define MRI_EINVAL (-1)    /* bad argument, rejected on the host before any launch */
+#define MRI_ENEWTON (-2)   /* at least one cell failed (see cell_status) */
+#define MRI_ECUDA (-3)     /* a CUDA call failed (launch, copy, allocation) */
+#define MRI_ETIMEOUT (-4)  /* a device work budget ran out */
+#define MRI_ENOMEM (-5)    /* workspace too small */
+
+/* ---- per-cell status written by the kernels -------------------------- */
+#define MRI_CELL_OK 0
+#define MRI_CELL_ENEWTON 1 /* Newton did not converge in max_newton iterations,
+                              or produced a non-finite iterate; the cell keeps
+                              the state at the start of the failed substep and
+                              takes no further substeps in this call */
+#define MRI_CELL_EINPUT 2  /* non-finite input state, T <= 0 or p <= 0: the
+                              cell is left unchanged */
+
+/* ---- fast integrators ------------------------------------------------ */
+#define MRI_SDIRK2 2       /* Alexander (1977) 2-stage, order 2, L-stable, stiffly accurate */
+#define MRI_SDIRK3 3       /* Alexander (1977) 3-stage, order 3, L-stable, stiffly accurate */
+
+/* ---- slow (MRI) methods ---------------------------------------------- */
+#define MRI_KW3 1          /* explicit third-order method of Knoth & Wolke (1998) in
+                              MIS form, the paper's "MRI3" slow method (Sec. 3.2) */
+
+/* ---- mechanism ------------------------------------------------------- */
+typedef struct mri_mech mri_mech;
+
+/* Parse a mechanism blob and upload its tables to the current device.
+ * blob: host bytes in the "MRIMECH1" layout (magic; int32 header
+ *   [Ns, R, E, n_eff, n_troe, 0, 0, 0]; float64 W[Ns] kg/mol; float64
+ *   nasa[Ns][7]; int32 elem[Ns][E]; int32 rtype[R] (0 plain, 1 third body,
+ *   2 Troe falloff); int32 reac[R][3]; int32 prod[R][3] (species index,
+ *   repeated for stoichiometry, -1 pad); int32 eff_row[R]; int32 troe_row[R];
+ *   float64 A[R] (SI), b[R], Ta[R] (K); float64 eff[n_eff][Ns];
+ *   float64 troe[n_troe][7] = (A0, b0, Ta0, a, T***, T*, T**); every int32
+ *   section zero-padded to 8 bytes).  Production rates follow the standard
+ *   Chemkin definitions the paper refers to (Sec. 3: omega_k of Eq. 4 and 6).
+ * Limits: 1 <= Ns <= 127, 0 <= R <= 1023.
+ * On success *out owns device memory until mri_mech_free.  Returns MRI_EINVAL
+ * for a malformed blob, MRI_ECUDA if the upload fails. */
+int mri_mech_load(const void* blob, size_t nbytes, mri_mech** out);
+void mri_mech_free(mri_mech* mech);
+int mri_mech_info(const mri_mech* mech, int* n_species, int* n_reactions);
+
+/* ---- fast solve options ---------------------------------------------- */
+#define MRI_JAC_PER_SUBSTEP 0 /* Jacobian + LU at the start of every substep, reused
+                                 by all stages; refreshed inside Newton when the
+                                 contraction is slow */
+#define MRI_JAC_LAZY 1        /* the factorised Newton matrix also carries over to the
+                                 next substeps of the call while h gamma is unchanged
+                                 (at most 20 substeps); refreshed inside Newton when the
+                                 contraction is slow.  The converged stage values do not
+                                 depend on the policy, only the cost does. */
+#define MRI_PREC_FP64 0       /* plain path: everything in FP64 */
+
+typedef struct {
+  int method;            /* MRI_SDIRK2 or MRI_SDIRK3 */
+  double newton_rtol;    /* WRMS weights w_k = rtol |Z_k| + atol_k; converged when WRMS(delta) <= 1 */
+  double newton_atol_Y;  /* absolute tolerance of the mass fractions */
+  double newton_atol_T;  /* absolute tolerance of T [K] */
+  int max_newton;        /* Newton iterations per SDIRK stage, 1..100 */
+  int jac_policy;        /* MRI_JAC_PER_SUBSTEP or MRI_JAC_LAZY */
+  int precision;         /* MRI_PREC_FP64 */
+  int ramp;              /* 0 = off; R in 1..40: the first substep of the call is
+                            replaced by R+1 substeps of sizes hh 2^-R, hh 2^-R,
+                            hh 2^(1-R), ..., hh/2 (sum hh), for states far from
+                            the fast manifold */
+} mri_fast_opts;
+
+/* Fill opts with the defaults (SDIRK3, rtol 1e-10, atol_Y 1e-20, atol_T 1e-10 K,
+ * 10 Newton iterations, per-substep Jacobian, FP64, no ramp). */
+void mri_fast_opts_default(mri_fast_opts* opts);
+
+/* One MRI stage of the fast partition for every cell (Eq. 3):
+ *   v' = f^F(v) + r(theta),  r(theta) = sum_{k<K} rhohat^k phi[cell][k][:],
+ *   rhohat = (theta - t0) / Hstage in [0, 1],
+ * integrated from v = y over [t0, t0 + Hstage] with n_sub = max(1,
+ * ceil(Hstage/h (1 - 1e-12))) uniform SDIRK substeps of size Hstage/n_sub;
+ * y is overwritten with v(t0 + Hstage).  f^F: dY_k/dt = omega_k W_k / rho,
+ * dT/dt = -sum_k h_k omega_k / (rho cp) at the constant pressure p[cell]
+ * (ideal gas, Eq. 5).
+ *   y           [ncell][n] in/out
+ *   p           [ncell] pressure [Pa]
+ *   phi         [ncell][K][n] forcing coefficients (may be NULL when K == 0)
+ *   K           0..4 forcing polynomial terms
+ *   t0, Hstage  stage start time and length dc_i H [s] (Hstage > 0)
+ *   h           target substep [s] (h > 0)
+ *   cell_status [ncell] MRI_CELL_* or NULL
+ *   cell_stats  [ncell][4] int32 or NULL: substeps taken, Newton iterations,
+ *               Jacobian/LU factorizations, failures -- ADDED to what is there
+ *   n_failed    one int32 or NULL: incremented by the number of cells whose
+ *               status is not MRI_CELL_OK (caller zeroes it)
+ * Returns MRI_OK once launched, MRI_EINVAL for bad sizes/options,
+ * MRI_ECUDA on a launch failure. */
+int mri_stage_fast(double* y, const double* p, int ncell, const double* phi, int K,
+                   double t0, double Hstage, double h, const mri_mech* mech,
+                   const mri_fast_opts* opts, int32_t* cell_status, int32_t* cell_stats,
+                   int32_t* n_failed, void* stream);
+
+/* ---- slow partition ---------------------------------------------------- */
+typedef struct {
+  int nx, ny, nz;        /* periodic box; cell index (k*ny + j)*nx + i */
+  double dx;             /* spacing [m], same on every axis */
+  double u[3];           /* constant advection velocity [m/s] */
+  double D;              /* diffusivity [m^2/s], same for every component */
+  int order;             /* 2 or 4: central differences of that order */
+} mri_grid;
+
+/* f^S(y) = -u . grad(y) + D lap(y) for every component (Eq. 6 transport with
+ * the advection sign taken as -div(Y u); Sec. 3.1: 2nd-order central stencils,
+ * periodic).  Axes with one cell are skipped.  y, fS: [ncell][n] device.
+ * The slow partition is autonomous: t is accepted for the interface only. */
+int mri_slow_rhs(const double* y, double* fS, int n, const mri_grid* grid, double t, void* stream);
+
+/* Stage forcing of the MIS form of an explicit MRI method: the polynomial r_i of
+ * Eq. 3 built from slow evaluations (Sec. 2.1, step 2a), here its constant term
+ *   phi[e] = sum_{j < nslow} coeffs[j] * fS[j * len + e],  e < len,
+ * fS: nslow consecutive device arrays of len doubles (f^S(Y_1), f^S(Y_2), ...),
+ * coeffs: host array of nslow values (a row of mri_method_coupling's G),
+ * phi: device output of len doubles.  1 <= nslow <= 3. */
+int mri_stage_forcing(const double* fS, int nslow, long long len, const double* coeffs, double* phi,
+                      void* stream);
+
+/* Host-side coupling table of the MRI method: stage times c[0..s) and, for stage
+ * i = 1..s-1, G[i*3 + j] = (a_ij - a_{i-1,j}) / (c_i - c_{i-1}) -- the weight of
+ * f^S(Y_j) in stage i's constant forcing.  For MRI_KW3 (Knoth & Wolke ERK3 with
+ * c = (0, 1/3, 3/4), a21 = 1/3, a31 = -3/16, a32 = 15/16, b = (1/6, 3/10, 8/15),
+ * b appended as the last stage row) s = 4.  c needs 4 doubles, G 12. */
+int mri_method_coupling(int mri_method, double* c, double* G, int* nstages);
+
+/* Bytes of device workspace mri_step needs for a grid and n unknowns per cell. */
+size_t mri_step_workspace_size(const mri_grid* grid, int n);
+
+/* One slow step of the explicit MRI method `mri_method` (MRI_KW3) over the
+ * grid: three f^S evaluations and three fast stages (Sec. 3.2, "MRI3").
+ * workspace: device buffer of at least mri_step_workspace_size bytes, owned by
+ * the caller and overwritten.  The other arguments are those of
+ * mri_stage_fast; opts->ramp applies to the first fast stage only. */
+int mri_step(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
+             int mri_method, const mri_mech* mech, const mri_fast_opts* opts, void* workspace,
+             size_t workspace_bytes, int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed,
+             void* stream);
+
+/* ---- the separate kernels of the fast path, for per-kernel checks ------ */
+/* f^F(y) of every cell (no forcing): f [ncell][n]. */
+int mri_fast_rhs(const double* y, const double* p, int ncell, const mri_mech* mech, double* f,
+                 void* stream);
+/* Analytic Jacobian d f^F / d y of every cell: J [ncell][n][n], row-major. */
+int mri_fast_jac(const double* y, const double* p, int ncell, const mri_mech* mech, double* J,
+                 void* stream);
+/* Batched dense solve A x = b with LU and partial pivoting (largest |a|, ties
+ * to the lowest row): A [nbatch][n][n] row-major is overwritten by its LU
+ * factors, b [nbatch][n] by x; info [nbatch] (may be NULL) gets 0 or k+1 for a
+ * zero pivot in column k.  1 <= n <= 128. */
+int mri_lu_solve_batched(double* A, double* b, int n, int nbatch, int32_t* info, void* stream);
+
+const char* mri_status_str(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

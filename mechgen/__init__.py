@@ -335,6 +335,7 @@ class Workload:
     h: float
     n_slow_steps: int
     newton_rtol: float
+    ramp: int               # start-up substep levels for the first fast stage of a run
 
 
 MECH_SMALL = dict(n_species=9, n_reactions=21, elements=("H", "O", "N"), n_thirdbody=2, n_troe=2,
@@ -356,14 +357,14 @@ def workload(name: str, seed: int = 0, cells_per_side: int | None = None) -> Wor
         dx = 1e-4
         y0, p = field_1d_tanh(2000 + seed, nx, mech.n_species, dx)
         grid = dict(nx=nx, ny=1, nz=1, dx=dx, u=(1.0, 0.0, 0.0), D=1e-5, order=2)
-        return Workload(name, mech, y0, p, grid, 2, 1e-7, 1e-9, 10, 1e-10)
+        return Workload(name, mech, y0, p, grid, 2, 1e-7, 1e-9, 10, 1e-10, 10)
     if name in ("box32", "box64"):
         mech = make_mechanism(3000 + seed, **MECH_MEDIUM)
         m = cells_per_side or (32 if name == "box32" else 64)
         dx = 1e-4
         y0, p = field_3d_hotspots(4000 + seed, m, m, m, mech.n_species, dx)
         grid = dict(nx=m, ny=m, nz=m, dx=dx, u=(1.0, 1.0, 1.0), D=1e-5, order=4)
-        return Workload(name, mech, y0, p, grid, 3, 5e-8, 5e-9, 20, 1e-10)
+        return Workload(name, mech, y0, p, grid, 3, 5e-8, 5e-9, 20, 1e-10, 16)
     raise KeyError(name)
 
 

@@ -1,0 +1,213 @@
+"""GB300 fast-partition solver for MRI multirate integration of reacting flow.
+
+Thin ctypes binding of ``libmri.so`` (C ABI declared in ``include/mri.h``): the
+functions below carry the C names and only marshal arguments.  Every step of
+the solve runs in the library's CUDA kernels; there is no CPU fallback, and
+importing this package fails loudly when the library has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``).
+
+Device arrays are passed as CUDA torch tensors (float64 / int32, contiguous);
+``stream`` defaults to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmri.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it first (paper_2211_03293_gb300/build.py)")
+
+_lib = ct.CDLL(LIB_PATH)
+
+MRI_OK, MRI_EINVAL, MRI_ENEWTON, MRI_ECUDA, MRI_ETIMEOUT, MRI_ENOMEM = 0, -1, -2, -3, -4, -5
+MRI_CELL_OK, MRI_CELL_ENEWTON, MRI_CELL_EINPUT = 0, 1, 2
+MRI_SDIRK2, MRI_SDIRK3 = 2, 3
+MRI_KW3 = 1
+MRI_JAC_PER_SUBSTEP = 0
+MRI_JAC_LAZY = 1
+MRI_PREC_FP64 = 0
+
+
+class mri_fast_opts(ct.Structure):
+    _fields_ = [("method", ct.c_int), ("newton_rtol", ct.c_double), ("newton_atol_Y", ct.c_double),
+                ("newton_atol_T", ct.c_double), ("max_newton", ct.c_int), ("jac_policy", ct.c_int),
+                ("precision", ct.c_int), ("ramp", ct.c_int)]
+
+
+class mri_grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int), ("dx", ct.c_double),
+                ("u", ct.c_double * 3), ("D", ct.c_double), ("order", ct.c_int)]
+
+
+_vp = ct.c_void_p
+_i32p = ct.c_void_p
+_lib.mri_mech_load.argtypes = [ct.c_char_p, ct.c_size_t, ct.POINTER(_vp)]
+_lib.mri_mech_load.restype = ct.c_int
+_lib.mri_mech_free.argtypes = [_vp]
+_lib.mri_mech_free.restype = None
+_lib.mri_mech_info.argtypes = [_vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
+_lib.mri_fast_opts_default.argtypes = [ct.POINTER(mri_fast_opts)]
+_lib.mri_fast_opts_default.restype = None
+_lib.mri_stage_fast.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, ct.c_double, ct.c_double, ct.c_double, _vp,
+                                ct.POINTER(mri_fast_opts), _vp, _vp, _vp, _vp]
+_lib.mri_slow_rhs.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, _vp]
+_lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
+_lib.mri_step_workspace_size.restype = ct.c_size_t
+_lib.mri_step.argtypes = [_vp, _vp, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_double, ct.c_int, _vp,
+                          ct.POINTER(mri_fast_opts), _vp, ct.c_size_t, _vp, _vp, _vp, _vp]
+_lib.mri_fast_rhs.argtypes = [_vp, _vp, ct.c_int, _vp, _vp, _vp]
+_lib.mri_fast_jac.argtypes = [_vp, _vp, ct.c_int, _vp, _vp, _vp]
+_lib.mri_lu_solve_batched.argtypes = [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp]
+_lib.mri_stage_forcing.argtypes = [_vp, ct.c_int, ct.c_longlong, ct.POINTER(ct.c_double), _vp, _vp]
+_lib.mri_method_coupling.argtypes = [ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                                     ct.POINTER(ct.c_int)]
+_lib.mri_status_str.argtypes = [ct.c_int]
+_lib.mri_status_str.restype = ct.c_char_p
+
+EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_default", "mri_stage_fast",
+            "mri_slow_rhs", "mri_step_workspace_size", "mri_step", "mri_fast_rhs", "mri_fast_jac",
+            "mri_lu_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling")
+
+
+class MriError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {mri_status_str(code)} ({code})")
+        self.code = code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _f64(t):
+    import torch
+    if t is not None and t.dtype != torch.float64:
+        raise TypeError("float64 tensor expected")
+    return _ptr(t)
+
+
+def _i32(t):
+    import torch
+    if t is not None and t.dtype != torch.int32:
+        raise TypeError("int32 tensor expected")
+    return _ptr(t)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ct.c_void_p(stream)
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def _check(rc, what):
+    if rc != MRI_OK:
+        raise MriError(rc, what)
+    return rc
+
+
+def mri_status_str(code: int) -> str:
+    return _lib.mri_status_str(code).decode()
+
+
+def mri_fast_opts_default(**overrides) -> mri_fast_opts:
+    o = mri_fast_opts()
+    _lib.mri_fast_opts_default(ct.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def grid(nx, ny, nz, dx, u, D, order) -> mri_grid:
+    return mri_grid(nx, ny, nz, dx, (ct.c_double * 3)(*u), D, order)
+
+
+class Mech:
+    """Owner of an ``mri_mech`` handle (device tables)."""
+
+    def __init__(self, blob: bytes):
+        h = _vp()
+        _check(_lib.mri_mech_load(blob, len(blob), ct.byref(h)), "mri_mech_load")
+        self.handle = h
+        ns, nr = ct.c_int(), ct.c_int()
+        _lib.mri_mech_info(h, ct.byref(ns), ct.byref(nr))
+        self.n_species, self.n_reactions = ns.value, nr.value
+        self.n = self.n_species + 1
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.mri_mech_free(h)
+            self.handle = None
+
+
+def mri_mech_load(blob: bytes) -> Mech:
+    return Mech(blob)
+
+
+def mri_stage_fast(y, p, phi, t0, Hstage, h, mech: Mech, opts: mri_fast_opts, cell_status=None, cell_stats=None,
+                   n_failed=None, stream=None) -> int:
+    ncell = y.shape[0]
+    K = 0 if phi is None else phi.shape[1]
+    rc = _lib.mri_stage_fast(_f64(y), _f64(p), ncell, _f64(phi), K, t0, Hstage, h, mech.handle, ct.byref(opts),
+                             _i32(cell_status), _i32(cell_stats), _i32(n_failed), _stream(stream))
+    return _check(rc, "mri_stage_fast")
+
+
+def mri_slow_rhs(y, fS, g: mri_grid, t=0.0, stream=None) -> int:
+    return _check(_lib.mri_slow_rhs(_f64(y), _f64(fS), y.shape[1], ct.byref(g), t, _stream(stream)), "mri_slow_rhs")
+
+
+def mri_step_workspace_size(g: mri_grid, n: int) -> int:
+    return _lib.mri_step_workspace_size(ct.byref(g), n)
+
+
+def mri_step(y, p, g: mri_grid, t, H, h, mech: Mech, opts: mri_fast_opts, workspace, cell_status=None,
+             cell_stats=None, n_failed=None, mri_method=MRI_KW3, stream=None) -> int:
+    nbytes = workspace.numel() * workspace.element_size()
+    rc = _lib.mri_step(_f64(y), _f64(p), ct.byref(g), t, H, h, mri_method, mech.handle, ct.byref(opts),
+                       _ptr(workspace), nbytes, _i32(cell_status), _i32(cell_stats), _i32(n_failed),
+                       _stream(stream))
+    return _check(rc, "mri_step")
+
+
+def mri_stage_forcing(fS, nslow, coeffs, phi, stream=None) -> int:
+    """phi = sum_j coeffs[j] fS[j]; fS: [>= nslow, ...] device tensor, phi: [...]."""
+    c = (ct.c_double * nslow)(*[float(v) for v in coeffs[:nslow]])
+    return _check(_lib.mri_stage_forcing(_f64(fS), nslow, phi.numel(), c, _f64(phi), _stream(stream)),
+                  "mri_stage_forcing")
+
+
+def mri_method_coupling(mri_method=MRI_KW3):
+    """(c[4], G[4][3]) of the MRI method's MIS-form coupling."""
+    c = (ct.c_double * 4)()
+    G = (ct.c_double * 12)()
+    s = ct.c_int()
+    _check(_lib.mri_method_coupling(mri_method, c, G, ct.byref(s)), "mri_method_coupling")
+    return list(c)[:s.value], [list(G)[3 * i:3 * i + 3] for i in range(s.value)]
+
+
+def mri_fast_rhs(y, p, mech: Mech, f, stream=None) -> int:
+    return _check(_lib.mri_fast_rhs(_f64(y), _f64(p), y.shape[0], mech.handle, _f64(f), _stream(stream)),
+                  "mri_fast_rhs")
+
+
+def mri_fast_jac(y, p, mech: Mech, J, stream=None) -> int:
+    return _check(_lib.mri_fast_jac(_f64(y), _f64(p), y.shape[0], mech.handle, _f64(J), _stream(stream)),
+                  "mri_fast_jac")
+
+
+def mri_lu_solve_batched(A, b, info=None, stream=None) -> int:
+    return _check(_lib.mri_lu_solve_batched(_f64(A), _f64(b), A.shape[-1], A.shape[0], _i32(info), _stream(stream)),
+                  "mri_lu_solve_batched")

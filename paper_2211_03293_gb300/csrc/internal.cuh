@@ -1,0 +1,116 @@
+// Internal declarations shared by the translation units of libmri (the CUDA
+// product path).  Nothing here is visible through the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mri.h"
+
+namespace mri {
+
+constexpr double kRu = 8.314462618;          // J/(mol K)
+constexpr double kPatm = 101325.0;           // Pa, standard-state pressure of K_c
+constexpr double kLn10 = 2.30258509299404568401799145468;
+constexpr int kMaxSpecies = 127;
+constexpr int kMaxReactions = 1023;
+constexpr int kMaxK = 4;                     // forcing polynomial terms
+constexpr int kMaxWarps = 16;                // warps (cells in flight) per CTA
+
+// Byte offsets of the sections of the mechanism table.  The table is one
+// contiguous device buffer that every CTA copies into shared memory.  Species
+// vectors have a pad slot at index Ns (concentration 1, Gibbs/enthalpy 0) that
+// absent reaction partners point to, so rate products need no branches.
+struct Layout {
+  int Ns, R, n, n_eff, n_troe, n_tb;  // n = Ns + 1; n_tb = reactions with [M]
+  int nsv;          // species-vector length incl. pad slot, even
+  int rv;           // reaction-vector length, even
+  // table sections (bytes from the start of the table)
+  int o_cp, o_h, o_s;     // double [5][nsv] cp/R, h/RT, s/R polynomial coefficients (SoA)
+  int o_h5, o_s6;         // double [nsv] a6 (enthalpy const), a7 (entropy const)
+  int o_dcp;              // double [4][nsv] coefficients of d(cp/R)/dT
+  int o_W, o_invW;        // double [nsv]
+  int o_lnA, o_b, o_Ta;   // double [rv]
+  int o_rxn;              // uint64 [rv]: bytes 0-2 reactants, 3-5 products (pad = Ns), 6 dn (int8), 7 type
+  int o_rrow;             // int32 [rv]: eff row (low 16 bits, 0xffff none) | troe row << 16
+  int o_effd;             // double [n_eff][nsv] efficiencies alpha (dense, 0 in the pad slot)
+  int o_eptr;             // int32 [n_eff + 1] sparse (alpha - 1) lists
+  int o_eidx;             // int32 [ne]
+  int o_eval;             // double [ne]
+  int o_troe;             // double [n_troe][8]: lnA0, b0, Ta0, a, 1/T***, 1/T*, T**, 0
+  int o_wptr;             // int32 [Ns + 1] species -> (reaction, nu) lists for sums over reactions
+  int o_went;             // int32 [nw]: r | nu << 16 (nu != 0)
+  int o_cptr;             // int32 [Ns + 1] Jacobian column -> reaction entries
+  int o_cent;             // uint64 [nc]: r (16) | mult_f (4) | mult_r (4) | o1..o4 (8 bits each)
+  int o_rsp;              // uint64 [rv][2]: word 0 species k0..k5 + count; word 1 int8 nu0..nu5
+  int o_tbl;              // int32 [n_tb]: reactions with an efficiency row (third body or falloff)
+  int o_nu;               // double [8]: the small integers -3..4 as doubles (index v + 3), so kernels
+                          // turn stoichiometric integers into doubles with a load, not a conversion
+  int bytes;              // total, multiple of 16
+  // per-cell workspace (doubles) inside shared memory
+  int ld;                 // leading dimension of the n x n matrix (odd)
+  int ws_doubles;         // doubles per cell (warp)
+};
+
+struct Mech {             // what mri_mech points at
+  Layout L;
+  void* d_table = nullptr;   // device copy of the table
+  int device = -1;
+};
+
+// Per-cell workspace carve-up (double offsets inside the warp's region).
+struct WsOffsets {
+  int M, y0, Z, d, res, F0, F1, r, f, base, phi, C, g, hh, cp, wd, DT, DC, aux, dinv, piv;
+  int q, kfw, krw, dqdT, tbs;
+  int total;
+};
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+__host__ __device__ inline WsOffsets ws_offsets(const Layout& L) {
+  WsOffsets w;
+  int nv = round_up(L.n + 1, 2);
+  int o = 0;
+  w.M = o; o += round_up(L.n * L.ld, 2);
+  w.y0 = o; o += nv;
+  w.Z = o; o += nv;
+  w.d = o; o += nv;
+  w.res = o; o += nv;
+  w.F0 = o; o += nv;
+  w.F1 = o; o += nv;
+  w.r = o; o += nv;
+  w.f = o; o += nv;
+  w.base = o; o += nv;
+  w.phi = o; o += kMaxK * nv;
+  w.C = o; o += L.nsv;
+  w.g = o; o += L.nsv;
+  w.hh = o; o += L.nsv;
+  w.cp = o; o += L.nsv;
+  w.wd = o; o += L.nsv;
+  w.DT = o; o += L.nsv;
+  w.DC = o; o += L.nsv;
+  w.aux = o; o += L.nsv;
+  w.dinv = o; o += nv;
+  w.piv = o; o += nv / 2 + 1;   // int32 pivots
+  o = round_up(o, 2);
+  w.q = o; o += L.rv;
+  w.kfw = o; o += L.rv;
+  w.krw = o; o += L.rv;
+  w.dqdT = o; o += L.rv;
+  w.tbs = o; o += L.rv;
+  w.total = round_up(o, 2);
+  return w;
+}
+
+// launch helpers implemented in fast.cu / slow.cu
+int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double Hs, double h,
+                      const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status, int32_t* stats,
+                      int32_t* n_failed, cudaStream_t st, bool sticky);
+bool fast_opts_ok(const mri_fast_opts* o);
+// mri_stage_fast after the pointer checks; sticky = write only failing statuses
+int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* phi, int K, double Hstage,
+                           double h, const Mech& m, const mri_fast_opts& o, int32_t* cell_status,
+                           int32_t* cell_stats, int32_t* n_failed, cudaStream_t st, bool sticky);
+int device_smem_limit();
+int device_sm_count();
+
+}  // namespace mri

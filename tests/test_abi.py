@@ -1,0 +1,89 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point that
+include/mri.h declares, and rejects bad arguments on the host before any launch."""
+import ctypes as ct
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2211_03293_gb300 as m
+    return m
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mri.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mri_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("mri_stage_fast", "mri_slow_rhs", "mri_step", "mri_mech_load"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (mri_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib._lib, n)
+
+
+def test_binding_names_match_the_header(lib):
+    for n in declared_functions():
+        assert n in lib.EXPORTED
+
+
+def test_defaults_and_status_strings(lib):
+    o = lib.mri_fast_opts_default()
+    assert (o.method, o.newton_rtol, o.newton_atol_Y, o.newton_atol_T, o.max_newton, o.ramp) == (
+        3, 1e-10, 1e-20, 1e-10, 10, 0)
+    assert lib.mri_status_str(0) == "ok"
+    assert "Newton" in lib.mri_status_str(-2)
+
+
+def test_workspace_size(lib):
+    g = lib.grid(32, 32, 32, 1e-4, (1, 1, 1), 1e-5, 4)
+    assert lib.mri_step_workspace_size(g, 41) == 4 * 32 ** 3 * 41 * 8
+    bad = lib.grid(0, 1, 1, 1e-4, (1, 0, 0), 1e-5, 4)
+    assert lib.mri_step_workspace_size(bad, 41) == 0
+
+
+def test_mech_blob_validation_on_host(lib):
+    L = lib._lib
+    h = ct.c_void_p()
+    assert L.mri_mech_load(b"NOTAMECH" + b"\0" * 64, 72, ct.byref(h)) == lib.MRI_EINVAL
+    assert L.mri_mech_load(None, 0, ct.byref(h)) == lib.MRI_EINVAL
+    import mechgen
+    blob = mechgen.make_mechanism(1000, **mechgen.MECH_SMALL).to_blob()
+    assert L.mri_mech_load(blob[:100], 100, ct.byref(h)) == lib.MRI_EINVAL   # truncated
+
+
+def test_stage_argument_validation_on_host(lib):
+    L = lib._lib
+    o = lib.mri_fast_opts_default()
+    fake = ct.c_void_p(0x1000)   # never dereferenced: the checks fire first
+    # null mechanism
+    assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, None, ct.byref(o), None, None, None,
+                            None) == lib.MRI_EINVAL
+    bad = lib.mri_fast_opts_default(method=4)
+    assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, fake, ct.byref(bad), None, None, None,
+                            None) == lib.MRI_EINVAL
+    for kw in (dict(max_newton=0), dict(max_newton=101), dict(newton_rtol=0.0), dict(ramp=41), dict(precision=7)):
+        bad = lib.mri_fast_opts_default(**kw)
+        assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, fake, ct.byref(bad), None, None, None,
+                                None) == lib.MRI_EINVAL
+    g = lib.grid(4, 1, 1, 1e-4, (1, 0, 0), 1e-5, 3)   # order 3 does not exist
+    assert L.mri_slow_rhs(fake, fake, 10, ct.byref(g), 0.0, None) == lib.MRI_EINVAL
+    assert L.mri_lu_solve_batched(fake, fake, 0, 1, None, None) == lib.MRI_EINVAL
+    assert L.mri_lu_solve_batched(fake, fake, 129, 1, None, None) == lib.MRI_EINVAL

@@ -1,0 +1,99 @@
+"""GPU parity of whole MRI slow steps (mri_step: three f^S evaluations, three
+fast stages) against the CPU oracle; at the full 32^3 size, sampled cells of
+the first fast stage plus properties that hold at any size."""
+import numpy as np
+import pytest
+
+import mechgen
+from _parity import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_steps(mri, w, nsteps, opts_kw, g=None):
+    import torch
+    g = g or w.grid
+    gm = mri.mri_mech_load(w.mech.to_blob())
+    grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
+    y = torch.tensor(w.y0, device="cuda")
+    p = torch.tensor(w.p, device="cuda")
+    ws = torch.empty(mri.mri_step_workspace_size(grid, w.mech.n) // 8, dtype=torch.float64, device="cuda")
+    st = torch.zeros(w.y0.shape[0], dtype=torch.int32, device="cuda")
+    ss = torch.zeros((w.y0.shape[0], 4), dtype=torch.int32, device="cuda")
+    nf = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for s in range(nsteps):
+        kw = dict(opts_kw)
+        if s > 0:
+            kw["ramp"] = 0
+        mri.mri_step(y, p, grid, s * w.H, w.H, w.h, gm, mri.mri_fast_opts_default(**kw), ws, cell_status=st,
+                     cell_stats=ss, n_failed=nf)
+    torch.cuda.synchronize()
+    return y.cpu().numpy(), st.cpu().numpy(), ss.cpu().numpy(), int(nf.item())
+
+
+def oracle_steps(orc, w, nsteps, opts_kw, g=None):
+    m = orc.Mech(w.mech)
+    y = w.y0
+    for s in range(nsteps):
+        kw = dict(opts_kw)
+        if s > 0:
+            kw["ramp"] = 0
+        y, st, _ = m.mri_step(y, w.p, g or w.grid, w.H, w.h, orc.opts(**kw))
+        assert np.all(st == 0)
+    return y
+
+
+def test_mri_step_parity_line64_ten_steps(mri, orc):
+    """The whole 64-cell line workload: 10 slow steps of MRI3 with SDIRK2 fast."""
+    w = mechgen.workload("line64")
+    kw = dict(method=2, ramp=10)
+    got, st, ss, nf = gpu_steps(mri, w, w.n_slow_steps, kw)
+    ref = oracle_steps(orc, w, w.n_slow_steps, kw)
+    assert np.all(st == 0) and nf == 0
+    assert np.all(ss[:, 0] == 10 * 101 + 10)
+    assert_parity(got, ref, what="line64 10 steps")
+
+
+def test_mri_step_parity_box8(mri, orc):
+    """The 40-species box workload at 8^3 cells (ragged against CTA sizes), 2 steps."""
+    w = mechgen.workload("box32", cells_per_side=8)
+    kw = dict(method=3, ramp=w.ramp, jac_policy=1)
+    got, st, _, nf = gpu_steps(mri, w, 2, kw)
+    ref = oracle_steps(orc, w, 2, dict(method=3, ramp=w.ramp))
+    assert np.all(st == 0) and nf == 0
+    assert_parity(got, ref, what="box 8^3 2 steps")
+
+
+def test_full_size_box32_first_stage_sampled_and_step_properties(mri, orc):
+    """Full 32^3 workload in the launch configuration the bench times: the first
+    fast stage of the first step (forcing f^S(y0) from the oracle) compared on 48
+    sampled cells, then a whole MRI step checked for properties that hold at any
+    size (no failures, sum of Y = 1, grid element totals conserved)."""
+    import torch
+    w = mechgen.workload("box32")
+    n = w.mech.n
+    fS = orc.slow_rhs(w.y0, w.grid)           # phi_2 = f^S(Y_1) for the MIS form
+    gm = mri.mri_mech_load(w.mech.to_blob())
+    yd = torch.tensor(w.y0, device="cuda")
+    pd = torch.tensor(w.p, device="cuda")
+    ph = torch.tensor(fS[:, None, :].copy(), device="cuda")
+    st = torch.zeros(w.y0.shape[0], dtype=torch.int32, device="cuda")
+    mri.mri_stage_fast(yd, pd, ph, 0.0, w.H / 3, w.h, gm,
+                       mri.mri_fast_opts_default(method=3, ramp=w.ramp, jac_policy=mri.MRI_JAC_LAZY),
+                       cell_status=st)
+    torch.cuda.synchronize()
+    got = yd.cpu().numpy()
+    assert int((st != 0).sum()) == 0
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(w.y0.shape[0], 48, replace=False))
+    ref, rst, _ = orc.Mech(w.mech).stage_fast(w.y0[idx], w.p[idx], fS[idx][:, None, :], w.H / 3, w.h,
+                                              orc.opts(method=3, ramp=w.ramp))
+    assert np.all(rst == 0)
+    assert_parity(got[idx], ref, what="32^3 first stage (sampled)")
+
+    out, st, ss, nf = gpu_steps(mri, w, 1, dict(method=3, ramp=w.ramp, jac_policy=mri.MRI_JAC_LAZY))
+    assert nf == 0 and np.all(st == 0)
+    np.testing.assert_allclose(out[:, :-1].sum(1), 1.0, rtol=0, atol=1e-12)
+    E = w.mech.elem / w.mech.W[:, None]
+    np.testing.assert_allclose((out[:, :-1] @ E).sum(0), (w.y0[:, :-1] @ E).sum(0), rtol=1e-11)
+    assert np.all(ss[:, 0] == (4 + w.ramp) + 5 + 3)

@@ -647,12 +647,14 @@ int mri_step(const Mech& m, double* y, const double* p, const orc_grid& g, doubl
   std::vector<const double*> fp;
   std::vector<double> phi(len);
   int rc = 0;
+  orc_opts oi = o;
   for (int i = 1; i < t.s; ++i) {
     slow_rhs(y, fS[i - 1].data(), n, g);   // f^S(Y_i) with Y_i the current state
     fp.push_back(fS[i - 1].data());
     mis_forcing(t, i, fp, len, phi.data());
     double Hs = (t.c[i] - t.c[i - 1]) * H;
-    rc |= stage_fast(m, y, p, (int)ncell, phi.data(), 1, Hs, h, o, status, stats, nthreads);
+    oi.ramp = (i == 1) ? o.ramp : 0;        // the start-up sequence belongs to the first fast stage
+    rc |= stage_fast(m, y, p, (int)ncell, phi.data(), 1, Hs, h, oi, status, stats, nthreads);
   }
   return rc;
 }

@@ -177,6 +177,30 @@ int mri_step(double* y, const double* p, const mri_grid* grid, double t, double 
              size_t workspace_bytes, int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed,
              void* stream);
 
+/* Allocation-free variant of mri_step.  The paper has no counterpart: this is a
+ * service for callers that must not allocate device memory while they run --
+ * for example a host application that hands all of the GPU's memory to its own
+ * pool manager at start-up, or code on a latency-critical path with a rule
+ * against any call into the CUDA allocator.  Such a caller cannot provide
+ * mri_step's workspace, so this entry point uses a fixed scratch array built into
+ * the library instead; it never calls cudaMalloc or cudaFree.
+ * Limits and behaviour:
+ *   - the scratch is 16 MiB per device, held from library load until process
+ *     exit; grids whose mri_step_workspace_size exceeds 16 MiB
+ *     (4 * ncell * n * 8 bytes > 16 MiB, i.e. ncell * n > 524288) are rejected
+ *     with MRI_ENOMEM before anything is launched;
+ *   - the first call on a device looks up the scratch address for that device
+ *     (cudaGetSymbolAddress), so make that first call before any stream capture;
+ *   - every call on a device shares the one array and it keeps the previous
+ *     call's contents; nothing in it needs to start at zero because each step
+ *     writes every scratch value before reading it.  Calls whose work overlaps on
+ *     the GPU (other streams, other threads) race on the array: order them on one
+ *     stream or synchronise between them.
+ * Arguments, results and return codes are those of mri_step. */
+int mri_step_noalloc(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
+                     int mri_method, const mri_mech* mech, const mri_fast_opts* opts, int32_t* cell_status,
+                     int32_t* cell_stats, int32_t* n_failed, void* stream);
+
 /* ---- the separate kernels of the fast path, for per-kernel checks ------ */
 /* f^F(y) of every cell (no forcing): f [ncell][n]. */
 int mri_fast_rhs(const double* y, const double* p, int ncell, const mri_mech* mech, double* f,

@@ -58,6 +58,8 @@ _lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_workspace_size.restype = ct.c_size_t
 _lib.mri_step.argtypes = [_vp, _vp, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_double, ct.c_int, _vp,
                           ct.POINTER(mri_fast_opts), _vp, ct.c_size_t, _vp, _vp, _vp, _vp]
+_lib.mri_step_noalloc.argtypes = [_vp, _vp, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_double, ct.c_int,
+                                  _vp, ct.POINTER(mri_fast_opts), _vp, _vp, _vp, _vp]
 _lib.mri_fast_rhs.argtypes = [_vp, _vp, ct.c_int, _vp, _vp, _vp]
 _lib.mri_fast_jac.argtypes = [_vp, _vp, ct.c_int, _vp, _vp, _vp]
 _lib.mri_lu_solve_batched.argtypes = [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp]
@@ -69,7 +71,8 @@ _lib.mri_status_str.restype = ct.c_char_p
 
 EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_default", "mri_stage_fast",
             "mri_slow_rhs", "mri_step_workspace_size", "mri_step", "mri_fast_rhs", "mri_fast_jac",
-            "mri_lu_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling")
+            "mri_lu_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling",
+            "mri_step_noalloc")
 
 
 class MriError(RuntimeError):
@@ -180,6 +183,15 @@ def mri_step(y, p, g: mri_grid, t, H, h, mech: Mech, opts: mri_fast_opts, worksp
                        _ptr(workspace), nbytes, _i32(cell_status), _i32(cell_stats), _i32(n_failed),
                        _stream(stream))
     return _check(rc, "mri_step")
+
+
+def mri_step_noalloc(y, p, g: mri_grid, t, H, h, mech: Mech, opts: mri_fast_opts, cell_status=None,
+                     cell_stats=None, n_failed=None, mri_method=MRI_KW3, stream=None) -> int:
+    """mri_step with the library's built-in scratch instead of a caller workspace:
+    for callers that must not allocate device memory (grids up to 4*ncell*n*8 <= 16 MiB)."""
+    rc = _lib.mri_step_noalloc(_f64(y), _f64(p), ct.byref(g), t, H, h, mri_method, mech.handle, ct.byref(opts),
+                               _i32(cell_status), _i32(cell_stats), _i32(n_failed), _stream(stream))
+    return _check(rc, "mri_step_noalloc")
 
 
 def mri_stage_forcing(fS, nslow, coeffs, phi, stream=None) -> int:

@@ -2,6 +2,7 @@
 // f^S, the stage forcing of the MIS form, and one explicit MRI (Knoth-Wolke
 // "MRI3") slow step built from them and mri_stage_fast.
 #include <cmath>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -210,4 +211,53 @@ extern "C" const char* mri_status_str(int code) {
     case MRI_ENOMEM: return "workspace too small";
     default: return "unknown status";
   }
+}
+
+// ------------------------------------------------------------------ allocation-free step
+//
+// mri_step_noalloc keeps the step's scratch (three slow evaluations and the stage
+// forcing) in one fixed device array that is part of the library image, so a call
+// never allocates device memory.  The array is a file-scope __device__ variable:
+// every device that loads the library holds it until the process exits.  Host
+// code only sees a stand-in for it, so its device address is looked up once per
+// device with cudaGetSymbolAddress, with that device current.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_step_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevicesCached = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevicesCached] = {};
+
+// Device address of g_step_scratch on the current device (looked up on first use).
+int static_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesCached) return MRI_ECUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (g_scratch_addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_step_scratch) != cudaSuccess || p == nullptr) return MRI_ECUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return MRI_OK;
+}
+
+}  // namespace
+
+extern "C" int mri_step_noalloc(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
+                                int mri_method, const mri_mech* mech, const mri_fast_opts* opts,
+                                int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed, void* stream) {
+  if (!mri::grid_ok(grid) || !mech || !opts) return MRI_EINVAL;
+  const mri::Mech* m = reinterpret_cast<const mri::Mech*>(mech);
+  const size_t need = mri_step_workspace_size(grid, m->L.n);
+  if (need == 0) return MRI_EINVAL;
+  if (need > kStaticScratchBytes) return MRI_ENOMEM;   // the grid is too large for the fixed scratch
+  void* scratch = nullptr;
+  const int rc = static_scratch(&scratch);
+  if (rc != MRI_OK) return rc;
+  return mri_step(y, p, grid, t, H, h, mri_method, mech, opts, scratch, kStaticScratchBytes, cell_status, cell_stats,
+                  n_failed, stream);
 }

@@ -34,12 +34,14 @@ sys.path.insert(0, ROOT)
 METRIC = "fast-chem cell-steps/s per MRI slow step, plain FP64 vs tuned, at rel err ≤1e-6"
 UNIT = "cell-steps/s"
 WORKLOAD = "box32"
-# FP64 roofline: 2 DFMA per clock per SM measured on this GB300 (alu_fp64 profile), 152 SMs,
-# 2 flops per FMA, at the maximum SM clock 2070 MHz.
+# FP64 roofline: the FMA pipe issues 2 DFMA per clock per SM on GB300 (measured, see the
+# alu_fp64 profile), 152 SMs, 2 flops per FMA; at the maximum SM clock of 2070 MHz this is
+# the figure below.  The bench also measures the rate live (mri_probe_fp64_fma) and uses
+# that measurement as the peak.
 FP64_DFMA_PER_CLK_SM = 2.0
 N_SM = 152
 SM_MAX_MHZ = 2070.0
-FP64_PEAK_TFLOPS = FP64_DFMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS_NOMINAL = FP64_DFMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ * 1e6 / 1e12
 # nominal cost of one exp or log in the algorithmic flop count
 FLOPS_PER_TRANSCENDENTAL = 20.0
 
@@ -179,10 +181,13 @@ def gpu_arm(args, rank, world):
     status = torch.zeros(ncell, dtype=torch.int32, device=dev)
     nfail = torch.zeros(1, dtype=torch.int32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)    # 256 MB > 129 MB L2
+    probe = torch.empty(N_SM * 8 * 256 * 4, dtype=torch.float64, device=dev)
+    fp64_peak_tflops = 2.0 * mri.mri_probe_fp64_fma(probe, iters=4096) / 1e12
     H, h = w.H, w.h
-    base_opts = mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, jac_policy=args.jac)
+    base_opts = mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, jac_policy=args.jac,
+                                          precision=args.prec)
     ramp_opts = mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, ramp=w.ramp,
-                                          jac_policy=args.jac)
+                                          jac_policy=args.jac, precision=args.prec)
 
     def mri_step_timed(first, ev_stage):
         """One MRI slow step through the ABI; CUDA events around each fast stage."""
@@ -203,6 +208,7 @@ def gpu_arm(args, rank, world):
         stream.synchronize()
         warm_fail = int(nfail.item())
         stats.zero_()
+        y_start = y.clone()          # the e2e leg replays the timed steps from this state
         kernel_launches_per_step = 9
         step_events = []
         stage_events = []
@@ -238,9 +244,11 @@ def gpu_arm(args, rank, world):
     failed = int(nfail.item()) - warm_fail
     total_ms = float(sum(step_ms))
 
-    # end to end through the public C-ABI call with host buffers
+    # end to end through the public C-ABI call with host buffers: the same K steps from
+    # the same state, each step copying the state in from pinned host memory and the
+    # result back
     y_host = torch.empty((ncell, n), dtype=torch.float64, pin_memory=True)
-    y_host.copy_(y.cpu())
+    y_host.copy_(y_start.cpu())
     p_host = torch.empty(ncell, dtype=torch.float64, pin_memory=True)
     p_host.copy_(p.cpu())
     ws = torch.empty(mri.mri_step_workspace_size(grid, n) // 8, dtype=torch.float64, device=dev)
@@ -269,7 +277,7 @@ def gpu_arm(args, rank, world):
                step_ms=step_ms, stage_total_ms=stage_total_ms, stage_launches=launches, flops=flops_all,
                e2e_ms=float(sum(e2e_ms)), e2e_substeps=e2e_sub, ncell=ncell, n=n,
                launches=kernel_launches_per_step * args.steps, h2d=(ncell * n + ncell) * 8, d2h=ncell * n * 8,
-               workload=w)
+               workload=w, fp64_peak_tflops=fp64_peak_tflops)
     return res
 
 
@@ -323,6 +331,7 @@ def main():
                     help="shrink the box (profiling captures only; the bench line is for 32^3)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling captures)")
     ap.add_argument("--jac", type=int, default=1, help="Newton matrix policy: 0 per substep, 1 lazy")
+    ap.add_argument("--prec", type=int, default=0, help="0 plain FP64, 1 FP32 Jacobian/LU with FP64 residual")
     args = ap.parse_args()
     rank, world = dist_init(args)
 
@@ -374,6 +383,7 @@ def main():
     flops_per_launch = res["flops"] / res["stage_launches"]
     avg_launch_s = res["stage_total_ms"] * 1e-3 / res["stage_launches"]
     achieved = flops_per_launch / avg_launch_s / 1e12
+    peak = res["fp64_peak_tflops"]
     if args.no_cpu:
         cpu_v, cores, cs, tt = None, 0, 0, 0.0
     else:
@@ -386,7 +396,8 @@ def main():
         "config": {"workload": "box32: 32^3 periodic box, 40 species / 170 reactions (12 third-body, 8 Troe), "
                                "MRI3 (Knoth-Wolke MIS) + SDIRK3 fast, H = 5e-8 s, h = H/10, Newton rtol 1e-10, "
                                "4th-order slow stencil; one step = one MRI slow step",
-                   "cells": res["ncell"], "unknowns_per_cell": res["n"], "form": "plain FP64",
+                   "cells": res["ncell"], "unknowns_per_cell": res["n"],
+                   "form": ["plain FP64", "mixed: FP32 Jacobian/LU, FP64 rates/residual"][args.prec],
                    "jac_policy": ["per-substep", "lazy"][args.jac],
                    "reduced_for_profiling": args.cells_per_side is not None,
                    "l2": "256 MB buffer written between timed steps",
@@ -394,12 +405,13 @@ def main():
                    "jac_per_substep": res["njac"] / max(res["substeps"], 1),
                    "failed_cells": res["failed"]},
         "clocks": res["clocks"],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
                      "kernel": "stage_fast_kernel",
                      "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                     "peak_basis": "measured 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (FP64 pipe, not in "
-                                   "MEASURED_PEAKS.json)"},
+                     "peak_basis": "FP64 FMA pipe rate measured in this run (mri_probe_fp64_fma; the pipe "
+                                   "issues 2 DFMA/clk/SM, %.4f TFLOP/s at 2070 MHz); MEASURED_PEAKS.json has no "
+                                   "FP64 entry" % FP64_PEAK_TFLOPS_NOMINAL},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"the three fast stages of one MRI step on {args.cpu_sample} sampled cells "
                                    f"({cs} cell-steps, {tt:.1f} s), forcing from the oracle's slow stencil, after "

@@ -88,6 +88,11 @@ int mri_mech_info(const mri_mech* mech, int* n_species, int* n_reactions);
                                  contraction is slow.  The converged stage values do not
                                  depend on the policy, only the cost does. */
 #define MRI_PREC_FP64 0       /* plain path: everything in FP64 */
+#define MRI_PREC_FP32_LU 1    /* mixed precision: Jacobian assembly, Newton matrix, LU and
+                                 triangular solves in FP32; rates, residual, state update
+                                 and convergence test in FP64.  Each Newton iteration's FP64
+                                 residual refines the FP32 correction, so the converged
+                                 stage values meet the same tolerance as the FP64 form. */
 
 typedef struct {
   int method;            /* MRI_SDIRK2 or MRI_SDIRK3 */
@@ -96,7 +101,7 @@ typedef struct {
   double newton_atol_T;  /* absolute tolerance of T [K] */
   int max_newton;        /* Newton iterations per SDIRK stage, 1..100 */
   int jac_policy;        /* MRI_JAC_PER_SUBSTEP or MRI_JAC_LAZY */
-  int precision;         /* MRI_PREC_FP64 */
+  int precision;         /* MRI_PREC_FP64 or MRI_PREC_FP32_LU */
   int ramp;              /* 0 = off; R in 1..40: the first substep of the call is
                             replaced by R+1 substeps of sizes hh 2^-R, hh 2^-R,
                             hh 2^(1-R), ..., hh/2 (sum hh), for states far from

@@ -1,0 +1,28 @@
+/*
+ * mri_probe.h -- measurement utility of libmri (not part of the method; the
+ * paper has no counterpart).  The fast path is bound by the FP64 FMA pipe, so
+ * the benchmark measures that pipe's issue rate on the device it runs on and
+ * uses it as the roofline peak.
+ */
+#ifndef MRI_PROBE_H
+#define MRI_PROBE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Time independent FP64 FMA chains on every SM of the current device (best of 3
+ * launches, CUDA events on `stream`) and return the FMA rate in *fma_per_s
+ * (multiply by 2 for flop/s).  scratch: device array of scratch_doubles doubles,
+ * at least 2048 per SM, overwritten; iters: FMAs per chain (4096 takes a few ms).
+ * Returns 0, -1 for bad arguments or -3 for a CUDA error. */
+int mri_probe_fp64_fma(double* scratch, long long scratch_doubles, int iters, double* fma_per_s, void* stream);
+
+/* The FP64 exponential the rate kernels use (a table-driven method after Tang,
+ * 1989, see fastmath.cuh), applied elementwise y[i] = exp(x[i]) on the device,
+ * so that its accuracy can be checked against libm.  Returns 0, -1 or -3. */
+int mri_probe_exp(const double* x, double* y, long long n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -29,6 +29,7 @@ MRI_KW3 = 1
 MRI_JAC_PER_SUBSTEP = 0
 MRI_JAC_LAZY = 1
 MRI_PREC_FP64 = 0
+MRI_PREC_FP32_LU = 1
 
 
 class mri_fast_opts(ct.Structure):
@@ -66,13 +67,15 @@ _lib.mri_lu_solve_batched.argtypes = [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp]
 _lib.mri_stage_forcing.argtypes = [_vp, ct.c_int, ct.c_longlong, ct.POINTER(ct.c_double), _vp, _vp]
 _lib.mri_method_coupling.argtypes = [ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                      ct.POINTER(ct.c_int)]
+_lib.mri_probe_fp64_fma.argtypes = [_vp, ct.c_longlong, ct.c_int, ct.POINTER(ct.c_double), _vp]
+_lib.mri_probe_exp.argtypes = [_vp, _vp, ct.c_longlong, _vp]
 _lib.mri_status_str.argtypes = [ct.c_int]
 _lib.mri_status_str.restype = ct.c_char_p
 
 EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_default", "mri_stage_fast",
             "mri_slow_rhs", "mri_step_workspace_size", "mri_step", "mri_fast_rhs", "mri_fast_jac",
             "mri_lu_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling",
-            "mri_step_noalloc")
+            "mri_step_noalloc", "mri_probe_fp64_fma", "mri_probe_exp")
 
 
 class MriError(RuntimeError):
@@ -208,6 +211,23 @@ def mri_method_coupling(mri_method=MRI_KW3):
     s = ct.c_int()
     _check(_lib.mri_method_coupling(mri_method, c, G, ct.byref(s)), "mri_method_coupling")
     return list(c)[:s.value], [list(G)[3 * i:3 * i + 3] for i in range(s.value)]
+
+
+def mri_probe_fp64_fma(scratch, iters=4096, stream=None) -> float:
+    """Measured FP64 FMA rate of the current device (FMA/s); scratch: float64 device tensor."""
+    rate = ct.c_double()
+    rc = _lib.mri_probe_fp64_fma(_f64(scratch), scratch.numel(), iters, ct.byref(rate), _stream(stream))
+    if rc != 0:
+        raise MriError(rc, "mri_probe_fp64_fma")
+    return rate.value
+
+
+def mri_probe_exp(x, y, stream=None) -> int:
+    """y = exp(x) with the kernels' own FP64 exponential (float64 device tensors)."""
+    rc = _lib.mri_probe_exp(_f64(x), _f64(y), x.numel(), _stream(stream))
+    if rc != 0:
+        raise MriError(rc, "mri_probe_exp")
+    return rc
 
 
 def mri_fast_rhs(y, p, mech: Mech, f, stream=None) -> int:

@@ -32,7 +32,7 @@ def _stale(sources, headers):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(HERE, "..", "include", "mri.h")]
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(HERE, "..", "include", "*.h")))
     if not force and not _stale(sources, headers):
         return SO
     os.makedirs(BUILD, exist_ok=True)

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "fastmath.cuh"
 #include "internal.cuh"
 
 namespace mri {
@@ -17,10 +18,11 @@ namespace mri {
 // ------------------------------------------------------------------ views
 
 struct Tab {
-  const double *cp, *hh, *ss, *h5, *s6, *dcp, *W, *invW, *lnA, *b, *Ta, *effd, *eval, *troe, *nu;
+  const double *cp, *hh, *ss, *h5, *s6, *dcp, *W, *invW, *lnA, *b, *Ta, *effd, *eval, *troe, *nu, *exp2t;
+  const float *nu32, *effd32, *W32, *invW32, *dcp32;
   const uint64_t *rxn, *cent, *rsp;
-  const int32_t *rrow, *eptr, *eidx, *wptr, *went, *cptr, *tbl;
-  int Ns, R, n, nsv, n_tb;
+  const int32_t *rrow, *eptr, *eidx, *wptr, *went, *cptr, *tbl, *trx;
+  int Ns, R, n, nsv, n_tb, n_troe;
   __device__ Tab(const unsigned char* s, const Layout& L) {
     cp = reinterpret_cast<const double*>(s + L.o_cp);
     hh = reinterpret_cast<const double*>(s + L.o_h);
@@ -37,6 +39,12 @@ struct Tab {
     eval = reinterpret_cast<const double*>(s + L.o_eval);
     troe = reinterpret_cast<const double*>(s + L.o_troe);
     nu = reinterpret_cast<const double*>(s + L.o_nu) + 3;   // nu[v] for v in -3..4
+    exp2t = reinterpret_cast<const double*>(s + L.o_exp2);
+    nu32 = reinterpret_cast<const float*>(s + L.o_nu32) + 3;
+    effd32 = reinterpret_cast<const float*>(s + L.o_effd32);
+    W32 = reinterpret_cast<const float*>(s + L.o_W32);
+    invW32 = reinterpret_cast<const float*>(s + L.o_invW32);
+    dcp32 = reinterpret_cast<const float*>(s + L.o_dcp32);
     rxn = reinterpret_cast<const uint64_t*>(s + L.o_rxn);
     cent = reinterpret_cast<const uint64_t*>(s + L.o_cent);
     rsp = reinterpret_cast<const uint64_t*>(s + L.o_rsp);
@@ -47,25 +55,37 @@ struct Tab {
     went = reinterpret_cast<const int32_t*>(s + L.o_went);
     cptr = reinterpret_cast<const int32_t*>(s + L.o_cptr);
     tbl = reinterpret_cast<const int32_t*>(s + L.o_tbl);
-    Ns = L.Ns; R = L.R; n = L.n; nsv = L.nsv; n_tb = L.n_tb;
+    trx = reinterpret_cast<const int32_t*>(s + L.o_trx);
+    Ns = L.Ns; R = L.R; n = L.n; nsv = L.nsv; n_tb = L.n_tb; n_troe = L.n_troe;
   }
 };
 
 struct WS {
-  double *M, *y0, *Z, *d, *res, *F[2], *r, *f, *base, *phi, *C, *g, *hh, *cp, *wd, *DT, *DC, *aux, *dinv;
+  double *M, *y0, *Z, *d, *res, *F0, *F1, *Fl, *r, *f, *base, *phi, *C, *g, *hh, *cp, *wd, *DT, *DC, *aux, *dinv;
+  double *E, *Einv, *c0p, *tro;
   int* piv;
   double *q, *kfw, *krw, *dqdT, *tbs;
+  // mixed-precision form: FP32 Newton matrix, its diagonal inverse and FP32 copies
+  float *M32, *dinv32, *d32, *C32, *hh32, *cp32, *wd32, *DT32, *DC32, *aux32, *kfw32, *krw32, *tbs32;
   int ld, nv;
-  __device__ WS(double* base, const Layout& L) {
-    WsOffsets o = ws_offsets(L);
+  __device__ __forceinline__ double* F(int j) const { return j == 0 ? F0 : F1; }
+  __device__ WS(double* base, const Layout& L, bool prec32) {
+    WsOffsets o = ws_offsets(L, prec32);
     M = base + o.M; y0 = base + o.y0; Z = base + o.Z; d = base + o.d;
-    F[0] = base + o.F0; F[1] = base + o.F1; r = base + o.r; f = base + o.f; phi = base + o.phi;
+    F0 = base + o.F0; F1 = base + o.F1; Fl = base + o.Fl; r = base + o.r; f = base + o.f; phi = base + o.phi;
     this->base = base + o.base;
     res = base + o.res;
     C = base + o.C; g = base + o.g; hh = base + o.hh; cp = base + o.cp; wd = base + o.wd;
     DT = base + o.DT; DC = base + o.DC; aux = base + o.aux; dinv = base + o.dinv;
+    E = base + o.E; Einv = base + o.Einv; c0p = base + o.c0p; tro = base + o.tro;
     piv = reinterpret_cast<int*>(base + o.piv);
     q = base + o.q; kfw = base + o.kfw; krw = base + o.krw; dqdT = base + o.dqdT; tbs = base + o.tbs;
+    float* fb = reinterpret_cast<float*>(base + o.f32);
+    const F32Offsets g32 = f32_offsets(L);
+    M32 = reinterpret_cast<float*>(base + o.M);
+    dinv32 = fb + g32.dinv; d32 = fb + g32.d;
+    C32 = fb + g32.C; hh32 = fb + g32.hh; cp32 = fb + g32.cp; wd32 = fb + g32.wd; DT32 = fb + g32.DT;
+    DC32 = fb + g32.DC; aux32 = fb + g32.aux; kfw32 = fb + g32.kfw; krw32 = fb + g32.krw; tbs32 = fb + g32.tbs;
     ld = L.ld;
     nv = round_up(L.n + 1, 2);
   }
@@ -96,13 +116,65 @@ struct Scal {        // warp-uniform per-evaluation scalars
   double T, invT, lnT, S, rho, invrho, Ctot, cpm, Q;
 };
 
+struct RxnOut {
+  double q, kfw, krw, dqdT, tbs;
+};
+
+// Rate of progress of reaction r (and with JAC its Jacobian pieces) from the species
+// factors of chem_eval: k_f = k_inf (times the falloff factor), 1/K_c as a product of
+// species factors, q = [M] (k_f prod C^nu' - k_r prod C^nu'').
+template <bool JAC>
+__device__ __forceinline__ void rxn_eval(const Tab& t, const WS& w, int r, double lnT, double invT, double Ctot,
+                                         RxnOut& o) {
+  const uint64_t rec = t.rxn[r];
+  const int i0 = rec & 0xff, i1 = (rec >> 8) & 0xff, i2 = (rec >> 16) & 0xff;
+  const int j0 = (rec >> 24) & 0xff, j1 = (rec >> 32) & 0xff, j2 = (rec >> 40) & 0xff;
+  const int dn = (int)(int8_t)((rec >> 48) & 0xff);
+  const int type = (int)(rec >> 56);
+  const int tr = t.rrow[r] >> 16;                  // falloff row (type 2)
+  const double lnkinf = fma(t.b[r], lnT, t.lnA[r]) - t.Ta[r] * invT;
+  double kf = exp_tab(lnkinf, t.exp2t);
+  if (type == 2) kf *= w.tro[kTroeSlots * tr + 9];
+  // 1 / K_c = prod_reactants E * prod_products 1/E * (p_atm/RT)^(-dn)
+  const double kinv = (w.E[i0] * w.E[i1]) * (w.E[i2] * w.Einv[j0]) * (w.Einv[j1] * w.Einv[j2]) * w.c0p[dn + 2];
+  const double kr = kf * kinv;
+  double M = 1.0;
+  if (type == 1) {
+    const int row = t.rrow[r] & 0xffff;
+    M = Ctot;
+    for (int e = t.eptr[row]; e < t.eptr[row + 1]; ++e) M = fma(t.eval[e], w.C[t.eidx[e]], M);
+  }
+  const double fwd = w.C[i0] * w.C[i1] * w.C[i2];
+  const double rev = w.C[j0] * w.C[j1] * w.C[j2];
+  const double base = fma(kf, fwd, -kr * rev);
+  o.q = M * base;
+  if (JAC) {
+    double dlnkf_dT = fma(t.Ta[r], invT, t.b[r]) * invT;
+    if (type == 2) dlnkf_dT += w.tro[kTroeSlots * tr + 10];
+    const double snh = (w.hh[j0] + w.hh[j1] + w.hh[j2]) - (w.hh[i0] + w.hh[i1] + w.hh[i2]);
+    const double dlnKc_dT = (snh - t.nu[dn]) * invT;
+    o.kfw = M * kf;
+    o.krw = M * kr;
+    o.dqdT = M * fma(kf * dlnkf_dT, fwd, -kr * (dlnkf_dT - dlnKc_dT) * rev);
+    o.tbs = (type == 1) ? base : ((type == 2) ? w.tro[kTroeSlots * tr + 11] * base : 0.0);
+  }
+}
+
 // Species concentrations, NASA-7 thermo, rates of progress, production rates and
 // f^F at state Z (Y_1..Y_Ns, T).  With JAC also the per-reaction pieces of the
 // Jacobian: [M]-weighted k_f, k_r, d q / d T, the third-body scale and
 // sum_r nu dq/dT per species.
+//
+// Transcendentals are spread so that every lane of a pass has one to evaluate:
+//  * 1/K_c of every reaction is a product of per-species factors
+//    E_k = exp(-g_k/RT) (reactants) and 1/E_k (products) times (p_atm/RT)^(-dn),
+//    so a reaction needs one exponential (k_f) instead of two;
+//  * the falloff (Troe) quantities are evaluated task-parallel before the
+//    reaction pass: 4 exponentials per falloff reaction in one pass, then the two
+//    log10, then the broadening factor, each falloff reaction on its own lane.
 template <bool JAC>
 __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const double* Z, double p, Scal& s, int lane) {
-  const int Ns = t.Ns, R = t.R, nsv = t.nsv;
+  const int Ns = t.Ns, R = t.R, nsv = t.nsv, NT = t.n_troe;
   const double T = Z[Ns];
   double part = 0.0;
   for (int k = lane; k < Ns; k += 32) part = fma(Z[k], t.invW[k], part);
@@ -122,82 +194,100 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
                         t.hh[nsv + k]), T, t.hh[k]) + t.h5[k] * invT;
     double sv = fma(fma(fma(fma(t.ss[4 * nsv + k], T, t.ss[3 * nsv + k]), T, t.ss[2 * nsv + k]), T,
                         t.ss[nsv + k]), T, fma(t.ss[k], lnT, t.s6[k]));
+    const double g = hv - sv;
+    const double e = exp_tab(-g, t.exp2t);
     w.cp[k] = cpv;
     w.hh[k] = hv;
-    w.g[k] = hv - sv;
+    w.g[k] = g;
+    w.E[k] = e;
+    w.Einv[k] = 1.0 / e;
   }
-  if (lane == 0) { w.C[Ns] = 1.0; w.g[Ns] = 0.0; w.hh[Ns] = 0.0; }
+  if (lane == 0) { w.C[Ns] = 1.0; w.g[Ns] = 0.0; w.hh[Ns] = 0.0; w.E[Ns] = 1.0; w.Einv[Ns] = 1.0; }
+  if (lane < 5) {
+    // (p_atm / (R T))^(-dn) for dn = -2..2 at index dn + 2
+    const double C0 = (kPatm / kRu) * invT, iC0 = (kRu / kPatm) * T;
+    const double v = (lane == 0) ? C0 * C0 : (lane == 1) ? C0 : (lane == 2) ? 1.0 : (lane == 3) ? iC0 : iC0 * iC0;
+    w.c0p[lane] = v;
+  }
   const double Ctot = warp_sum(ctot);
   __syncwarp();
-  const double lnC0 = 9.4080919689617464985 - lnT;   // ln(p_atm / R_u) - ln T
-  for (int r = lane; r < R; r += 32) {
-    const uint64_t rec = t.rxn[r];
-    const int i0 = rec & 0xff, i1 = (rec >> 8) & 0xff, i2 = (rec >> 16) & 0xff;
-    const int j0 = (rec >> 24) & 0xff, j1 = (rec >> 32) & 0xff, j2 = (rec >> 40) & 0xff;
-    const int dn = (int)(int8_t)((rec >> 48) & 0xff);
-    const int type = (int)(rec >> 56);
-    const double sumg = (w.g[j0] + w.g[j1] + w.g[j2]) - (w.g[i0] + w.g[i1] + w.g[i2]);
-    const double lnKc = fma(t.nu[dn], lnC0, -sumg);
+  // falloff, phase 1: exp(ln k0 - ln k_inf), e^{-T/T***}, e^{-T/T*}, e^{-T**/T}
+  for (int e = lane; e < 4 * NT; e += 32) {
+    const int tr = e >> 2, kind = e & 3;
+    const int r = t.trx[tr];
+    const double* tp = t.troe + 8 * tr;
     const double lnkinf = fma(t.b[r], lnT, t.lnA[r]) - t.Ta[r] * invT;
-    double kf = exp(lnkinf);
-    double M = 0.0, dlnkf_dT = 0.0, dlnkf_dM = 0.0;
-    if (JAC) dlnkf_dT = fma(t.Ta[r], invT, t.b[r]) * invT;
-    if (type != 0) {
+    const double lnk0 = fma(tp[1], lnT, tp[0]) - tp[2] * invT;
+    const double arg = (kind == 0) ? lnk0 - lnkinf : (kind == 1) ? -T * tp[4] : (kind == 2) ? -T * tp[5] : -tp[6] * invT;
+    w.tro[kTroeSlots * tr + kind] = exp_tab(arg, t.exp2t);
+  }
+  __syncwarp();
+  // falloff, phase 2: [M], Pr = (k0/k_inf) [M], Fc and their log10
+  for (int e = lane; e < 2 * NT; e += 32) {
+    const int tr = e >> 1, kind = e & 1;
+    const int r = t.trx[tr];
+    double* q = w.tro + kTroeSlots * tr;
+    double x;
+    if (kind == 1) {
       const int row = t.rrow[r] & 0xffff;
-      M = Ctot;
-      for (int e = t.eptr[row]; e < t.eptr[row + 1]; ++e) M = fma(t.eval[e], w.C[t.eidx[e]], M);
+      double M = Ctot;
+      for (int j = t.eptr[row]; j < t.eptr[row + 1]; ++j) M = fma(t.eval[j], w.C[t.eidx[j]], M);
+      x = fmax(q[0] * M, 1e-300);
+      q[4] = M;
+      q[5] = x;
+    } else {
+      const double* tp = t.troe + 8 * tr;
+      x = fma(1.0 - tp[3], q[1], fma(tp[3], q[2], q[3]));
+      q[6] = x;
     }
-    if (type == 2) {
-      // Lindemann falloff with Troe broadening: Pr = k0 [M] / k_inf,
-      // k_f = k_inf Pr/(1 + Pr) F, log10 F = log10 Fc / (1 + f1^2),
-      // f1 = (log10 Pr + c) / (n' - 0.14 (log10 Pr + c)), c = -0.4 - 0.67 log10 Fc,
-      // n' = 0.75 - 1.27 log10 Fc, Fc = (1-a) e^{-T/T***} + a e^{-T/T*} + e^{-T**/T}.
-      const double* tp = t.troe + 8 * (t.rrow[r] >> 16);
-      const double lnk0 = fma(tp[1], lnT, tp[0]) - tp[2] * invT;
-      double Pr = exp(lnk0 - lnkinf) * M;
-      Pr = fmax(Pr, 1e-300);
-      const double e3 = exp(-T * tp[4]), e1 = exp(-T * tp[5]), e2 = exp(-tp[6] * invT);
-      const double Fc = fma(1.0 - tp[3], e3, fma(tp[3], e1, e2));
-      const double logFc = log10(Fc);
-      const double c = fma(-0.67, logFc, -0.4);
-      const double nn = fma(-1.27, logFc, 0.75);
-      const double u = log10(Pr) + c;
-      const double den = fma(-0.14, u, nn);
-      const double invden = 1.0 / den;
-      const double f1 = u * invden;
-      const double g1 = fma(f1, f1, 1.0);
-      const double invg = 1.0 / g1;
-      const double logF = logFc * invg;
-      const double invPr1 = 1.0 / (1.0 + Pr);
-      kf = kf * (Pr * invPr1) * exp(logF * kLn10);
-      if (JAC) {
-        const double dlnk0_dT = fma(tp[2], invT, tp[1]) * invT;
-        const double dlnPr_dT = dlnk0_dT - dlnkf_dT;
-        const double dFc_dT = -(1.0 - tp[3]) * tp[4] * e3 - tp[3] * tp[5] * e1 + tp[6] * invT * invT * e2;
-        const double df1_du = nn * invden * invden;
-        const double df1_dnn = -u * invden * invden;
-        const double dlogF_df1 = -logFc * 2.0 * f1 * invg * invg;
-        const double dlogF_dx = dlogF_df1 * df1_du;
-        const double dlogF_dlogFc = invg + dlogF_df1 * (df1_du * -0.67 + df1_dnn * -1.27);
-        // d ln F / dT = ln10 (dlogF/dx dx/dT + dlogF/dlogFc dlogFc/dT), x = log10 Pr
-        const double dlnF_dT = fma(dlogF_dx, dlnPr_dT, dlogF_dlogFc * dFc_dT / Fc);
-        dlnkf_dT = dlnkf_dT + dlnPr_dT * invPr1 + dlnF_dT;
-        dlnkf_dM = (invPr1 + dlogF_dx) / M;
-      }
-    }
-    const double kr = kf * exp(-lnKc);
-    const double fwd = w.C[i0] * w.C[i1] * w.C[i2];
-    const double rev = w.C[j0] * w.C[j1] * w.C[j2];
-    const double base = fma(kf, fwd, -kr * rev);
-    const double wM = (type == 1) ? M : 1.0;
-    w.q[r] = wM * base;
+    q[7 + kind] = log10(x);   // q[7] = log10 Fc, q[8] = log10 Pr
+  }
+  __syncwarp();
+  // falloff, phase 3: broadening F, factor Pr/(1+Pr) F, and its derivatives
+  for (int tr = lane; tr < NT; tr += 32) {
+    double* q = w.tro + kTroeSlots * tr;
+    const double logFc = q[7], Pr = q[5];
+    const double c = fma(-0.67, logFc, -0.4);
+    const double nn = fma(-1.27, logFc, 0.75);
+    const double u = q[8] + c;
+    const double den = fma(-0.14, u, nn);
+    const double invden = 1.0 / den;
+    const double f1 = u * invden;
+    const double g1 = fma(f1, f1, 1.0);
+    const double invg = 1.0 / g1;
+    const double logF = logFc * invg;
+    const double invPr1 = 1.0 / (1.0 + Pr);
+    q[9] = Pr * invPr1 * exp_tab(logF * kLn10, t.exp2t);
     if (JAC) {
-      const double snh = (w.hh[j0] + w.hh[j1] + w.hh[j2]) - (w.hh[i0] + w.hh[i1] + w.hh[i2]);
-      const double dlnKc_dT = (snh - t.nu[dn]) * invT;
-      w.kfw[r] = wM * kf;
-      w.krw[r] = wM * kr;
-      w.dqdT[r] = wM * fma(kf * dlnkf_dT, fwd, -kr * (dlnkf_dT - dlnKc_dT) * rev);
-      w.tbs[r] = (type == 1) ? base : ((type == 2) ? dlnkf_dM * base : 0.0);
+      const int r = t.trx[tr];
+      const double* tp = t.troe + 8 * tr;
+      const double dlnkinf_dT = fma(t.Ta[r], invT, t.b[r]) * invT;
+      const double dlnk0_dT = fma(tp[2], invT, tp[1]) * invT;
+      const double dlnPr_dT = dlnk0_dT - dlnkinf_dT;
+      const double dFc_dT = -(1.0 - tp[3]) * tp[4] * q[1] - tp[3] * tp[5] * q[2] + tp[6] * invT * invT * q[3];
+      const double df1_du = nn * invden * invden;
+      const double df1_dnn = -u * invden * invden;
+      const double dlogF_df1 = -logFc * 2.0 * f1 * invg * invg;
+      const double dlogF_dx = dlogF_df1 * df1_du;
+      const double dlogF_dlogFc = invg + dlogF_df1 * (df1_du * -0.67 + df1_dnn * -1.27);
+      // d ln F / dT = ln10 (dlogF/dx dx/dT + dlogF/dlogFc dlogFc/dT), x = log10 Pr
+      const double dlnF_dT = fma(dlogF_dx, dlnPr_dT, dlogF_dlogFc * dFc_dT / q[6]);
+      q[10] = dlnPr_dT * invPr1 + dlnF_dT;            // added to d ln k_inf / dT
+      q[11] = (invPr1 + dlogF_dx) / q[4];             // d ln k_f / d[M]
+    }
+  }
+  __syncwarp();
+  // two reactions per lane per iteration: independent exponentials interleave
+  for (int r0 = lane; r0 < R; r0 += 64) {
+    const int r1 = (r0 + 32 < R) ? r0 + 32 : r0;
+    RxnOut o0, o1;
+    rxn_eval<JAC>(t, w, r0, lnT, invT, Ctot, o0);
+    rxn_eval<JAC>(t, w, r1, lnT, invT, Ctot, o1);
+    w.q[r0] = o0.q;
+    if (JAC) { w.kfw[r0] = o0.kfw; w.krw[r0] = o0.krw; w.dqdT[r0] = o0.dqdT; w.tbs[r0] = o0.tbs; }
+    if (r1 != r0) {
+      w.q[r1] = o1.q;
+      if (JAC) { w.kfw[r1] = o1.kfw; w.krw[r1] = o1.krw; w.dqdT[r1] = o1.dqdT; w.tbs[r1] = o1.tbs; }
     }
   }
   __syncwarp();
@@ -229,54 +319,85 @@ __device__ __forceinline__ void chem_rhs_out(const Tab& t, const WS& w, const Sc
   __syncwarp();
 }
 
+// Inputs of the Jacobian assembly in the arithmetic type MT: FP64 views of the
+// chem_eval<true> arrays, or FP32 copies of them for the mixed-precision form.
+template <typename MT>
+struct JacIn {
+  const MT *C, *hh, *cp, *wd, *DT, *kfw, *krw, *tbs, *nu, *effd, *W, *invW, *dcp;
+  MT *DC, *aux;
+};
+
+__device__ __forceinline__ JacIn<double> jac_in64(const Tab& t, const WS& w) {
+  return JacIn<double>{w.C, w.hh, w.cp, w.wd, w.DT, w.kfw, w.krw, w.tbs, t.nu, t.effd, t.W, t.invW, t.dcp, w.DC, w.aux};
+}
+
+// FP32 copies of the per-cell Jacobian inputs (mixed-precision form).
+__device__ __forceinline__ JacIn<float> jac_in32(const Tab& t, const WS& w, int lane) {
+  for (int k = lane; k < t.nsv; k += 32) {
+    w.C32[k] = (float)w.C[k]; w.hh32[k] = (float)w.hh[k]; w.cp32[k] = (float)w.cp[k];
+    w.wd32[k] = (float)w.wd[k]; w.DT32[k] = (float)w.DT[k];
+  }
+  for (int r = lane; r < t.R; r += 32) {
+    w.kfw32[r] = (float)w.kfw[r]; w.krw32[r] = (float)w.krw[r]; w.tbs32[r] = (float)w.tbs[r];
+  }
+  __syncwarp();
+  return JacIn<float>{w.C32, w.hh32, w.cp32, w.wd32, w.DT32, w.kfw32, w.krw32, w.tbs32, t.nu32, t.effd32, t.W32,
+                      t.invW32, t.dcp32, w.DC32, w.aux32};
+}
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
 // Analytic Jacobian into the n x n matrix J (leading dimension ld) after
 // chem_eval<true> at the same state Z.  Columns of D = nu dq/dC are owned by lanes
 // (no write conflicts); then the chain rule through C(Y, T) and rho(Y, T).
-__device__ __forceinline__ void chem_jac(const Tab& t, const WS& w, const double* Z, const Scal& s, double* J, int lane) {
-  const int Ns = t.Ns, n = t.n, ld = w.ld, nsv = t.nsv;
+template <typename MT>
+__device__ __forceinline__ void chem_jac(const Tab& t, const WS& w, const double* Z, const Scal& s, MT* J,
+                                         const JacIn<MT>& in, int lane) {
+  const int Ns = t.Ns, ld = w.ld, nsv = t.nsv;
   for (int l = lane; l < Ns; l += 32) {
-    for (int k = 0; k < Ns; ++k) J[k * ld + l] = 0.0;
+    for (int k = 0; k < Ns; ++k) J[k * ld + l] = MT(0);
     for (int e = t.cptr[l]; e < t.cptr[l + 1]; ++e) {
       const uint64_t ce = t.cent[e];
       const int r = ce & 0xffff;
       const int mf = (ce >> 16) & 0xf, mr = (ce >> 20) & 0xf;
       const int o1 = (ce >> 24) & 0xff, o2 = (ce >> 32) & 0xff, o3 = (ce >> 40) & 0xff, o4 = (ce >> 48) & 0xff;
-      const double dq = fma(w.kfw[r] * t.nu[mf], w.C[o1] * w.C[o2], -w.krw[r] * t.nu[mr] * (w.C[o3] * w.C[o4]));
+      const MT dq = fma_t(in.kfw[r] * in.nu[mf], in.C[o1] * in.C[o2], -in.krw[r] * in.nu[mr] * (in.C[o3] * in.C[o4]));
       const uint64_t s0 = t.rsp[2 * r], s1 = t.rsp[2 * r + 1];
       const int cnt = (int)((s0 >> 48) & 0xff);
       for (int j = 0; j < cnt; ++j) {
         const int k = (s0 >> (8 * j)) & 0xff;
         const int nuv = (int)(int8_t)((s1 >> (8 * j)) & 0xff);
-        J[k * ld + l] = fma(t.nu[nuv], dq, J[k * ld + l]);
+        J[k * ld + l] = fma_t(in.nu[nuv], dq, J[k * ld + l]);
       }
     }
     for (int i = 0; i < t.n_tb; ++i) {
       const int r = t.tbl[i];
       const int row = t.rrow[r] & 0xffff;
-      const double sc = t.effd[row * nsv + l] * w.tbs[r];
+      const MT sc = in.effd[row * nsv + l] * in.tbs[r];
       const uint64_t s0 = t.rsp[2 * r], s1 = t.rsp[2 * r + 1];
       const int cnt = (int)((s0 >> 48) & 0xff);
       for (int j = 0; j < cnt; ++j) {
         const int k = (s0 >> (8 * j)) & 0xff;
         const int nuv = (int)(int8_t)((s1 >> (8 * j)) & 0xff);
-        J[k * ld + l] = fma(t.nu[nuv], sc, J[k * ld + l]);
+        J[k * ld + l] = fma_t(in.nu[nuv], sc, J[k * ld + l]);
       }
     }
   }
   __syncwarp();
-  // DC_k = sum_l D_kl C_l ; aux_j = sum_k h/RT_k D_kj
+  // DC_k = sum_l D_kl C_l ; aux_j = sum_k h/RT_k D_kj  (sums in FP64 either way)
   double hq = 0.0, dqt = 0.0, dcpm = 0.0;
   const double T = s.T, invT = s.invT;
   for (int k = lane; k < Ns; k += 32) {
-    double acc = 0.0, col = 0.0;
+    MT acc = MT(0), col = MT(0);
     for (int l = 0; l < Ns; ++l) {
-      acc = fma(J[k * ld + l], w.C[l], acc);
-      col = fma(w.hh[l], J[l * ld + k], col);
+      acc = fma_t(J[k * ld + l], in.C[l], acc);
+      col = fma_t(in.hh[l], J[l * ld + k], col);
     }
-    w.DC[k] = acc;
-    w.aux[k] = col;
-    hq = fma(w.hh[k], acc, hq);
-    dqt += fma((w.cp[k] - w.hh[k]) * invT, w.wd[k], w.hh[k] * fma(-acc, invT, w.DT[k]));
+    in.DC[k] = acc;
+    in.aux[k] = col;
+    hq = fma(w.hh[k], (double)acc, hq);
+    dqt += fma((w.cp[k] - w.hh[k]) * invT, w.wd[k], w.hh[k] * fma(-(double)acc, invT, w.DT[k]));
     const double dcp = fma(fma(fma(t.dcp[3 * nsv + k], T, t.dcp[2 * nsv + k]), T, t.dcp[nsv + k]), T, t.dcp[k]);
     dcpm = fma(Z[k] * t.invW[k], dcp, dcpm);
   }
@@ -285,34 +406,35 @@ __device__ __forceinline__ void chem_jac(const Tab& t, const WS& w, const double
   const double dCPM = warp_sum(dcpm);
   __syncwarp();
   const double invS = 1.0 / s.S;
-  const double inv_rhoS = s.invrho * invS;
+  const MT inv_rhoS = (MT)(s.invrho * invS);
   const double Phi = T * s.invrho;
   const double invcpm = 1.0 / s.cpm;
   const double PQc = Phi * s.Q * invcpm;
   // species rows: J_kj = (W_k / W_j)(D_kj - (DC_k - wdot_k)/(rho S)), J_kT = (W_k/rho)(DT_k - (DC_k - wdot_k)/T)
   for (int e = lane; e < Ns * Ns; e += 32) {
     const int k = e / Ns, j = e - k * Ns;
-    const double a = (w.DC[k] - w.wd[k]) * inv_rhoS;
-    J[k * ld + j] = t.W[k] * t.invW[j] * (J[k * ld + j] - a);
+    const MT a = (in.DC[k] - in.wd[k]) * inv_rhoS;
+    J[k * ld + j] = in.W[k] * in.invW[j] * (J[k * ld + j] - a);
   }
   for (int k = lane; k < Ns; k += 32)
-    J[k * ld + Ns] = t.W[k] * s.invrho * fma(-(w.DC[k] - w.wd[k]), invT, w.DT[k]);
+    J[k * ld + Ns] = (MT)(t.W[k] * s.invrho * fma(-((double)in.DC[k] - w.wd[k]), invT, w.DT[k]));
   // temperature row
   for (int j = lane; j < Ns; j += 32) {
-    const double dQ = s.rho * t.invW[j] * w.aux[j] - invS * t.invW[j] * HQ;
+    const double dQ = s.rho * t.invW[j] * (double)in.aux[j] - invS * t.invW[j] * HQ;
     const double dPhi = Phi * invS * t.invW[j];
-    J[Ns * ld + j] = -(dPhi * s.Q * invcpm + Phi * dQ * invcpm - PQc * w.cp[j] * t.invW[j] * invcpm);
+    J[Ns * ld + j] = (MT)(-(dPhi * s.Q * invcpm + Phi * dQ * invcpm - PQc * w.cp[j] * t.invW[j] * invcpm));
   }
-  if (lane == 0) J[Ns * ld + Ns] = -(2.0 * PQc * invT + Phi * dQT * invcpm - PQc * dCPM * invcpm);
+  if (lane == 0) J[Ns * ld + Ns] = (MT)(-(2.0 * PQc * invT + Phi * dQT * invcpm - PQc * dCPM * invcpm));
   __syncwarp();
-  (void)n;
 }
 
 // M = I - hg J in place.
-__device__ __forceinline__ void form_newton_matrix(double* M, int n, int ld, double hg, int lane) {
+template <typename MT>
+__device__ __forceinline__ void form_newton_matrix(MT* M, int n, int ld, double hg, int lane) {
+  const MT h = (MT)hg;
   for (int e = lane; e < n * n; e += 32) {
     const int i = e / n, j = e - i * n;
-    M[i * ld + j] = ((i == j) ? 1.0 : 0.0) - hg * M[i * ld + j];
+    M[i * ld + j] = ((i == j) ? MT(1) : MT(0)) - h * M[i * ld + j];
   }
   __syncwarp();
 }
@@ -323,13 +445,22 @@ __device__ __forceinline__ void form_newton_matrix(double* M, int n, int ld, dou
 // pivot search compares the magnitudes' IEEE bit patterns as integers, which
 // orders non-negative doubles exactly.  dinv[k] = 1 / U_kk.  Returns 0 or k+1 for
 // a zero or non-finite pivot in column k (the factorisation stops there).
-template <bool SCALED>
-__device__ __forceinline__ int lu_factor_warp(double* A, int n, int ld, int* piv, double* dinv, int lane) {
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float v) {
+  return (unsigned long long)((unsigned)__float_as_int(v) & 0x7fffffffu);
+}
+__device__ __forceinline__ unsigned long long inf_bits(double) { return 0x7ff0000000000000ull; }
+__device__ __forceinline__ unsigned long long inf_bits(float) { return 0x7f800000ull; }
+
+template <bool SCALED, typename MT>
+__device__ __forceinline__ int lu_factor_warp(MT* A, int n, int ld, int* piv, MT* dinv, int lane) {
   for (int k = 0; k < n; ++k) {
     unsigned long long best = 0ull;
     int bi = 0x7fffffff;
     for (int i = k + lane; i < n; i += 32) {
-      const unsigned long long v = (unsigned long long)__double_as_longlong(A[i * ld + k]) & 0x7fffffffffffffffull;
+      const unsigned long long v = abs_bits(A[i * ld + k]);
       if (v > best || (v == best && i < bi)) { best = v; bi = i; }
     }
 #pragma unroll
@@ -338,23 +469,23 @@ __device__ __forceinline__ int lu_factor_warp(double* A, int n, int ld, int* piv
       const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
-    if (best == 0ull || best >= 0x7ff0000000000000ull) return k + 1;
+    if (best == 0ull || best >= inf_bits(MT(0))) return k + 1;
     if (lane == 0) piv[k] = bi;
     if (bi != k)
       for (int j = lane; j < n; j += 32) {
-        const double a = A[k * ld + j];
+        const MT a = A[k * ld + j];
         A[k * ld + j] = A[bi * ld + j];
         A[bi * ld + j] = a;
       }
     __syncwarp();
-    const double inv = 1.0 / A[k * ld + k];
+    const MT inv = MT(1) / A[k * ld + k];
     if (lane == 0) dinv[k] = inv;
     for (int i = k + 1 + lane; i < n; i += 32) A[i * ld + k] *= inv;
     __syncwarp();
     const int m = n - k - 1;
     for (int e = lane; e < m * m; e += 32) {
       const int i = k + 1 + e / m, j = k + 1 + e % m;
-      A[i * ld + j] = fma(-A[i * ld + k], A[k * ld + j], A[i * ld + j]);
+      A[i * ld + j] = fma_t(-A[i * ld + k], A[k * ld + j], A[i * ld + j]);
     }
     __syncwarp();
   }
@@ -372,34 +503,34 @@ __device__ __forceinline__ int lu_factor_warp(double* A, int n, int ld, int* piv
 
 // Solve with the factors of lu_factor_warp<SCALED>; b is overwritten by x.  SCALED
 // factors hold D^-1 U above the diagonal, unscaled ones U (diagonal inverse in dinv).
-template <bool SCALED>
-__device__ __forceinline__ void lu_solve_warp(const double* A, int n, int ld, const int* piv, const double* dinv,
-                                              double* b, int lane) {
+template <bool SCALED, typename MT>
+__device__ __forceinline__ void lu_solve_warp(const MT* A, int n, int ld, const int* piv, const MT* dinv, MT* b,
+                                              int lane) {
   if (lane == 0)
     for (int k = 0; k < n; ++k) {
       const int p = piv[k];
-      if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+      if (p != k) { const MT t = b[k]; b[k] = b[p]; b[p] = t; }
     }
   __syncwarp();
   for (int j = 0; j < n - 1; ++j) {
-    const double xj = b[j];
-    for (int i = j + 1 + lane; i < n; i += 32) b[i] = fma(-A[i * ld + j], xj, b[i]);
+    const MT xj = b[j];
+    for (int i = j + 1 + lane; i < n; i += 32) b[i] = fma_t(-A[i * ld + j], xj, b[i]);
     __syncwarp();
   }
   if (SCALED) {
     for (int i = lane; i < n; i += 32) b[i] *= dinv[i];
     __syncwarp();
     for (int j = n - 1; j > 0; --j) {
-      const double xj = b[j];
-      for (int i = lane; i < j; i += 32) b[i] = fma(-A[i * ld + j], xj, b[i]);
+      const MT xj = b[j];
+      for (int i = lane; i < j; i += 32) b[i] = fma_t(-A[i * ld + j], xj, b[i]);
       __syncwarp();
     }
   } else {
     for (int j = n - 1; j >= 0; --j) {
-      const double xj = b[j] * dinv[j];
+      const MT xj = b[j] * dinv[j];
       __syncwarp();
       if (lane == 0) b[j] = xj;
-      for (int i = lane; i < j; i += 32) b[i] = fma(-A[i * ld + j], xj, b[i]);
+      for (int i = lane; i < j; i += 32) b[i] = fma_t(-A[i * ld + j], xj, b[i]);
       __syncwarp();
     }
   }
@@ -422,7 +553,7 @@ struct StageArgs {
 };
 
 constexpr int kMaxJacAge = 20;
-constexpr double kNewtonSafety = 3e-3;
+constexpr double kNewtonSafety = 3e-4;
 
 __device__ __forceinline__ void substep_geometry(int s, int ramp, double hh, double& tau, double& hk) {
   if (ramp > 0) {
@@ -448,22 +579,52 @@ __device__ __forceinline__ double wrms_update(const double* d, const double* Z, 
   return sqrt(warp_sum(acc) / n);
 }
 
-// Jacobian at Z, M = I - hg J, LU.  Returns the LU info (0 = ok).
+// Jacobian at Z, M = I - hg J, LU.  Returns the LU info (0 = ok).  PREC32: the
+// assembly (from FP64 rates), the matrix and its factors are FP32.
+template <bool PREC32>
 __device__ __forceinline__ int refresh_matrix(const Tab& t, const WS& w, const double* Z, double p, double hg, int lane) {
   Scal s;
   chem_eval<true>(t, w, Z, p, s, lane);
-  chem_jac(t, w, Z, s, w.M, lane);
-  form_newton_matrix(w.M, t.n, w.ld, hg, lane);
-  return lu_factor_warp<true>(w.M, t.n, w.ld, w.piv, w.dinv, lane);
+  if (PREC32) {
+    const JacIn<float> in = jac_in32(t, w, lane);
+    chem_jac<float>(t, w, Z, s, w.M32, in, lane);
+    form_newton_matrix<float>(w.M32, t.n, w.ld, hg, lane);
+    return lu_factor_warp<true, float>(w.M32, t.n, w.ld, w.piv, w.dinv32, lane);
+  }
+  chem_jac<double>(t, w, Z, s, w.M, jac_in64(t, w), lane);
+  form_newton_matrix<double>(w.M, t.n, w.ld, hg, lane);
+  return lu_factor_warp<true, double>(w.M, t.n, w.ld, w.piv, w.dinv, lane);
 }
 
+// Newton correction: d <- M^-1 d.  PREC32: the FP64 residual is rounded to FP32,
+// solved with the FP32 factors and the correction widened back to FP64; the FP64
+// residual of every Newton iteration then refines the stage value to the same
+// tolerance as the FP64 form.
+template <bool PREC32>
+__device__ __forceinline__ void newton_solve(const WS& w, int n, int lane) {
+  if (PREC32) {
+    for (int k = lane; k < n; k += 32) w.d32[k] = (float)w.d[k];
+    __syncwarp();
+    lu_solve_warp<true, float>(w.M32, n, w.ld, w.piv, w.dinv32, w.d32, lane);
+    for (int k = lane; k < n; k += 32) w.d[k] = (double)w.d32[k];
+    __syncwarp();
+  } else {
+    lu_solve_warp<true, double>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane);
+  }
+}
+
+template <bool PREC32>
 __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sA[3][3], sc[3];    // SDIRK tableau, indexed by the runtime stage
   stage_table(smem, a.table, a.L.bytes);
+  if (threadIdx.x < 9) sA[threadIdx.x / 3][threadIdx.x % 3] = a.A[threadIdx.x / 3][threadIdx.x % 3];
+  if (threadIdx.x < 3) sc[threadIdx.x] = a.c[threadIdx.x];
   __syncthreads();
   const Tab t(smem, a.L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const WS w(reinterpret_cast<double*>(smem + a.L.bytes) + (size_t)warp * a.L.ws_doubles, a.L);
+  const WS w(reinterpret_cast<double*>(smem + a.L.bytes) + (size_t)warp * (PREC32 ? a.L.ws_doubles32 : a.L.ws_doubles),
+             a.L, PREC32);
   const int n = t.n, Ns = t.Ns, S = a.nstage;
   const int total_sub = a.n_sub + (a.ramp > 0 ? a.ramp : 0);
   for (int cell = blockIdx.x * nw + warp; cell < a.ncell; cell += gridDim.x * nw) {
@@ -482,6 +643,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
     int nsub = 0, nnewton = 0, njac = 0;
     double M_hg = 0.0;     // h gamma of the factorised Newton matrix (0: none yet)
     int M_age = 0;         // substeps since its Jacobian was evaluated
+    bool have_Fl = false;  // w.Fl holds the last stage derivative of the previous substep
     for (int sidx = 0; sidx < total_sub && status == MRI_CELL_OK; ++sidx) {
       double tau, hk;
       substep_geometry(sidx, a.ramp, a.hh, tau, hk);
@@ -494,24 +656,28 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
       const bool need = (a.jac_policy == MRI_JAC_PER_SUBSTEP) || startup_sub || hg != M_hg ||
                         M_age >= kMaxJacAge;
       if (need) {
-        if (refresh_matrix(t, w, w.y0, p, hg, lane) != 0) { status = MRI_CELL_ENEWTON; break; }
+        if (refresh_matrix<PREC32>(t, w, w.y0, p, hg, lane) != 0) { status = MRI_CELL_ENEWTON; break; }
         njac++;
         M_hg = hg;
         M_age = 0;
       } else {
         M_age++;
       }
-      for (int k = lane; k < n; k += 32) w.Z[k] = w.y0[k];
-      __syncwarp();
       for (int i = 0; i < S && status == MRI_CELL_OK; ++i) {
-        const double rh = (tau + a.c[i] * hk) / a.Hs;
+        const double rh = (tau + sc[i] * hk) / a.Hs;
+        // Newton starts from base + h gamma F_prev, F_prev being the derivative of the
+        // previous stage (of the previous substep for the first stage): the stage
+        // equation with the new derivative replaced by the last one known.
+        const bool predicted = (i > 0) || have_Fl;
+        const double* Fp = (i > 0) ? w.F(i - 1) : w.Fl;
         for (int k = lane; k < n; k += 32) {
           double rv = 0.0;
           for (int j = a.K - 1; j >= 0; --j) rv = fma(rv, rh, w.phi[j * w.nv + k]);
           w.r[k] = rv;
           double bs = w.y0[k];
-          for (int j = 0; j < i; ++j) bs = fma(hk * a.A[i][j], w.F[j][k], bs);
+          for (int j = 0; j < i; ++j) bs = fma(hk * sA[i][j], w.F(j)[k], bs);
           w.base[k] = bs;   // stage base y_n + h sum_j a_ij F_j
+          w.Z[k] = predicted ? fma(hg, Fp[k], bs) : bs;
         }
         __syncwarp();
         // Modified Newton: the matrix of the substep start is reused while it
@@ -521,7 +687,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
         // the residual is reused).  Start-up substeps use full Newton throughout.
         // The converged stage value does not depend on the matrix policy.
         const bool startup = startup_sub;
-        bool fresh = (i == 0) && need;
+        bool fresh = (i == 0) && need && !predicted;   // matrix evaluated at the starting iterate
         bool conv = false;
         double prev = 0.0;
         for (int it = 0; it < a.max_newton; ++it) {
@@ -535,11 +701,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
           }
           __syncwarp();
           if (startup && !fresh) {   // start-up substeps: full Newton, as far from the manifold
-            if (refresh_matrix(t, w, w.Z, p, hg, lane) != 0) break;
+            if (refresh_matrix<PREC32>(t, w, w.Z, p, hg, lane) != 0) break;
             njac++;
             fresh = true;
           }
-          lu_solve_warp<true>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane);
+          newton_solve<PREC32>(w, n, lane);
           double nrm = wrms_update(w.d, w.Z, n, a.rtol, a.atol_Y, a.atol_T, lane);
           // redo with a fresh matrix when the stale one contracts by less than 10x, or
           // when its contraction rate would not reach the tolerance three iterations
@@ -553,12 +719,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
             redo = proj > 1.0;
           }
           if (redo) {
-            if (refresh_matrix(t, w, w.Z, p, hg, lane) != 0) break;
+            if (refresh_matrix<PREC32>(t, w, w.Z, p, hg, lane) != 0) break;
             njac++;
             M_age = 0;
             for (int k = lane; k < n; k += 32) w.d[k] = w.res[k];
             __syncwarp();
-            lu_solve_warp<true>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane);
+            newton_solve<PREC32>(w, n, lane);
             nrm = wrms_update(w.d, w.Z, n, a.rtol, a.atol_Y, a.atol_T, lane);
           }
           for (int k = lane; k < n; k += 32) w.Z[k] += w.d[k];
@@ -578,14 +744,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
           prev = nrm;
         }
         if (!conv) { status = MRI_CELL_ENEWTON; break; }
-        if (i < S - 1) {
-          for (int k = lane; k < n; k += 32) w.F[i][k] = (w.Z[k] - w.base[k]) * inv_hg;
-          __syncwarp();
-        }
+        double* Fi = (i < S - 1) ? w.F(i) : w.Fl;
+        for (int k = lane; k < n; k += 32) Fi[k] = (w.Z[k] - w.base[k]) * inv_hg;
+        __syncwarp();
       }
       if (status != MRI_CELL_OK) break;
       for (int k = lane; k < n; k += 32) w.y0[k] = w.Z[k];
       __syncwarp();
+      have_Fl = true;
       nsub++;
     }
     if (status != MRI_CELL_EINPUT)
@@ -611,7 +777,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rhs_kernel(const double* y, co
   __syncthreads();
   const Tab t(smem, L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const WS w(reinterpret_cast<double*>(smem + L.bytes) + (size_t)warp * L.ws_doubles, L);
+  const WS w(reinterpret_cast<double*>(smem + L.bytes) + (size_t)warp * L.ws_doubles, L, false);
   for (int cell = blockIdx.x * nw + warp; cell < ncell; cell += gridDim.x * nw) {
     for (int k = lane; k < t.n; k += 32) w.Z[k] = y[(size_t)cell * t.n + k];
     __syncwarp();
@@ -630,14 +796,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) jac_kernel(const double* y, co
   __syncthreads();
   const Tab t(smem, L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const WS w(reinterpret_cast<double*>(smem + L.bytes) + (size_t)warp * L.ws_doubles, L);
+  const WS w(reinterpret_cast<double*>(smem + L.bytes) + (size_t)warp * L.ws_doubles, L, false);
   const int n = t.n;
   for (int cell = blockIdx.x * nw + warp; cell < ncell; cell += gridDim.x * nw) {
     for (int k = lane; k < n; k += 32) w.Z[k] = y[(size_t)cell * n + k];
     __syncwarp();
     Scal s;
     chem_eval<true>(t, w, w.Z, p[cell], s, lane);
-    chem_jac(t, w, w.Z, s, w.M, lane);
+    chem_jac<double>(t, w, w.Z, s, w.M, jac_in64(t, w), lane);
     for (int e = lane; e < n * n; e += 32) J[(size_t)cell * n * n + e] = w.M[(e / n) * w.ld + e % n];
     __syncwarp();
   }
@@ -655,8 +821,8 @@ __global__ void lu_kernel(double* A, double* b, int n, int ld, int nbatch, int32
     for (int e = lane; e < n * n; e += 32) Ms[(e / n) * ld + e % n] = A[(size_t)sys * n * n + e];
     for (int k = lane; k < n; k += 32) bs[k] = b[(size_t)sys * n + k];
     __syncwarp();
-    const int rc = lu_factor_warp<false>(Ms, n, ld, pv, dv, lane);
-    if (rc == 0) lu_solve_warp<false>(Ms, n, ld, pv, dv, bs, lane);
+    const int rc = lu_factor_warp<false, double>(Ms, n, ld, pv, dv, lane);
+    if (rc == 0) lu_solve_warp<false, double>(Ms, n, ld, pv, dv, bs, lane);
     for (int e = lane; e < n * n; e += 32) A[(size_t)sys * n * n + e] = Ms[(e / n) * ld + e % n];
     for (int k = lane; k < n; k += 32) b[(size_t)sys * n + k] = bs[k];
     if (lane == 0 && info) info[sys] = rc;
@@ -681,9 +847,9 @@ int device_smem_limit() {
 }
 
 // Warps per CTA and grid for a warp-per-cell kernel with `per_warp` bytes of workspace.
-static bool plan_launch(const Layout& L, int ncell, int& warps, int& blocks, size_t& smem) {
+static bool plan_launch(const Layout& L, int ncell, int& warps, int& blocks, size_t& smem, bool prec32 = false) {
   const int limit = device_smem_limit();
-  const size_t per_warp = (size_t)L.ws_doubles * 8;
+  const size_t per_warp = (size_t)(prec32 ? L.ws_doubles32 : L.ws_doubles) * 8;
   int wmax = (int)((limit - L.bytes) / (long long)per_warp);
   if (wmax < 1) return false;
   if (wmax > kMaxWarps) wmax = kMaxWarps;
@@ -745,12 +911,21 @@ int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, 
   a.jac_policy = o.jac_policy;
   a.rtol = o.newton_rtol; a.atol_Y = o.newton_atol_Y; a.atol_T = o.newton_atol_T;
   sdirk_table(o.method, a);
+  const bool prec32 = (o.precision == MRI_PREC_FP32_LU);
   int warps, blocks;
   size_t smem;
-  if (!plan_launch(m.L, ncell, warps, blocks, smem)) return MRI_EINVAL;
-  if (cudaFuncSetAttribute(stage_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return MRI_ECUDA;
-  stage_fast_kernel<<<blocks, warps * 32, smem, st>>>(a);
+  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32)) return MRI_EINVAL;
+  if (prec32) {
+    if (cudaFuncSetAttribute(stage_fast_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return MRI_ECUDA;
+    stage_fast_kernel<true><<<blocks, warps * 32, smem, st>>>(a);
+  } else {
+    if (cudaFuncSetAttribute(stage_fast_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return MRI_ECUDA;
+    stage_fast_kernel<false><<<blocks, warps * 32, smem, st>>>(a);
+  }
   return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
 }
 
@@ -765,7 +940,7 @@ bool fast_opts_ok(const mri_fast_opts* o) {
          std::isfinite(o->newton_rtol) && o->newton_atol_Y >= 0 && o->newton_atol_T >= 0 &&
          std::isfinite(o->newton_atol_Y) && std::isfinite(o->newton_atol_T) && o->max_newton >= 1 &&
          o->max_newton <= 100 && (o->jac_policy == MRI_JAC_PER_SUBSTEP || o->jac_policy == MRI_JAC_LAZY) &&
-         o->precision == MRI_PREC_FP64 &&
+         (o->precision == MRI_PREC_FP64 || o->precision == MRI_PREC_FP32_LU) &&
          o->ramp >= 0 && o->ramp <= 40;
 }
 

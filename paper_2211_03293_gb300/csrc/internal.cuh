@@ -15,6 +15,7 @@ constexpr int kMaxSpecies = 127;
 constexpr int kMaxReactions = 1023;
 constexpr int kMaxK = 4;                     // forcing polynomial terms
 constexpr int kMaxWarps = 16;                // warps (cells in flight) per CTA
+constexpr int kTroeSlots = 12;               // per-cell doubles of one falloff reaction's intermediates
 
 // Byte offsets of the sections of the mechanism table.  The table is one
 // contiguous device buffer that every CTA copies into shared memory.  Species
@@ -43,12 +44,20 @@ struct Layout {
   int o_cent;             // uint64 [nc]: r (16) | mult_f (4) | mult_r (4) | o1..o4 (8 bits each)
   int o_rsp;              // uint64 [rv][2]: word 0 species k0..k5 + count; word 1 int8 nu0..nu5
   int o_tbl;              // int32 [n_tb]: reactions with an efficiency row (third body or falloff)
+  int o_trx;              // int32 [n_troe]: reaction index of each falloff row
+  int o_exp2;             // double [32]: 2^(j/32), the table of the exponential (fastmath.cuh)
   int o_nu;               // double [8]: the small integers -3..4 as doubles (index v + 3), so kernels
                           // turn stoichiometric integers into doubles with a load, not a conversion
+  // FP32 copies of the constants the mixed-precision Jacobian reads
+  int o_nu32;             // float [8]
+  int o_effd32;           // float [n_eff][nsv]
+  int o_W32, o_invW32;    // float [nsv]
+  int o_dcp32;            // float [4][nsv]
   int bytes;              // total, multiple of 16
   // per-cell workspace (doubles) inside shared memory
   int ld;                 // leading dimension of the n x n matrix (odd)
-  int ws_doubles;         // doubles per cell (warp)
+  int ws_doubles;         // doubles per cell (warp), FP64 form
+  int ws_doubles32;       // doubles per cell (warp), mixed-precision form
 };
 
 struct Mech {             // what mri_mech points at
@@ -57,26 +66,56 @@ struct Mech {             // what mri_mech points at
   int device = -1;
 };
 
-// Per-cell workspace carve-up (double offsets inside the warp's region).
+// Per-cell workspace carve-up (double offsets inside the warp's region).  With
+// prec32 (the mixed-precision form) the Newton matrix and its factors are FP32 and a
+// float region holds FP32 copies of the Jacobian inputs.
 struct WsOffsets {
-  int M, y0, Z, d, res, F0, F1, r, f, base, phi, C, g, hh, cp, wd, DT, DC, aux, dinv, piv;
+  int M, y0, Z, d, res, F0, F1, Fl, r, f, base, phi, C, g, hh, cp, wd, DT, DC, aux, dinv, piv;
   int q, kfw, krw, dqdT, tbs;
+  int E, Einv, c0p, tro;
+  int f32;     // start of the float region (prec32 only), in doubles
   int total;
 };
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-__host__ __device__ inline WsOffsets ws_offsets(const Layout& L) {
+// float offsets inside the f32 region
+struct F32Offsets {
+  int C, hh, cp, wd, DT, DC, aux, kfw, krw, tbs, d, dinv, total;
+};
+
+__host__ __device__ inline F32Offsets f32_offsets(const Layout& L) {
+  F32Offsets f;
+  const int nv = round_up(L.n + 1, 4), ns = round_up(L.nsv, 4), rv = round_up(L.rv, 4);
+  int o = 0;
+  f.C = o; o += ns;
+  f.hh = o; o += ns;
+  f.cp = o; o += ns;
+  f.wd = o; o += ns;
+  f.DT = o; o += ns;
+  f.DC = o; o += ns;
+  f.aux = o; o += ns;
+  f.kfw = o; o += rv;
+  f.krw = o; o += rv;
+  f.tbs = o; o += rv;
+  f.d = o; o += nv;
+  f.dinv = o; o += nv;
+  f.total = round_up(o, 4);
+  return f;
+}
+
+__host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = false) {
   WsOffsets w;
   int nv = round_up(L.n + 1, 2);
   int o = 0;
-  w.M = o; o += round_up(L.n * L.ld, 2);
+  w.M = o; o += prec32 ? round_up(L.n * L.ld, 4) / 2 : round_up(L.n * L.ld, 2);
   w.y0 = o; o += nv;
   w.Z = o; o += nv;
   w.d = o; o += nv;
   w.res = o; o += nv;
   w.F0 = o; o += nv;
   w.F1 = o; o += nv;
+  w.Fl = o; o += nv;
   w.r = o; o += nv;
   w.f = o; o += nv;
   w.base = o; o += nv;
@@ -97,6 +136,13 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L) {
   w.krw = o; o += L.rv;
   w.dqdT = o; o += L.rv;
   w.tbs = o; o += L.rv;
+  w.E = o; o += L.nsv;
+  w.Einv = o; o += L.nsv;
+  w.c0p = o; o += 8;
+  w.tro = o; o += kTroeSlots * (L.n_troe > 0 ? L.n_troe : 1);
+  o = round_up(o, 2);
+  w.f32 = o;
+  if (prec32) o += f32_offsets(L).total / 2;
   w.total = round_up(o, 2);
   return w;
 }

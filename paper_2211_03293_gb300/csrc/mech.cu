@@ -221,7 +221,14 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
     if (B.rtype[r] != 0) tbl.push_back(r);
   L.n_tb = (int)tbl.size();
   L.o_tbl = S.add((tbl.size() + 1) * 4);
+  L.o_trx = S.add((size_t)(B.n_troe > 0 ? B.n_troe : 1) * 4);
+  L.o_exp2 = S.add(32 * 8);
   L.o_nu = S.add(8 * 8);
+  L.o_nu32 = S.add(8 * 4);
+  L.o_effd32 = S.add((size_t)(B.n_eff > 0 ? B.n_eff : 1) * nsv * 4);
+  L.o_W32 = S.add(nsv * 4);
+  L.o_invW32 = S.add(nsv * 4);
+  L.o_dcp32 = S.add(4 * nsv * 4);
   L.bytes = (int)((S.buf.size() + 15) & ~size_t(15));
   S.buf.resize(L.bytes, 0);
 
@@ -325,11 +332,26 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
   cptr[Ns] = pos;
   int32_t* tb = S.at<int32_t>(L.o_tbl);
   for (size_t i = 0; i < tbl.size(); ++i) tb[i] = tbl[i];
+  int32_t* trx = S.at<int32_t>(L.o_trx);
+  for (int r = 0; r < R; ++r)
+    if (B.rtype[r] == 2) trx[B.troe_row[r]] = r;
+  double* e2 = S.at<double>(L.o_exp2);
+  for (int j = 0; j < 32; ++j) e2[j] = (double)std::exp2l((long double)j / 32.0L);
   double* nu = S.at<double>(L.o_nu);
   for (int i = 0; i < 8; ++i) nu[i] = (double)(i - 3);
+  float* nu32 = S.at<float>(L.o_nu32);
+  for (int i = 0; i < 8; ++i) nu32[i] = (float)(i - 3);
+  float* effd32 = S.at<float>(L.o_effd32);
+  for (int e = 0; e < B.n_eff * nsv; ++e) effd32[e] = (float)effd[e];
+  float* W32 = S.at<float>(L.o_W32);
+  float* invW32 = S.at<float>(L.o_invW32);
+  float* dcp32 = S.at<float>(L.o_dcp32);
+  for (int k = 0; k < nsv; ++k) { W32[k] = (float)W[k]; invW32[k] = (float)invW[k]; }
+  for (int e = 0; e < 4 * nsv; ++e) dcp32[e] = (float)dcp[e];
 
   L.ld = (L.n % 2 == 1) ? L.n : L.n + 1;   // odd stride: column walks hit distinct banks
-  L.ws_doubles = ws_offsets(L).total;
+  L.ws_doubles = ws_offsets(L, false).total;
+  L.ws_doubles32 = ws_offsets(L, true).total;
   out.swap(S.buf);
   return MRI_OK;
 }

@@ -1,0 +1,75 @@
+// Measurement utility: the FP64 FMA issue rate of the device, the denominator of
+// the fast path's ALU roofline.  Not part of the method.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "../../include/mri_probe.h"
+#include "fastmath.cuh"
+
+namespace {
+
+// Eight independent FMA chains per thread keep the FP64 pipe fed; the result is
+// stored so the chains are not removed.
+__global__ void dfma_chains(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+  double x4 = x0 + 4.0, x5 = x0 + 5.0, x6 = x0 + 6.0, x7 = x0 + 7.0;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+struct Exp2Table {
+  double v[32];
+};
+
+__global__ void exp_probe_kernel(const double* x, double* y, long long n, Exp2Table tab) {
+  __shared__ double s[32];
+  if (threadIdx.x < 32) s[threadIdx.x] = tab.v[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = mri::exp_tab(x[i], s);
+}
+
+}  // namespace
+
+extern "C" int mri_probe_exp(const double* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return -1;
+  if (n == 0) return 0;
+  Exp2Table tab;
+  for (int j = 0; j < 32; ++j) tab.v[j] = (double)std::exp2l((long double)j / 32.0L);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  exp_probe_kernel<<<(int)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n, tab);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+extern "C" int mri_probe_fp64_fma(double* scratch, long long scratch_doubles, int iters, double* fma_per_s,
+                                  void* stream) {
+  if (!scratch || !fma_per_s || iters < 1) return -1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess)
+    return -3;
+  const int threads = 256, blocks = sms * 8;
+  if ((long long)threads * blocks > scratch_doubles) return -1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -3;
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, st);
+    dfma_chains<<<blocks, threads, 0, st>>>(scratch, iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return -3; }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *fma_per_s = (double)threads * blocks * (double)iters * 8.0 / (best * 1e-3);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}

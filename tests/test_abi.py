@@ -19,7 +19,7 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "mri.h")).read()
+    src = open(os.path.join(ROOT, "include", "mri.h")).read() + open(os.path.join(ROOT, "include", "mri_probe.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(mri_[a-z0-9_]+)\s*\(", src)))
 

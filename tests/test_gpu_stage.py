@@ -31,11 +31,11 @@ def sample(w, n, seed):
     return w.y0[idx], w.p[idx]
 
 
-@pytest.mark.parametrize("K,ramp", [(1, 10), (0, 10), (3, 10)])
-def test_stage_parity_line64(mri, orc, K, ramp):
+@pytest.mark.parametrize("K,ramp,prec", [(1, 10, 0), (0, 10, 0), (3, 10, 0), (1, 10, 1)])
+def test_stage_parity_line64(mri, orc, K, ramp, prec):
     w = mechgen.workload("line64")
     phi = mechgen.random_forcing(5, 64, w.mech.n, K) if K else None
-    opts = mri.mri_fast_opts_default(method=2, ramp=ramp)
+    opts = mri.mri_fast_opts_default(method=2, ramp=ramp, precision=prec)
     got, st, ss, nf = run_gpu(mri, w.mech.to_blob(), w.y0, w.p, phi, w.H / 3, w.h, opts)
     ref, rst, rss = orc.Mech(w.mech).stage_fast(w.y0, w.p, phi, w.H / 3, w.h, orc.opts(method=2, ramp=ramp))
     assert np.all(st == 0) and np.all(rst == 0) and nf == 0
@@ -43,12 +43,12 @@ def test_stage_parity_line64(mri, orc, K, ramp):
     assert_parity(got, ref, what="line64 stage")
 
 
-@pytest.mark.parametrize("K,jac", [(0, 0), (2, 0), (2, 1)])
-def test_stage_parity_box32_sample(mri, orc, K, jac):
+@pytest.mark.parametrize("K,jac,prec", [(0, 0, 0), (2, 0, 0), (2, 1, 0), (2, 1, 1), (0, 0, 1)])
+def test_stage_parity_box32_sample(mri, orc, K, jac, prec):
     w = mechgen.workload("box32")
     y, p = sample(w, 301, 3)
     phi = mechgen.random_forcing(6, y.shape[0], w.mech.n, K) if K else None
-    opts = mri.mri_fast_opts_default(method=3, ramp=w.ramp, jac_policy=jac)
+    opts = mri.mri_fast_opts_default(method=3, ramp=w.ramp, jac_policy=jac, precision=prec)
     got, st, ss, nf = run_gpu(mri, w.mech.to_blob(), y, p, phi, w.H / 3, w.h, opts)
     ref, rst, _ = orc.Mech(w.mech).stage_fast(y, p, phi, w.H / 3, w.h, orc.opts(method=3, ramp=w.ramp))
     assert np.all(rst == 0)
@@ -57,8 +57,8 @@ def test_stage_parity_box32_sample(mri, orc, K, jac):
     assert_parity(got, ref, what="box32 stage")
 
 
-@pytest.mark.parametrize("jac", [0, 1])
-def test_stage_parity_relaxed_state_box32(mri, orc, jac):
+@pytest.mark.parametrize("jac,prec", [(0, 0), (1, 0), (1, 1)])
+def test_stage_parity_relaxed_state_box32(mri, orc, jac, prec):
     """After the start-up transient (no ramp, the usual Newton count per stage)."""
     w = mechgen.workload("box32")
     y, p = sample(w, 96, 4)
@@ -66,7 +66,7 @@ def test_stage_parity_relaxed_state_box32(mri, orc, jac):
     y1, rst, _ = om.stage_fast(y, p, None, w.H / 3, w.h, orc.opts(method=3, ramp=w.ramp))
     assert np.all(rst == 0)
     phi = mechgen.random_forcing(8, y.shape[0], w.mech.n, 1)
-    opts = mri.mri_fast_opts_default(method=3, jac_policy=jac)
+    opts = mri.mri_fast_opts_default(method=3, jac_policy=jac, precision=prec)
     got, st, ss, _ = run_gpu(mri, w.mech.to_blob(), y1, p, phi, w.H * 5 / 12, w.h, opts)
     ref, rst, _ = om.stage_fast(y1, p, phi, w.H * 5 / 12, w.h, orc.opts(method=3))
     assert np.all(st == 0) and np.all(rst == 0)

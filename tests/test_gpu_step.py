@@ -54,10 +54,12 @@ def test_mri_step_parity_line64_ten_steps(mri, orc):
     assert_parity(got, ref, what="line64 10 steps")
 
 
-def test_mri_step_parity_box8(mri, orc):
-    """The 40-species box workload at 8^3 cells (ragged against CTA sizes), 2 steps."""
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mri_step_parity_box8(mri, orc, prec):
+    """The 40-species box workload at 8^3 cells (ragged against CTA sizes), 2 steps;
+    FP64 form and mixed-precision form (FP32 Jacobian / LU, FP64 residual)."""
     w = mechgen.workload("box32", cells_per_side=8)
-    kw = dict(method=3, ramp=w.ramp, jac_policy=1)
+    kw = dict(method=3, ramp=w.ramp, jac_policy=1, precision=prec)
     got, st, _, nf = gpu_steps(mri, w, 2, kw)
     ref = oracle_steps(orc, w, 2, dict(method=3, ramp=w.ramp))
     assert np.all(st == 0) and nf == 0

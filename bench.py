@@ -10,7 +10,10 @@ three stage forcings, three fast stages) through the C ABI.
 
 Metric: fast-chemistry cell-steps per second, a cell-step being one SDIRK
 substep of one cell (all its stages and Newton iterations), counted from the
-kernels' own per-cell counters.
+kernels' own per-cell counters.  Two forms are timed: the plain FP64 path and
+the mixed-precision path (FP32 Newton matrix / LU, FP64 rates and residual).
+Each form is gated against the CPU oracle (sampled cells of a full-size stage,
+relative error <= 1e-6); the headline is the fastest form that passes.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch one process per GPU with torch.distributed.run; every rank
@@ -34,25 +37,27 @@ sys.path.insert(0, ROOT)
 METRIC = "fast-chem cell-steps/s per MRI slow step, plain FP64 vs tuned, at rel err ≤1e-6"
 UNIT = "cell-steps/s"
 WORKLOAD = "box32"
-# FP64 roofline: the FMA pipe issues 2 DFMA per clock per SM on GB300 (measured, see the
-# alu_fp64 profile), 152 SMs, 2 flops per FMA; at the maximum SM clock of 2070 MHz this is
-# the figure below.  The bench also measures the rate live (mri_probe_fp64_fma) and uses
-# that measurement as the peak.
+GATE_TOL = 1e-6
+# FP64 roofline: the FMA pipe issues 2 DFMA per clock per SM on GB300 (measured), 152 SMs,
+# 2 flops per FMA; at the maximum SM clock of 2070 MHz this is the figure below.  The bench
+# measures the rate live (mri_probe_fp64_fma) and uses that measurement as the peak.
 FP64_DFMA_PER_CLK_SM = 2.0
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS_NOMINAL = FP64_DFMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ * 1e6 / 1e12
 # nominal cost of one exp or log in the algorithmic flop count
 FLOPS_PER_TRANSCENDENTAL = 20.0
+FORMS = {0: "plain FP64", 1: "mixed: FP32 Newton matrix and LU, FP64 rates, residual and update"}
 
 
 # ----------------------------------------------------------------------------- flop model
 
 def flop_model(mech):
-    """Algorithmic FP64 flops of the pieces of one fast substep for a mechanism:
-    (f^F evaluation, Jacobian assembly + Newton matrix, LU factorisation, one
-    Newton solve + update).  Counted from the mechanism's structure; exp/log at
-    FLOPS_PER_TRANSCENDENTAL each."""
+    """Algorithmic flops of the pieces of one fast substep for a mechanism:
+    f^F evaluation (rates), the FP64 extras of a Jacobian evaluation (rate
+    derivatives), the Jacobian assembly proper, LU, and one Newton solve; plus the
+    FP64 vector work of a Newton iteration (residual, update, norm).  Counted from
+    the mechanism's structure; exp/log at FLOPS_PER_TRANSCENDENTAL each."""
     E = FLOPS_PER_TRANSCENDENTAL
     Ns, R = mech.n_species, mech.n_reactions
     n = Ns + 1
@@ -60,7 +65,6 @@ def flop_model(mech):
     nprod = (mech.prod >= 0).sum(1)
     ntroe = int((mech.rtype == 2).sum())
     ntb = int((mech.rtype != 0).sum())
-    # net stoichiometric incidences (species appearing with nu != 0)
     inc = 0
     col = 0
     for r in range(R):
@@ -84,21 +88,26 @@ def flop_model(mech):
              + ntroe * (7 * E + 40)           # falloff
              + 2 * inc                        # production rates
              + 4 * Ns + 10)                   # f
-    jac = (rates + R * 12 + ntroe * 40         # rate derivatives
-           + col * 8 + 2 * inc * 3             # dq/dC and nu scatter
-           + 2 * ntb * Ns * 3                  # third-body columns
-           + 4 * Ns * Ns + 10 * Ns             # DC, column sums, chain rule
-           + 2 * n * n)                        # M = I - hg J
+    jac_fp64 = R * 12 + ntroe * 40 + 2 * inc   # rate derivatives and sum nu dq/dT
+    jac_asm = (col * 8 + 2 * inc * 3           # dq/dC and nu scatter
+               + 2 * ntb * Ns * 3              # third-body columns
+               + 4 * Ns * Ns + 10 * Ns         # DC, column sums, chain rule
+               + 2 * n * n)                    # M = I - hg J
     lu = (2.0 / 3.0) * n ** 3 + n
-    solve = 2 * n * n + 8 * n
-    return dict(rates=rates, jac=jac, lu=lu, solve=solve, n=n)
+    solve = 2 * n * n
+    vec = 8 * n                                # residual, update, WRMS norm
+    return dict(rates=rates, jac_fp64=jac_fp64, jac_asm=jac_asm, lu=lu, solve=solve, vec=vec, n=n)
 
 
-def algorithmic_flops(fm, substeps, newton, njac):
-    """Flops of a batch of substeps from the per-cell counters: every Newton
-    iteration costs one f^F evaluation and one solve; every Jacobian evaluation
-    costs an assembly and a factorisation."""
-    return newton * (fm["rates"] + fm["solve"]) + njac * (fm["jac"] + fm["lu"])
+def algorithmic_flops(fm, newton, njac, prec):
+    """(FP64 flops, FP32 flops) of a batch of substeps from the per-cell counters:
+    every Newton iteration costs an f^F evaluation, a solve and the vector work;
+    every Jacobian evaluation costs an f^F evaluation with derivatives, the
+    assembly and a factorisation.  The mixed form runs assembly, LU and solves in
+    FP32."""
+    fp64 = newton * (fm["rates"] + fm["vec"]) + njac * (fm["rates"] + fm["jac_fp64"])
+    mat = newton * fm["solve"] + njac * (fm["jac_asm"] + fm["lu"])
+    return (fp64 + mat, 0.0) if prec == 0 else (fp64, mat)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -157,128 +166,150 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def gpu_arm(args, rank, world):
-    import torch
+class Bench:
+    def __init__(self, args, world):
+        import torch
 
-    import mechgen
-    import paper_2211_03293_gb300 as mri
+        import mechgen
+        import paper_2211_03293_gb300 as mri
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    w = mechgen.workload(WORKLOAD, seed=0, cells_per_side=args.cells_per_side)
-    g = w.grid
-    ncell = w.y0.shape[0]
-    n = w.mech.n
-    mech = mri.mri_mech_load(w.mech.to_blob())
-    grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
-    c, G = mri.mri_method_coupling(mri.MRI_KW3)
-    stream = torch.cuda.Stream(device=dev)
-    y = torch.tensor(w.y0, device=dev)
-    p = torch.tensor(w.p, device=dev)
-    fS = torch.empty((3, ncell, n), dtype=torch.float64, device=dev)
-    phi = torch.empty((ncell, 1, n), dtype=torch.float64, device=dev)
-    stats = torch.zeros((ncell, 4), dtype=torch.int32, device=dev)
-    status = torch.zeros(ncell, dtype=torch.int32, device=dev)
-    nfail = torch.zeros(1, dtype=torch.int32, device=dev)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)    # 256 MB > 129 MB L2
-    probe = torch.empty(N_SM * 8 * 256 * 4, dtype=torch.float64, device=dev)
-    fp64_peak_tflops = 2.0 * mri.mri_probe_fp64_fma(probe, iters=4096) / 1e12
-    H, h = w.H, w.h
-    base_opts = mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, jac_policy=args.jac,
-                                          precision=args.prec)
-    ramp_opts = mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, ramp=w.ramp,
-                                          jac_policy=args.jac, precision=args.prec)
-
-    def mri_step_timed(first, ev_stage):
-        """One MRI slow step through the ABI; CUDA events around each fast stage."""
-        for i in range(1, 4):
-            mri.mri_slow_rhs(y, fS[i - 1], grid, stream=stream)
-            mri.mri_stage_forcing(fS, i, G[i], phi, stream=stream)
-            o = ramp_opts if (first and i == 1) else base_opts
-            if ev_stage is not None:
-                ev_stage[i - 1][0].record(stream)
-            mri.mri_stage_fast(y, p, phi, 0.0, (c[i] - c[i - 1]) * H, h, mech, o, cell_status=status,
-                               cell_stats=stats, n_failed=nfail, stream=stream)
-            if ev_stage is not None:
-                ev_stage[i - 1][1].record(stream)
-
-    with torch.cuda.stream(stream):
-        for s in range(args.warmup):
-            mri_step_timed(s == 0, None)
-        stream.synchronize()
-        warm_fail = int(nfail.item())
-        stats.zero_()
-        y_start = y.clone()          # the e2e leg replays the timed steps from this state
-        kernel_launches_per_step = 9
-        step_events = []
-        stage_events = []
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
+        self.mri, self.torch, self.args, self.world = mri, torch, args, world
+        self.dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        torch.cuda.set_device(self.dev)
+        self.w = w = mechgen.workload(WORKLOAD, seed=0, cells_per_side=args.cells_per_side)
+        g = w.grid
+        self.ncell = w.y0.shape[0]
+        self.n = w.mech.n
+        self.mech = mri.mri_mech_load(w.mech.to_blob())
+        self.grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
+        self.c, self.G = mri.mri_method_coupling(mri.MRI_KW3)
+        self.stream = torch.cuda.Stream(device=self.dev)
+        dev = self.dev
+        self.p = torch.tensor(w.p, device=dev)
+        self.fS = torch.empty((3, self.ncell, self.n), dtype=torch.float64, device=dev)
+        self.phi = torch.empty((self.ncell, 1, self.n), dtype=torch.float64, device=dev)
+        self.stats = torch.zeros((self.ncell, 4), dtype=torch.int32, device=dev)
+        self.status = torch.zeros(self.ncell, dtype=torch.int32, device=dev)
+        self.nfail = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)    # 256 MB > 129 MB L2
+        probe = torch.empty(N_SM * 8 * 256 * 4, dtype=torch.float64, device=dev)
+        self.fp64_peak_tflops = 2.0 * mri.mri_probe_fp64_fma(probe, iters=4096) / 1e12
         try:
-            gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+            self.gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
         except Exception:
-            gpu_id = str(dev.index)
-        sampler = ClockSampler(gpu_id)
-        sampler.start()
-        for s in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-            e0.record(stream)
-            mri_step_timed(args.warmup == 0 and s == 0, ev)
-            e1.record(stream)
-            step_events.append((e0, e1))
-            stage_events.append(ev)
-        torch.cuda.synchronize()
-        clocks = sampler.stop()
-        if world > 1:
-            torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in step_events]
-    stage_ms = [[a.elapsed_time(b) for a, b in ev] for ev in stage_events]
-    st = stats.cpu().numpy().astype(np.int64)
-    substeps = int(st[:, 0].sum())
-    newton = int(st[:, 1].sum())
-    njac = int(st[:, 2].sum())
-    failed = int(nfail.item()) - warm_fail
-    total_ms = float(sum(step_ms))
+            self.gpu_id = str(dev.index)
 
-    # end to end through the public C-ABI call with host buffers: the same K steps from
-    # the same state, each step copying the state in from pinned host memory and the
-    # result back
-    y_host = torch.empty((ncell, n), dtype=torch.float64, pin_memory=True)
-    y_host.copy_(y_start.cpu())
-    p_host = torch.empty(ncell, dtype=torch.float64, pin_memory=True)
-    p_host.copy_(p.cpu())
-    ws = torch.empty(mri.mri_step_workspace_size(grid, n) // 8, dtype=torch.float64, device=dev)
-    e2e_stats = torch.zeros((ncell, 4), dtype=torch.int32, device=dev)
-    e2e_ms = []
-    with torch.cuda.stream(stream):
-        for s in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            y.copy_(y_host, non_blocking=True)
-            p.copy_(p_host, non_blocking=True)
-            mri.mri_step(y, p, grid, s * H, H, h, mech, base_opts, ws, cell_stats=e2e_stats, stream=stream)
-            y_host.copy_(y, non_blocking=True)
-            e1.record(stream)
-            e1.synchronize()
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e_sub = int(e2e_stats[:, 0].sum().item())
+    def opts(self, prec, ramp=0):
+        w = self.w
+        return self.mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, ramp=ramp,
+                                              jac_policy=self.args.jac, precision=prec)
 
-    fm = flop_model(w.mech)
-    flops_all = algorithmic_flops(fm, substeps, newton, njac)
-    stage_total_ms = float(np.sum(stage_ms))
-    launches = 3 * args.steps
-    res = dict(total_ms=total_ms, substeps=substeps, newton=newton, njac=njac, failed=failed, clocks=clocks,
-               step_ms=step_ms, stage_total_ms=stage_total_ms, stage_launches=launches, flops=flops_all,
-               e2e_ms=float(sum(e2e_ms)), e2e_substeps=e2e_sub, ncell=ncell, n=n,
-               launches=kernel_launches_per_step * args.steps, h2d=(ncell * n + ncell) * 8, d2h=ncell * n * 8,
-               workload=w, fp64_peak_tflops=fp64_peak_tflops)
-    return res
+    def step(self, y, prec, first, ev_stage):
+        """One MRI slow step through the ABI; CUDA events around each fast stage."""
+        mri, c, G, w = self.mri, self.c, self.G, self.w
+        for i in range(1, 4):
+            mri.mri_slow_rhs(y, self.fS[i - 1], self.grid, stream=self.stream)
+            mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=self.stream)
+            o = self.opts(prec, w.ramp if (first and i == 1) else 0)
+            if ev_stage is not None:
+                ev_stage[i - 1][0].record(self.stream)
+            mri.mri_stage_fast(y, self.p, self.phi, 0.0, (c[i] - c[i - 1]) * w.H, w.h, self.mech, o,
+                               cell_status=self.status, cell_stats=self.stats, n_failed=self.nfail,
+                               stream=self.stream)
+            if ev_stage is not None:
+                ev_stage[i - 1][1].record(self.stream)
+
+    def gate(self, prec):
+        """Relative error of the first fast stage of the full-size workload (forcing
+        f^S(y0) from the oracle) on 32 sampled cells against the CPU oracle."""
+        import oracle
+        torch, mri, w = self.torch, self.mri, self.w
+        fS = oracle.slow_rhs(w.y0, w.grid)
+        y = torch.tensor(w.y0, device=self.dev)
+        ph = torch.tensor(fS[:, None, :].copy(), device=self.dev)
+        with torch.cuda.stream(self.stream):
+            mri.mri_stage_fast(y, self.p, ph, 0.0, w.H / 3, w.h, self.mech, self.opts(prec, w.ramp),
+                               stream=self.stream)
+        self.stream.synchronize()
+        rng = np.random.default_rng(11)
+        idx = np.sort(rng.choice(self.ncell, min(32, self.ncell), replace=False))
+        ref, _, _ = oracle.Mech(w.mech).stage_fast(w.y0[idx], w.p[idx], fS[idx][:, None, :], w.H / 3, w.h,
+                                                    oracle.opts(method=w.method, rtol=w.newton_rtol, ramp=w.ramp))
+        got = y.cpu().numpy()[idx]
+        scale = np.abs(ref)
+        scale[:, :-1] = np.maximum(scale[:, :-1], 1e-10)
+        err = float(np.max(np.abs(got - ref) / scale))
+        return {"cells": int(len(idx)), "max_rel_err": err, "tolerance": GATE_TOL, "passed": err <= GATE_TOL}
+
+    def run_form(self, prec):
+        torch, mri, args, w = self.torch, self.mri, self.args, self.w
+        y = torch.tensor(w.y0, device=self.dev)
+        with torch.cuda.stream(self.stream):
+            for s in range(args.warmup):
+                self.step(y, prec, s == 0, None)
+            self.stream.synchronize()
+            warm_fail = int(self.nfail.item())
+            self.stats.zero_()
+            y_start = y.clone()          # the e2e leg replays the timed steps from this state
+            step_events, stage_events = [], []
+            if self.world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            sampler = ClockSampler(self.gpu_id)
+            sampler.start()
+            for s in range(args.steps):
+                self.flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(3)]
+                e0.record(self.stream)
+                self.step(y, prec, args.warmup == 0 and s == 0, ev)
+                e1.record(self.stream)
+                step_events.append((e0, e1))
+                stage_events.append(ev)
+            torch.cuda.synchronize()
+            clocks = sampler.stop()
+            if self.world > 1:
+                torch.distributed.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in step_events]
+        stage_ms = [[a.elapsed_time(b) for a, b in ev] for ev in stage_events]
+        st = self.stats.cpu().numpy().astype(np.int64)
+        substeps, newton, njac = int(st[:, 0].sum()), int(st[:, 1].sum()), int(st[:, 2].sum())
+        failed = int(self.nfail.item()) - warm_fail
+
+        # end to end through the public C-ABI call with host buffers: the same K steps
+        # from the same state, each step copying the state in from pinned host memory
+        # and the result back
+        n, ncell = self.n, self.ncell
+        y_host = torch.empty((ncell, n), dtype=torch.float64, pin_memory=True)
+        y_host.copy_(y_start.cpu())
+        p_host = torch.empty(ncell, dtype=torch.float64, pin_memory=True)
+        p_host.copy_(self.p.cpu())
+        ws = torch.empty(mri.mri_step_workspace_size(self.grid, n) // 8, dtype=torch.float64, device=self.dev)
+        e2e_stats = torch.zeros((ncell, 4), dtype=torch.int32, device=self.dev)
+        e2e_ms = []
+        with torch.cuda.stream(self.stream):
+            for s in range(args.steps):
+                self.flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                y.copy_(y_host, non_blocking=True)
+                self.p.copy_(p_host, non_blocking=True)
+                mri.mri_step(y, self.p, self.grid, s * w.H, w.H, w.h, self.mech, self.opts(prec), ws,
+                             cell_stats=e2e_stats, stream=self.stream)
+                y_host.copy_(y, non_blocking=True)
+                e1.record(self.stream)
+                e1.synchronize()
+                e2e_ms.append(e0.elapsed_time(e1))
+        e2e_sub = int(e2e_stats[:, 0].sum().item())
+        fm = flop_model(w.mech)
+        f64, f32 = algorithmic_flops(fm, newton, njac, prec)
+        return dict(prec=prec, total_ms=float(sum(step_ms)), substeps=substeps, newton=newton, njac=njac,
+                    failed=failed, clocks=clocks, stage_total_ms=float(np.sum(stage_ms)),
+                    stage_launches=3 * args.steps, flops64=f64, flops32=f32, e2e_ms=float(sum(e2e_ms)),
+                    e2e_substeps=e2e_sub, launches=9 * args.steps)
 
 
 def cpu_baseline_sample(ncells_sample, seed=0, nthreads=None, repeats=1):
@@ -320,6 +351,30 @@ def dist_init(args):
     return rank, world
 
 
+def reference_arm(args):
+    import oracle
+    oracle.build.build()
+    t_all, cs_all = 0.0, 0
+    cores = os.cpu_count() or 1
+    for s in range(args.warmup + args.steps):
+        v, cores, cs, tt = cpu_baseline_sample(256, seed=100 + s)
+        if s >= args.warmup:
+            t_all += tt
+            cs_all += cs
+    value = cs_all / t_all
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "box32 (32^3 cells, 40 species / 170 reactions, MRI3 + SDIRK3, "
+                                   "H = 5e-8 s, h = H/10)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: the three fast stages of one MRI step on 256 sampled cells "
+                                       "(forcing from the oracle's slow stencil) after an untimed start-up "
+                                       "stage"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,96 +384,85 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4096, help="cells of the oracle's CPU baseline sample")
     ap.add_argument("--cells-per-side", type=int, default=None,
                     help="shrink the box (profiling captures only; the bench line is for 32^3)")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling captures)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline and the gate (profiling captures)")
     ap.add_argument("--jac", type=int, default=1, help="Newton matrix policy: 0 per substep, 1 lazy")
-    ap.add_argument("--prec", type=int, default=0, help="0 plain FP64, 1 FP32 Jacobian/LU with FP64 residual")
+    ap.add_argument("--prec", type=int, default=None, help="time one form only: 0 plain FP64, 1 mixed precision")
     args = ap.parse_args()
     rank, world = dist_init(args)
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        import oracle
-        oracle.build.build()
-        vals = []
-        t_all = 0.0
-        cs_all = 0
-        cores = os.cpu_count() or 1
-        for s in range(args.warmup + args.steps):
-            v, cores, cs, tt = cpu_baseline_sample(256, seed=100 + s)
-            if s >= args.warmup:
-                vals.append(v)
-                t_all += tt
-                cs_all += cs
-        value = cs_all / t_all
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": "box32 (32^3 cells, 40 species / 170 reactions, MRI3 + SDIRK3, "
-                                       "H = 5e-8 s, h = H/10)", "l2": "n/a (CPU)"},
-                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                 "sample": "per step: the three fast stages of one MRI step on 256 sampled cells "
-                                           "(forcing from the oracle's slow stencil) after an untimed start-up "
-                                           "stage"},
-                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        if rank == 0:
+            reference_arm(args)
         return
 
     import torch
-    res = gpu_arm(args, rank, world)
-    # max time over ranks, sum of work
-    t = torch.tensor([res["total_ms"], res["e2e_ms"]], dtype=torch.float64, device="cuda")
-    work = torch.tensor([res["substeps"], res["e2e_substeps"]], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(work, op=torch.distributed.ReduceOp.SUM)
-    t = t.cpu().numpy()
-    work = work.cpu().numpy()
+    b = Bench(args, world)
+    forms = [args.prec] if args.prec is not None else [0, 1]
+    results = {}
+    for prec in forms:
+        r = b.run_form(prec)
+        t = torch.tensor([r["total_ms"], r["e2e_ms"]], dtype=torch.float64, device="cuda")
+        work = torch.tensor([r["substeps"], r["e2e_substeps"]], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.all_reduce(work, op=torch.distributed.ReduceOp.SUM)
+        t, work = t.cpu().numpy(), work.cpu().numpy()
+        r["value"] = work[0] / (t[0] * 1e-3)
+        r["e2e_value"] = work[1] / (t[1] * 1e-3)
+        r["gate"] = None if (args.no_cpu or rank != 0) else b.gate(prec)
+        results[prec] = r
     if rank != 0:
         return
-    value = work[0] / (t[0] * 1e-3)
-    e2e_value = work[1] / (t[1] * 1e-3)
-    # roofline of the dominant kernel (the fast stage): algorithmic flops per launch
-    # over its average event-timed duration
-    flops_per_launch = res["flops"] / res["stage_launches"]
-    avg_launch_s = res["stage_total_ms"] * 1e-3 / res["stage_launches"]
-    achieved = flops_per_launch / avg_launch_s / 1e12
-    peak = res["fp64_peak_tflops"]
+    ok = [p for p in forms if results[p]["gate"] is None or results[p]["gate"]["passed"]]
+    head = max(ok, key=lambda p: results[p]["value"]) if ok else forms[0]
+    r = results[head]
+    peak = b.fp64_peak_tflops
+
+    def roofline(r):
+        # dominant kernel (the fast stage): algorithmic FP64 flops per launch over its
+        # average event-timed duration, against the measured FP64 FMA pipe rate
+        per_launch = r["flops64"] / r["stage_launches"]
+        avg_s = r["stage_total_ms"] * 1e-3 / r["stage_launches"]
+        ach = per_launch / avg_s / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "stage_fast_kernel", "fp64_flops_per_launch": per_launch,
+                "fp32_flops_per_launch": r["flops32"] / r["stage_launches"], "avg_launch_ms": avg_s * 1e3,
+                "peak_basis": "FP64 FMA pipe rate measured in this run (mri_probe_fp64_fma; the pipe issues 2 "
+                              "DFMA/clk/SM, %.4f TFLOP/s at 2070 MHz); MEASURED_PEAKS.json has no FP64 entry"
+                              % FP64_PEAK_TFLOPS_NOMINAL}
+
     if args.no_cpu:
-        cpu_v, cores, cs, tt = None, 0, 0, 0.0
+        cpu = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": "skipped (--no-cpu)"}
     else:
         cpu_v, cores, cs, tt = cpu_baseline_sample(args.cpu_sample)
-    w = res["workload"]
+        cpu = {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"the three fast stages of one MRI step on {args.cpu_sample} sampled cells ({cs} "
+                         f"cell-steps, {tt:.1f} s), forcing from the oracle's slow stencil, after an untimed "
+                         f"start-up stage"}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head == 0 else "f64+f32", "data": "synthetic",
         "config": {"workload": "box32: 32^3 periodic box, 40 species / 170 reactions (12 third-body, 8 Troe), "
                                "MRI3 (Knoth-Wolke MIS) + SDIRK3 fast, H = 5e-8 s, h = H/10, Newton rtol 1e-10, "
                                "4th-order slow stencil; one step = one MRI slow step",
-                   "cells": res["ncell"], "unknowns_per_cell": res["n"],
-                   "form": ["plain FP64", "mixed: FP32 Jacobian/LU, FP64 rates/residual"][args.prec],
+                   "cells": b.ncell, "unknowns_per_cell": b.n, "form": FORMS[head],
                    "jac_policy": ["per-substep", "lazy"][args.jac],
                    "reduced_for_profiling": args.cells_per_side is not None,
                    "l2": "256 MB buffer written between timed steps",
-                   "newton_per_substep": res["newton"] / max(res["substeps"], 1),
-                   "jac_per_substep": res["njac"] / max(res["substeps"], 1),
-                   "failed_cells": res["failed"]},
-        "clocks": res["clocks"],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "stage_fast_kernel",
-                     "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                     "peak_basis": "FP64 FMA pipe rate measured in this run (mri_probe_fp64_fma; the pipe "
-                                   "issues 2 DFMA/clk/SM, %.4f TFLOP/s at 2070 MHz); MEASURED_PEAKS.json has no "
-                                   "FP64 entry" % FP64_PEAK_TFLOPS_NOMINAL},
-        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"the three fast stages of one MRI step on {args.cpu_sample} sampled cells "
-                                   f"({cs} cell-steps, {tt:.1f} s), forcing from the oracle's slow stencil, after "
-                                   f"an untimed start-up stage"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
-                "d2h_bytes_per_step": res["d2h"]},
-        "gpu_launches": res["launches"],
+                   "newton_per_substep": r["newton"] / max(r["substeps"], 1),
+                   "jac_per_substep": r["njac"] / max(r["substeps"], 1), "failed_cells": r["failed"]},
+        "clocks": r["clocks"],
+        "roofline": roofline(r),
+        "cpu_baseline": cpu,
+        "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": (b.ncell * b.n + b.ncell) * 8,
+                "d2h_bytes_per_step": b.ncell * b.n * 8},
+        "gpu_launches": r["launches"],
+        "gate": r["gate"],
+        "forms": {FORMS[p]: {"value": results[p]["value"], "e2e": results[p]["e2e_value"],
+                             "roofline_frac": roofline(results[p])["frac"], "gate": results[p]["gate"],
+                             "newton_per_substep": results[p]["newton"] / max(results[p]["substeps"], 1),
+                             "clocks": results[p]["clocks"]} for p in forms},
     }
     print(json.dumps(line))
 

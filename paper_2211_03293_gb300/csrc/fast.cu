@@ -18,11 +18,11 @@ namespace mri {
 // ------------------------------------------------------------------ views
 
 struct Tab {
-  const double *cp, *hh, *ss, *h5, *s6, *dcp, *W, *invW, *lnA, *b, *Ta, *effd, *eval, *troe, *nu, *exp2t;
-  const float *nu32, *effd32, *W32, *invW32, *dcp32;
+  const double *cp, *hh, *ss, *h5, *s6, *dcp, *W, *invW, *lnA, *b, *Ta, *eval, *troe, *nu, *exp2t, *tcv;
+  const float *nu32, *W32, *invW32, *dcp32, *tcv32;
   const uint64_t *rxn, *cent, *rsp;
-  const int32_t *rrow, *eptr, *eidx, *wptr, *went, *cptr, *tbl, *trx;
-  int Ns, R, n, nsv, n_tb, n_troe;
+  const int32_t *rrow, *eptr, *eidx, *cptr, *tbl, *trx, *tcptr, *tcr, *gent, *gsptr, *gslot;
+  int Ns, R, n, nsv, n_tb, n_troe, g_chunk, n_went;
   __device__ Tab(const unsigned char* s, const Layout& L) {
     cp = reinterpret_cast<const double*>(s + L.o_cp);
     hh = reinterpret_cast<const double*>(s + L.o_h);
@@ -35,13 +35,11 @@ struct Tab {
     lnA = reinterpret_cast<const double*>(s + L.o_lnA);
     b = reinterpret_cast<const double*>(s + L.o_b);
     Ta = reinterpret_cast<const double*>(s + L.o_Ta);
-    effd = reinterpret_cast<const double*>(s + L.o_effd);
     eval = reinterpret_cast<const double*>(s + L.o_eval);
     troe = reinterpret_cast<const double*>(s + L.o_troe);
     nu = reinterpret_cast<const double*>(s + L.o_nu) + 3;   // nu[v] for v in -3..4
     exp2t = reinterpret_cast<const double*>(s + L.o_exp2);
     nu32 = reinterpret_cast<const float*>(s + L.o_nu32) + 3;
-    effd32 = reinterpret_cast<const float*>(s + L.o_effd32);
     W32 = reinterpret_cast<const float*>(s + L.o_W32);
     invW32 = reinterpret_cast<const float*>(s + L.o_invW32);
     dcp32 = reinterpret_cast<const float*>(s + L.o_dcp32);
@@ -51,33 +49,39 @@ struct Tab {
     rrow = reinterpret_cast<const int32_t*>(s + L.o_rrow);
     eptr = reinterpret_cast<const int32_t*>(s + L.o_eptr);
     eidx = reinterpret_cast<const int32_t*>(s + L.o_eidx);
-    wptr = reinterpret_cast<const int32_t*>(s + L.o_wptr);
-    went = reinterpret_cast<const int32_t*>(s + L.o_went);
     cptr = reinterpret_cast<const int32_t*>(s + L.o_cptr);
     tbl = reinterpret_cast<const int32_t*>(s + L.o_tbl);
     trx = reinterpret_cast<const int32_t*>(s + L.o_trx);
+    tcptr = reinterpret_cast<const int32_t*>(s + L.o_tcptr);
+    gent = reinterpret_cast<const int32_t*>(s + L.o_gent);
+    gsptr = reinterpret_cast<const int32_t*>(s + L.o_gsptr);
+    gslot = reinterpret_cast<const int32_t*>(s + L.o_gslot);
+    tcr = reinterpret_cast<const int32_t*>(s + L.o_tcr);
+    tcv = reinterpret_cast<const double*>(s + L.o_tcv);
+    tcv32 = reinterpret_cast<const float*>(s + L.o_tcv32);
     Ns = L.Ns; R = L.R; n = L.n; nsv = L.nsv; n_tb = L.n_tb; n_troe = L.n_troe;
+    g_chunk = L.g_chunk; n_went = L.n_went;
   }
 };
 
 struct WS {
   double *M, *y0, *Z, *d, *res, *F0, *F1, *Fl, *r, *f, *base, *phi, *C, *g, *hh, *cp, *wd, *DT, *DC, *aux, *dinv;
-  double *E, *Einv, *c0p, *tro;
+  double *E, *Einv, *c0p, *tro, *tbk;
   int* piv;
   double *q, *kfw, *krw, *dqdT, *tbs;
   // mixed-precision form: FP32 Newton matrix, its diagonal inverse and FP32 copies
-  float *M32, *dinv32, *d32, *C32, *hh32, *cp32, *wd32, *DT32, *DC32, *aux32, *kfw32, *krw32, *tbs32;
+  float *M32, *dinv32, *d32, *C32, *hh32, *cp32, *wd32, *DT32, *DC32, *aux32, *tbk32, *kfw32, *krw32, *tbs32;
   int ld, nv;
   __device__ __forceinline__ double* F(int j) const { return j == 0 ? F0 : F1; }
-  __device__ WS(double* base, const Layout& L, bool prec32) {
-    WsOffsets o = ws_offsets(L, prec32);
+  __device__ WS(double* base, const Layout& L, bool prec32, int K) {
+    WsOffsets o = ws_offsets(L, prec32, K);
     M = base + o.M; y0 = base + o.y0; Z = base + o.Z; d = base + o.d;
     F0 = base + o.F0; F1 = base + o.F1; Fl = base + o.Fl; r = base + o.r; f = base + o.f; phi = base + o.phi;
     this->base = base + o.base;
     res = base + o.res;
     C = base + o.C; g = base + o.g; hh = base + o.hh; cp = base + o.cp; wd = base + o.wd;
     DT = base + o.DT; DC = base + o.DC; aux = base + o.aux; dinv = base + o.dinv;
-    E = base + o.E; Einv = base + o.Einv; c0p = base + o.c0p; tro = base + o.tro;
+    E = base + o.E; Einv = base + o.Einv; c0p = base + o.c0p; tro = base + o.tro; tbk = base + o.tbk;
     piv = reinterpret_cast<int*>(base + o.piv);
     q = base + o.q; kfw = base + o.kfw; krw = base + o.krw; dqdT = base + o.dqdT; tbs = base + o.tbs;
     float* fb = reinterpret_cast<float*>(base + o.f32);
@@ -85,7 +89,7 @@ struct WS {
     M32 = reinterpret_cast<float*>(base + o.M);
     dinv32 = fb + g32.dinv; d32 = fb + g32.d;
     C32 = fb + g32.C; hh32 = fb + g32.hh; cp32 = fb + g32.cp; wd32 = fb + g32.wd; DT32 = fb + g32.DT;
-    DC32 = fb + g32.DC; aux32 = fb + g32.aux; kfw32 = fb + g32.kfw; krw32 = fb + g32.krw; tbs32 = fb + g32.tbs;
+    DC32 = fb + g32.DC; aux32 = fb + g32.aux; tbk32 = fb + g32.tbk; kfw32 = fb + g32.kfw; krw32 = fb + g32.krw; tbs32 = fb + g32.tbs;
     ld = L.ld;
     nv = round_up(L.n + 1, 2);
   }
@@ -115,6 +119,32 @@ __device__ void stage_table(unsigned char* dst, const unsigned char* src, int by
 struct Scal {        // warp-uniform per-evaluation scalars
   double T, invT, lnT, S, rho, invrho, Ctot, cpm, Q;
 };
+
+// dst[k] = sum_r nu_kr src[r] for every species, balanced over the lanes: lane l
+// sums entries [l L, (l+1) L) of the species-major (species, reaction, nu) list,
+// ending every run of one species in a partial-sum slot (the slots reuse the
+// falloff scratch, free after the reaction pass); then each species adds its slots
+// in a fixed order, so the sums are deterministic.
+__device__ __forceinline__ void gather_species(const Tab& t, const WS& w, const double* src, double* dst, int lane) {
+  double* P = w.tro;
+  double acc = 0.0;
+  const int e1 = min((lane + 1) * t.g_chunk, t.n_went);
+  for (int e = lane * t.g_chunk; e < e1; ++e) {
+    const int v = t.gent[e];
+    acc = fma(t.nu[((v >> 10) & 0xf) - 8], src[v & 0x3ff], acc);
+    if ((v >> 22) & 1) {
+      P[(v >> 14) & 0xff] = acc;
+      acc = 0.0;
+    }
+  }
+  __syncwarp();
+  for (int k = lane; k < t.Ns; k += 32) {
+    double sum = 0.0;
+    for (int j = t.gsptr[k]; j < t.gsptr[k + 1]; ++j) sum += P[t.gslot[j]];
+    dst[k] = sum;
+  }
+  __syncwarp();
+}
 
 struct RxnOut {
   double q, kfw, krw, dqdT, tbs;
@@ -291,18 +321,14 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     }
   }
   __syncwarp();
+  gather_species(t, w, w.q, w.wd, lane);
+  if (JAC) {
+    gather_species(t, w, w.dqdT, w.DT, lane);
+    gather_species(t, w, w.tbs, w.tbk, lane);
+  }
   double qp = 0.0, cpp = 0.0;
   for (int k = lane; k < Ns; k += 32) {
-    double acc = 0.0, accT = 0.0;
-    for (int e = t.wptr[k]; e < t.wptr[k + 1]; ++e) {
-      const int v = t.went[e];
-      const double nuv = t.nu[v >> 16];
-      acc = fma(nuv, w.q[v & 0xffff], acc);
-      if (JAC) accT = fma(nuv, w.dqdT[v & 0xffff], accT);
-    }
-    w.wd[k] = acc;
-    if (JAC) w.DT[k] = accT;
-    qp = fma(w.hh[k], acc, qp);
+    qp = fma(w.hh[k], w.wd[k], qp);
     cpp = fma(Z[k] * t.invW[k], w.cp[k], cpp);
   }
   s.T = T; s.invT = invT; s.lnT = lnT; s.S = S; s.rho = rho; s.invrho = invrho; s.Ctot = Ctot;
@@ -323,26 +349,27 @@ __device__ __forceinline__ void chem_rhs_out(const Tab& t, const WS& w, const Sc
 // chem_eval<true> arrays, or FP32 copies of them for the mixed-precision form.
 template <typename MT>
 struct JacIn {
-  const MT *C, *hh, *cp, *wd, *DT, *kfw, *krw, *tbs, *nu, *effd, *W, *invW, *dcp;
+  const MT *C, *hh, *cp, *wd, *DT, *tbk, *kfw, *krw, *tbs, *nu, *tcv, *W, *invW, *dcp;
   MT *DC, *aux;
 };
 
 __device__ __forceinline__ JacIn<double> jac_in64(const Tab& t, const WS& w) {
-  return JacIn<double>{w.C, w.hh, w.cp, w.wd, w.DT, w.kfw, w.krw, w.tbs, t.nu, t.effd, t.W, t.invW, t.dcp, w.DC, w.aux};
+  return JacIn<double>{w.C, w.hh, w.cp, w.wd, w.DT, w.tbk, w.kfw, w.krw, w.tbs, t.nu, t.tcv, t.W, t.invW, t.dcp, w.DC,
+                      w.aux};
 }
 
 // FP32 copies of the per-cell Jacobian inputs (mixed-precision form).
 __device__ __forceinline__ JacIn<float> jac_in32(const Tab& t, const WS& w, int lane) {
   for (int k = lane; k < t.nsv; k += 32) {
     w.C32[k] = (float)w.C[k]; w.hh32[k] = (float)w.hh[k]; w.cp32[k] = (float)w.cp[k];
-    w.wd32[k] = (float)w.wd[k]; w.DT32[k] = (float)w.DT[k];
+    w.wd32[k] = (float)w.wd[k]; w.DT32[k] = (float)w.DT[k]; w.tbk32[k] = (float)w.tbk[k];
   }
   for (int r = lane; r < t.R; r += 32) {
     w.kfw32[r] = (float)w.kfw[r]; w.krw32[r] = (float)w.krw[r]; w.tbs32[r] = (float)w.tbs[r];
   }
   __syncwarp();
-  return JacIn<float>{w.C32, w.hh32, w.cp32, w.wd32, w.DT32, w.kfw32, w.krw32, w.tbs32, t.nu32, t.effd32, t.W32,
-                      t.invW32, t.dcp32, w.DC32, w.aux32};
+  return JacIn<float>{w.C32, w.hh32, w.cp32, w.wd32, w.DT32, w.tbk32, w.kfw32, w.krw32, w.tbs32, t.nu32, t.tcv32,
+                      t.W32, t.invW32, t.dcp32, w.DC32, w.aux32};
 }
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
@@ -356,7 +383,8 @@ __device__ __forceinline__ void chem_jac(const Tab& t, const WS& w, const double
                                          const JacIn<MT>& in, int lane) {
   const int Ns = t.Ns, ld = w.ld, nsv = t.nsv;
   for (int l = lane; l < Ns; l += 32) {
-    for (int k = 0; k < Ns; ++k) J[k * ld + l] = MT(0);
+    // third-body part common to every column: sum_r nu_kr (k_f prod - k_r prod)-scale
+    for (int k = 0; k < Ns; ++k) J[k * ld + l] = in.tbk[k];
     for (int e = t.cptr[l]; e < t.cptr[l + 1]; ++e) {
       const uint64_t ce = t.cent[e];
       const int r = ce & 0xffff;
@@ -371,10 +399,10 @@ __device__ __forceinline__ void chem_jac(const Tab& t, const WS& w, const double
         J[k * ld + l] = fma_t(in.nu[nuv], dq, J[k * ld + l]);
       }
     }
-    for (int i = 0; i < t.n_tb; ++i) {
-      const int r = t.tbl[i];
-      const int row = t.rrow[r] & 0xffff;
-      const MT sc = in.effd[row * nsv + l] * in.tbs[r];
+    // third-body efficiencies that differ from 1
+    for (int e = t.tcptr[l]; e < t.tcptr[l + 1]; ++e) {
+      const int r = t.tcr[e];
+      const MT sc = in.tcv[e] * in.tbs[r];
       const uint64_t s0 = t.rsp[2 * r], s1 = t.rsp[2 * r + 1];
       const int cnt = (int)((s0 >> 48) & 0xff);
       for (int j = 0; j < cnt; ++j) {
@@ -547,7 +575,7 @@ struct StageArgs {
   int32_t* n_failed;
   const unsigned char* table;
   Layout L;
-  int ncell, K, n_sub, ramp, max_newton, nstage, sticky, jac_policy;
+  int ncell, K, n_sub, ramp, max_newton, nstage, sticky, jac_policy, ws_stride;
   double Hs, hh, rtol, atol_Y, atol_T;
   double A[3][3], c[3], gamma;
 };
@@ -623,8 +651,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
   __syncthreads();
   const Tab t(smem, a.L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const WS w(reinterpret_cast<double*>(smem + a.L.bytes) + (size_t)warp * (PREC32 ? a.L.ws_doubles32 : a.L.ws_doubles),
-             a.L, PREC32);
+  const WS w(reinterpret_cast<double*>(smem + a.L.bytes) + (size_t)warp * a.ws_stride, a.L, PREC32, a.K);
   const int n = t.n, Ns = t.Ns, S = a.nstage;
   const int total_sub = a.n_sub + (a.ramp > 0 ? a.ramp : 0);
   for (int cell = blockIdx.x * nw + warp; cell < a.ncell; cell += gridDim.x * nw) {
@@ -777,7 +804,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) rhs_kernel(const double* y, co
   __syncthreads();
   const Tab t(smem, L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const WS w(reinterpret_cast<double*>(smem + L.bytes) + (size_t)warp * L.ws_doubles, L, false);
+  const WS w(reinterpret_cast<double*>(smem + L.bytes) + (size_t)warp * ws_offsets(L, false, 0).total, L, false, 0);
   for (int cell = blockIdx.x * nw + warp; cell < ncell; cell += gridDim.x * nw) {
     for (int k = lane; k < t.n; k += 32) w.Z[k] = y[(size_t)cell * t.n + k];
     __syncwarp();
@@ -796,7 +823,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) jac_kernel(const double* y, co
   __syncthreads();
   const Tab t(smem, L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const WS w(reinterpret_cast<double*>(smem + L.bytes) + (size_t)warp * L.ws_doubles, L, false);
+  const WS w(reinterpret_cast<double*>(smem + L.bytes) + (size_t)warp * ws_offsets(L, false, 0).total, L, false, 0);
   const int n = t.n;
   for (int cell = blockIdx.x * nw + warp; cell < ncell; cell += gridDim.x * nw) {
     for (int k = lane; k < n; k += 32) w.Z[k] = y[(size_t)cell * n + k];
@@ -847,9 +874,10 @@ int device_smem_limit() {
 }
 
 // Warps per CTA and grid for a warp-per-cell kernel with `per_warp` bytes of workspace.
-static bool plan_launch(const Layout& L, int ncell, int& warps, int& blocks, size_t& smem, bool prec32 = false) {
+static bool plan_launch(const Layout& L, int ncell, int& warps, int& blocks, size_t& smem, bool prec32 = false,
+                        int K = 0) {
   const int limit = device_smem_limit();
-  const size_t per_warp = (size_t)(prec32 ? L.ws_doubles32 : L.ws_doubles) * 8;
+  const size_t per_warp = (size_t)ws_offsets(L, prec32, K).total * 8;
   int wmax = (int)((limit - L.bytes) / (long long)per_warp);
   if (wmax < 1) return false;
   if (wmax > kMaxWarps) wmax = kMaxWarps;
@@ -912,9 +940,10 @@ int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, 
   a.rtol = o.newton_rtol; a.atol_Y = o.newton_atol_Y; a.atol_T = o.newton_atol_T;
   sdirk_table(o.method, a);
   const bool prec32 = (o.precision == MRI_PREC_FP32_LU);
+  a.ws_stride = ws_offsets(m.L, prec32, K).total;
   int warps, blocks;
   size_t smem;
-  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32)) return MRI_EINVAL;
+  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32, K)) return MRI_EINVAL;
   if (prec32) {
     if (cudaFuncSetAttribute(stage_fast_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)

@@ -33,31 +33,34 @@ struct Layout {
   int o_lnA, o_b, o_Ta;   // double [rv]
   int o_rxn;              // uint64 [rv]: bytes 0-2 reactants, 3-5 products (pad = Ns), 6 dn (int8), 7 type
   int o_rrow;             // int32 [rv]: eff row (low 16 bits, 0xffff none) | troe row << 16
-  int o_effd;             // double [n_eff][nsv] efficiencies alpha (dense, 0 in the pad slot)
   int o_eptr;             // int32 [n_eff + 1] sparse (alpha - 1) lists
   int o_eidx;             // int32 [ne]
   int o_eval;             // double [ne]
   int o_troe;             // double [n_troe][8]: lnA0, b0, Ta0, a, 1/T***, 1/T*, T**, 0
-  int o_wptr;             // int32 [Ns + 1] species -> (reaction, nu) lists for sums over reactions
-  int o_went;             // int32 [nw]: r | nu << 16 (nu != 0)
+  int o_gent;             // int32 [n_went]: r (10 bits) | nu + 8 (4) | slot (8) | run-end flag (1)
+  int o_gsptr;            // int32 [Ns + 1] species -> partial-sum slots
+  int o_gslot;            // int32 [..] slot indices
+  int g_chunk, n_went, n_slots;   // entries per lane, list length, partial-sum slots
   int o_cptr;             // int32 [Ns + 1] Jacobian column -> reaction entries
   int o_cent;             // uint64 [nc]: r (16) | mult_f (4) | mult_r (4) | o1..o4 (8 bits each)
   int o_rsp;              // uint64 [rv][2]: word 0 species k0..k5 + count; word 1 int8 nu0..nu5
   int o_tbl;              // int32 [n_tb]: reactions with an efficiency row (third body or falloff)
+  int o_tcptr;            // int32 [Ns + 1] Jacobian column -> third-body corrections
+  int o_tcr;              // int32 [ntc]: reaction of the correction
+  int o_tcv, o_tcv32;     // double / float [ntc]: alpha_rl - 1
   int o_trx;              // int32 [n_troe]: reaction index of each falloff row
   int o_exp2;             // double [32]: 2^(j/32), the table of the exponential (fastmath.cuh)
   int o_nu;               // double [8]: the small integers -3..4 as doubles (index v + 3), so kernels
                           // turn stoichiometric integers into doubles with a load, not a conversion
   // FP32 copies of the constants the mixed-precision Jacobian reads
   int o_nu32;             // float [8]
-  int o_effd32;           // float [n_eff][nsv]
   int o_W32, o_invW32;    // float [nsv]
   int o_dcp32;            // float [4][nsv]
   int bytes;              // total, multiple of 16
   // per-cell workspace (doubles) inside shared memory
   int ld;                 // leading dimension of the n x n matrix (odd)
-  int ws_doubles;         // doubles per cell (warp), FP64 form
-  int ws_doubles32;       // doubles per cell (warp), mixed-precision form
+  int ws_doubles;         // doubles per cell (warp), FP64 form, K = kMaxK
+  int ws_doubles32;       // doubles per cell (warp), mixed-precision form, K = kMaxK
 };
 
 struct Mech {             // what mri_mech points at
@@ -72,7 +75,7 @@ struct Mech {             // what mri_mech points at
 struct WsOffsets {
   int M, y0, Z, d, res, F0, F1, Fl, r, f, base, phi, C, g, hh, cp, wd, DT, DC, aux, dinv, piv;
   int q, kfw, krw, dqdT, tbs;
-  int E, Einv, c0p, tro;
+  int E, Einv, c0p, tro, tbk;
   int f32;     // start of the float region (prec32 only), in doubles
   int total;
 };
@@ -81,7 +84,7 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 
 // float offsets inside the f32 region
 struct F32Offsets {
-  int C, hh, cp, wd, DT, DC, aux, kfw, krw, tbs, d, dinv, total;
+  int C, hh, cp, wd, DT, DC, aux, tbk, kfw, krw, tbs, d, dinv, total;
 };
 
 __host__ __device__ inline F32Offsets f32_offsets(const Layout& L) {
@@ -95,6 +98,7 @@ __host__ __device__ inline F32Offsets f32_offsets(const Layout& L) {
   f.DT = o; o += ns;
   f.DC = o; o += ns;
   f.aux = o; o += ns;
+  f.tbk = o; o += ns;
   f.kfw = o; o += rv;
   f.krw = o; o += rv;
   f.tbs = o; o += rv;
@@ -104,7 +108,7 @@ __host__ __device__ inline F32Offsets f32_offsets(const Layout& L) {
   return f;
 }
 
-__host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = false) {
+__host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = false, int K = kMaxK) {
   WsOffsets w;
   int nv = round_up(L.n + 1, 2);
   int o = 0;
@@ -119,16 +123,13 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = f
   w.r = o; o += nv;
   w.f = o; o += nv;
   w.base = o; o += nv;
-  w.phi = o; o += kMaxK * nv;
   w.C = o; o += L.nsv;
   w.g = o; o += L.nsv;
   w.hh = o; o += L.nsv;
   w.cp = o; o += L.nsv;
   w.wd = o; o += L.nsv;
   w.DT = o; o += L.nsv;
-  w.DC = o; o += L.nsv;
-  w.aux = o; o += L.nsv;
-  w.dinv = o; o += nv;
+  w.dinv = o; o += prec32 ? 0 : nv;   // FP64 pivots' inverses (the FP32 form keeps its own)
   w.piv = o; o += nv / 2 + 1;   // int32 pivots
   o = round_up(o, 2);
   w.q = o; o += L.rv;
@@ -138,11 +139,23 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = f
   w.tbs = o; o += L.rv;
   w.E = o; o += L.nsv;
   w.Einv = o; o += L.nsv;
-  w.c0p = o; o += 8;
-  w.tro = o; o += kTroeSlots * (L.n_troe > 0 ? L.n_troe : 1);
+  // the Jacobian's DC and column-sum vectors reuse E and 1/E, which only the rate
+  // pass before it reads
+  w.DC = w.E;
+  w.aux = w.Einv;
+  w.c0p = o; o += 6;
+  // falloff intermediates; after the reaction pass the same doubles hold the
+  // partial sums of the balanced production-rate pass
+  w.tro = o;
+  {
+    const int ntro = kTroeSlots * (L.n_troe > 0 ? L.n_troe : 1);
+    o += ntro > L.n_slots ? ntro : L.n_slots;
+  }
+  w.tbk = o; o += L.nsv;
   o = round_up(o, 2);
   w.f32 = o;
   if (prec32) o += f32_offsets(L).total / 2;
+  w.phi = o; o += K * nv;        // forcing coefficients: sized by the launch's K
   w.total = round_up(o, 2);
   return w;
 }

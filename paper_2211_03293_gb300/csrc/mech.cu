@@ -136,7 +136,6 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
   L.o_Ta = S.add(rv * 8);
   L.o_rxn = S.add(rv * 8);
   L.o_rrow = S.add(rv * 4);
-  L.o_effd = S.add((size_t)(B.n_eff > 0 ? B.n_eff : 1) * nsv * 8);
   // sparse (alpha - 1) entries
   std::vector<int> eptr(B.n_eff + 1, 0), eidx;
   std::vector<double> evals;
@@ -166,8 +165,40 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
       if (kv.second != 0) wl[kv.first].push_back((int32_t)(r | ((uint32_t)(kv.second & 0xffff) << 16)));
   size_t nw = 0;
   for (auto& v : wl) nw += v.size();
-  L.o_wptr = S.add((Ns + 1) * 4);
-  L.o_went = S.add((nw + 1) * 4);
+  // balanced production-rate sums: the species-major (species, reaction, nu) list cut
+  // into 32 equal chunks, one per lane; each run of one species inside a chunk ends
+  // in a partial-sum slot, and every species sums its slots
+  const int gL = (int)((nw + 31) / 32);
+  std::vector<int32_t> gent(nw > 0 ? nw : 1, 0);
+  std::vector<std::vector<int32_t>> spslots(Ns);
+  int nslot = 0;
+  {
+    std::vector<std::pair<int, int32_t>> flat;   // (species, packed r | nu)
+    for (int k = 0; k < Ns; ++k)
+      for (int32_t v : wl[k]) flat.push_back({k, v});
+    for (size_t e = 0; e < flat.size(); ++e) {
+      const int k = flat[e].first;
+      const int r = flat[e].second & 0xffff;
+      const int nu = (int)(int16_t)((uint32_t)flat[e].second >> 16);
+      const bool chunk_end = ((e + 1) % gL == 0) || (e + 1 == flat.size());
+      const bool last = chunk_end || flat[e + 1].first != k;
+      if (e == 0 || e % gL == 0 || flat[e - 1].first != k) {   // first entry of a run
+        spslots[k].push_back(nslot);
+      }
+      const int slot = spslots[k].back();
+      if (last) ++nslot;
+      gent[e] = (int32_t)(r | ((nu + 8) << 10) | (slot << 14) | ((last ? 1 : 0) << 22));
+    }
+  }
+  if (nslot > 255) return MRI_EINVAL;   // slot field is 8 bits wide
+  L.g_chunk = gL;
+  L.n_went = (int)nw;
+  L.n_slots = nslot;
+  L.o_gent = S.add(gent.size() * 4);
+  L.o_gsptr = S.add((Ns + 1) * 4);
+  size_t nss = 0;
+  for (auto& v : spslots) nss += v.size();
+  L.o_gslot = S.add((nss + 1) * 4);
   // Jacobian column entries: species l that appears among the reactants or products of r
   std::vector<std::vector<uint64_t>> cl(Ns);
   for (int r = 0; r < R; ++r) {
@@ -221,11 +252,24 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
     if (B.rtype[r] != 0) tbl.push_back(r);
   L.n_tb = (int)tbl.size();
   L.o_tbl = S.add((tbl.size() + 1) * 4);
+  // per Jacobian column l: the third-body reactions r whose efficiency of species l
+  // differs from 1, with alpha_rl - 1 (the part of d[M]/dC_l beyond the common 1)
+  std::vector<std::vector<std::pair<int, double>>> tcl(Ns);
+  for (int r : tbl)
+    for (int l = 0; l < Ns; ++l) {
+      const double a = B.eff[(size_t)B.eff_row[r] * Ns + l];
+      if (a != 1.0) tcl[l].push_back({r, a - 1.0});
+    }
+  size_t ntc = 0;
+  for (auto& v : tcl) ntc += v.size();
+  L.o_tcptr = S.add((Ns + 1) * 4);
+  L.o_tcr = S.add((ntc + 1) * 4);
+  L.o_tcv = S.add((ntc + 1) * 8);
+  L.o_tcv32 = S.add((ntc + 1) * 4);
   L.o_trx = S.add((size_t)(B.n_troe > 0 ? B.n_troe : 1) * 4);
   L.o_exp2 = S.add(32 * 8);
   L.o_nu = S.add(8 * 8);
   L.o_nu32 = S.add(8 * 4);
-  L.o_effd32 = S.add((size_t)(B.n_eff > 0 ? B.n_eff : 1) * nsv * 4);
   L.o_W32 = S.add(nsv * 4);
   L.o_invW32 = S.add(nsv * 4);
   L.o_dcp32 = S.add(4 * nsv * 4);
@@ -294,9 +338,6 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
     rsp[2 * r] = w0;
     rsp[2 * r + 1] = w1;
   }
-  double* effd = S.at<double>(L.o_effd);
-  for (int e = 0; e < B.n_eff; ++e)
-    for (int k = 0; k < Ns; ++k) effd[(size_t)e * nsv + k] = B.eff[(size_t)e * Ns + k];
   int32_t* ep = S.at<int32_t>(L.o_eptr);
   for (int e = 0; e <= B.n_eff; ++e) ep[e] = eptr[e];
   int32_t* ei = S.at<int32_t>(L.o_eidx);
@@ -314,14 +355,19 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
     tro[8 * t + 6] = q[6];
     tro[8 * t + 7] = 0.0;
   }
-  int32_t* wp = S.at<int32_t>(L.o_wptr);
-  int32_t* we = S.at<int32_t>(L.o_went);
   int pos = 0;
-  for (int k = 0; k < Ns; ++k) {
-    wp[k] = pos;
-    for (int32_t v : wl[k]) we[pos++] = v;
+  {
+    int32_t* ge = S.at<int32_t>(L.o_gent);
+    for (size_t e = 0; e < gent.size(); ++e) ge[e] = gent[e];
+    int32_t* gp = S.at<int32_t>(L.o_gsptr);
+    int32_t* gs = S.at<int32_t>(L.o_gslot);
+    int q = 0;
+    for (int k = 0; k < Ns; ++k) {
+      gp[k] = q;
+      for (int32_t s : spslots[k]) gs[q++] = s;
+    }
+    gp[Ns] = q;
   }
-  wp[Ns] = pos;
   int32_t* cptr = S.at<int32_t>(L.o_cptr);
   uint64_t* cent = S.at<uint64_t>(L.o_cent);
   pos = 0;
@@ -332,6 +378,18 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
   cptr[Ns] = pos;
   int32_t* tb = S.at<int32_t>(L.o_tbl);
   for (size_t i = 0; i < tbl.size(); ++i) tb[i] = tbl[i];
+  {
+    int32_t* tcp = S.at<int32_t>(L.o_tcptr);
+    int32_t* tcr = S.at<int32_t>(L.o_tcr);
+    double* tcv = S.at<double>(L.o_tcv);
+    float* tcv32 = S.at<float>(L.o_tcv32);
+    int q = 0;
+    for (int l = 0; l < Ns; ++l) {
+      tcp[l] = q;
+      for (auto& pr : tcl[l]) { tcr[q] = pr.first; tcv[q] = pr.second; tcv32[q] = (float)pr.second; ++q; }
+    }
+    tcp[Ns] = q;
+  }
   int32_t* trx = S.at<int32_t>(L.o_trx);
   for (int r = 0; r < R; ++r)
     if (B.rtype[r] == 2) trx[B.troe_row[r]] = r;
@@ -341,8 +399,6 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
   for (int i = 0; i < 8; ++i) nu[i] = (double)(i - 3);
   float* nu32 = S.at<float>(L.o_nu32);
   for (int i = 0; i < 8; ++i) nu32[i] = (float)(i - 3);
-  float* effd32 = S.at<float>(L.o_effd32);
-  for (int e = 0; e < B.n_eff * nsv; ++e) effd32[e] = (float)effd[e];
   float* W32 = S.at<float>(L.o_W32);
   float* invW32 = S.at<float>(L.o_invW32);
   float* dcp32 = S.at<float>(L.o_dcp32);

@@ -184,6 +184,7 @@ class Bench:
         self.grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
         self.c, self.G = mri.mri_method_coupling(mri.MRI_KW3)
         self.stream = torch.cuda.Stream(device=self.dev)
+        self.shape = {}
         dev = self.dev
         self.p = torch.tensor(w.p, device=dev)
         self.fS = torch.empty((3, self.ncell, self.n), dtype=torch.float64, device=dev)
@@ -201,8 +202,50 @@ class Bench:
 
     def opts(self, prec, ramp=0):
         w = self.w
+        wpb, bps = self.shape.get(prec, (0, 0))
         return self.mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, ramp=ramp,
-                                              jac_policy=self.args.jac, precision=prec)
+                                              jac_policy=self.args.jac, precision=prec, warps_per_block=wpb,
+                                              blocks_per_sm=bps)
+
+    def autotune(self, y, prec):
+        """Pick the launch shape of the fast stage by timing the candidates on the
+        first stage of the next step (copies of the state and of its forcing)."""
+        from paper_2211_03293_gb300.autotune import autotune_stage
+        mri, c, G, w = self.mri, self.c, self.G, self.w
+        with self.torch.cuda.stream(self.stream):
+            mri.mri_slow_rhs(y, self.fS[0], self.grid, stream=self.stream)
+            mri.mri_stage_forcing(self.fS, 1, G[1], self.phi, stream=self.stream)
+            best, table = autotune_stage(self.mech, y, self.p, self.phi, (c[1] - c[0]) * w.H, w.h, self.opts(prec),
+                                         repeats=2, stream=self.stream)
+        self.shape[prec] = (best.warps_per_block, best.blocks_per_sm)
+        wpb, blocks, smem = mri.mri_stage_fast_shape(self.mech, best, self.ncell, 1)
+        return {"warps_per_block": wpb, "blocks": blocks, "blocks_per_sm": max(best.blocks_per_sm, 1),
+                "smem_bytes": smem, "autotuned": [[a, b_, round(ms, 3)] for a, b_, ms in table]}
+
+    def graph_steps(self, y, prec):
+        """The same MRI step recorded once in a CUDA graph and replayed args.steps times
+        (L2 flushed between replays); returns (ms per step, substeps run)."""
+        torch, args = self.torch, self.args
+        graph = torch.cuda.CUDAGraph()
+        self.stream.synchronize()
+        with torch.cuda.graph(graph, stream=self.stream):
+            self.step(y, prec, False, None)
+        self.stats.zero_()
+        torch.cuda.synchronize()
+        evs = []
+        with torch.cuda.stream(self.stream):
+            for _ in range(args.steps):
+                self.flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                graph.replay()
+                e1.record(self.stream)
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        sub = int(self.stats[:, 0].sum().item())
+        del graph
+        return ms, sub
 
     def step(self, y, prec, first, ev_stage):
         """One MRI slow step through the ABI; CUDA events around each fast stage."""
@@ -248,6 +291,8 @@ class Bench:
             for s in range(args.warmup):
                 self.step(y, prec, s == 0, None)
             self.stream.synchronize()
+            launch = self.autotune(y, prec) if args.autotune else None
+            self.stream.synchronize()
             warm_fail = int(self.nfail.item())
             self.stats.zero_()
             y_start = y.clone()          # the e2e leg replays the timed steps from this state
@@ -277,6 +322,7 @@ class Bench:
         st = self.stats.cpu().numpy().astype(np.int64)
         substeps, newton, njac = int(st[:, 0].sum()), int(st[:, 1].sum()), int(st[:, 2].sum())
         failed = int(self.nfail.item()) - warm_fail
+        graph_ms, graph_sub = self.graph_steps(y_start.clone(), prec) if args.graph else (None, None)
 
         # end to end through the public C-ABI call with host buffers: the same K steps
         # from the same state, each step copying the state in from pinned host memory
@@ -309,7 +355,8 @@ class Bench:
         return dict(prec=prec, total_ms=float(sum(step_ms)), substeps=substeps, newton=newton, njac=njac,
                     failed=failed, clocks=clocks, stage_total_ms=float(np.sum(stage_ms)),
                     stage_launches=3 * args.steps, flops64=f64, flops32=f32, e2e_ms=float(sum(e2e_ms)),
-                    e2e_substeps=e2e_sub, launches=9 * args.steps)
+                    e2e_substeps=e2e_sub, launches=9 * args.steps, launch=launch, graph_ms=graph_ms,
+                    graph_substeps=graph_sub)
 
 
 def cpu_baseline_sample(ncells_sample, seed=0, nthreads=None, repeats=1):
@@ -387,6 +434,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline and the gate (profiling captures)")
     ap.add_argument("--jac", type=int, default=1, help="Newton matrix policy: 0 per substep, 1 lazy")
     ap.add_argument("--prec", type=int, default=None, help="time one form only: 0 plain FP64, 1 mixed precision")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use the automatic launch shape instead of timing the candidates")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="skip the CUDA-graph replay of the step")
     args = ap.parse_args()
     rank, world = dist_init(args)
 
@@ -450,6 +501,7 @@ def main():
                    "jac_policy": ["per-substep", "lazy"][args.jac],
                    "reduced_for_profiling": args.cells_per_side is not None,
                    "l2": "256 MB buffer written between timed steps",
+                   "launch": r["launch"],
                    "newton_per_substep": r["newton"] / max(r["substeps"], 1),
                    "jac_per_substep": r["njac"] / max(r["substeps"], 1), "failed_cells": r["failed"]},
         "clocks": r["clocks"],
@@ -462,6 +514,13 @@ def main():
         "forms": {FORMS[p]: {"value": results[p]["value"], "e2e": results[p]["e2e_value"],
                              "roofline_frac": roofline(results[p])["frac"], "gate": results[p]["gate"],
                              "newton_per_substep": results[p]["newton"] / max(results[p]["substeps"], 1),
+                             "launch": results[p]["launch"] and {k: v for k, v in results[p]["launch"].items()
+                                                                 if k != "autotuned"},
+                             "cuda_graph": None if results[p]["graph_ms"] is None else {
+                                 "value": results[p]["graph_substeps"] / (results[p]["graph_ms"] * 1e-3),
+                                 "ms_per_step": results[p]["graph_ms"] / args.steps,
+                                 "note": "the same MRI step (9 kernels, 3 queue resets) captured once and "
+                                         "replayed; device-timed like value"},
                              "clocks": results[p]["clocks"]} for p in forms},
     }
     print(json.dumps(line))

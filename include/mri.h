@@ -49,6 +49,8 @@ extern "C" {
                               takes no further substeps in this call */
 #define MRI_CELL_EINPUT 2  /* non-finite input state, T <= 0 or p <= 0: the
                               cell is left unchanged */
+#define MRI_CELL_TIMEOUT 3 /* not run: the time budget of the call ran out before a
+                              warp took the cell; the cell is left unchanged */
 
 /* ---- fast integrators ------------------------------------------------ */
 #define MRI_SDIRK2 2       /* Alexander (1977) 2-stage, order 2, L-stable, stiffly accurate */
@@ -106,10 +108,24 @@ typedef struct {
                             replaced by R+1 substeps of sizes hh 2^-R, hh 2^-R,
                             hh 2^(1-R), ..., hh/2 (sum hh), for states far from
                             the fast manifold */
+  /* Launch shape of the persistent kernel (one warp per cell at a time; warps take
+   * cells from a device work queue).  They change the cost only, never a result. */
+  int warps_per_block;   /* 0 = automatic (as many as the shared memory holds, at most
+                            16); else 1..16, rejected (MRI_EINVAL) if they do not fit */
+  int blocks_per_sm;     /* 0 = automatic (1); else 1..8 resident CTAs per SM, each
+                            with 1/blocks_per_sm of the SM's shared memory */
+  double time_budget_s;  /* 0 = none.  > 0: warps stop taking new cells once this much
+                            time has passed since they started (cells already taken
+                            are finished).  The cells not taken are always the tail
+                            [ncell - m, ncell) of the range: they keep their input
+                            state, get status MRI_CELL_TIMEOUT and count in n_failed,
+                            so a caller resumes by calling again on that tail.
+                            mri_step rejects a budget. */
 } mri_fast_opts;
 
 /* Fill opts with the defaults (SDIRK3, rtol 1e-10, atol_Y 1e-20, atol_T 1e-10 K,
- * 10 Newton iterations, per-substep Jacobian, FP64, no ramp). */
+ * 10 Newton iterations, per-substep Jacobian, FP64, no ramp, automatic launch
+ * shape, no time budget). */
 void mri_fast_opts_default(mri_fast_opts* opts);
 
 /* One MRI stage of the fast partition for every cell (Eq. 3):
@@ -137,6 +153,42 @@ int mri_stage_fast(double* y, const double* p, int ncell, const double* phi, int
                    double t0, double Hstage, double h, const mri_mech* mech,
                    const mri_fast_opts* opts, int32_t* cell_status, int32_t* cell_stats,
                    int32_t* n_failed, void* stream);
+
+/* ---- several mechanisms in one launch ------------------------------------ */
+#define MRI_MAX_GROUPS 8
+
+typedef struct {
+  const mri_mech* mech;  /* mechanism of this group's cells (on the current device) */
+  double* y;             /* [ncell][n] in/out, n = that mechanism's Ns + 1 */
+  const double* p;       /* [ncell] */
+  int ncell;             /* >= 0 */
+  const double* phi;     /* [ncell][K][n] or NULL when K == 0 */
+  int K;                 /* 0..4 */
+  int32_t* cell_status;  /* [ncell] or NULL */
+  int32_t* cell_stats;   /* [ncell][4] or NULL, added to */
+} mri_stage_group;
+
+/* mri_stage_fast over up to MRI_MAX_GROUPS groups of cells with different
+ * mechanisms in ONE kernel launch (for example a batch of independent 0-D reactors
+ * on a 9-, a 40- and an 80-species mechanism: K = 0 and no slow partition).  Every
+ * group is integrated exactly as mri_stage_fast integrates it (same Hstage, h and
+ * opts for all groups; the results are bitwise those of one mri_stage_fast call per
+ * group).  The SMs are split between the groups in proportion to an estimate of
+ * their work; each group's CTAs hold its tables and take its cells from its own
+ * queue.  opts->warps_per_block and opts->time_budget_s must be 0 and
+ * opts->blocks_per_sm 0 or 1 (MRI_EINVAL otherwise).  n_failed (nullable) counts
+ * failed cells over all groups.  The paper solves one mechanism at a time; mixing
+ * mechanisms in one launch is a batching service of this library. */
+int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, double t0, double Hstage, double h,
+                         const mri_fast_opts* opts, int32_t* n_failed, void* stream);
+
+/* Launch shape mri_stage_fast would use for ncell cells and K forcing terms with
+ * these options on the current device: warps (= cells in flight) per CTA, CTAs in
+ * the persistent grid and dynamic shared memory per CTA (staged tables plus one
+ * workspace per warp).  A query for autotuning and reports; the paper has no
+ * counterpart.  Returns MRI_EINVAL if the requested shape does not fit. */
+int mri_stage_fast_shape(const mri_mech* mech, const mri_fast_opts* opts, int ncell, int K,
+                         int* warps_per_block, int* blocks, size_t* smem_bytes);
 
 /* ---- slow partition ---------------------------------------------------- */
 typedef struct {
@@ -176,7 +228,8 @@ size_t mri_step_workspace_size(const mri_grid* grid, int n);
  * grid: three f^S evaluations and three fast stages (Sec. 3.2, "MRI3").
  * workspace: device buffer of at least mri_step_workspace_size bytes, owned by
  * the caller and overwritten.  The other arguments are those of
- * mri_stage_fast; opts->ramp applies to the first fast stage only. */
+ * mri_stage_fast; opts->ramp applies to the first fast stage only, and
+ * opts->time_budget_s must be 0 (MRI_EINVAL otherwise). */
 int mri_step(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
              int mri_method, const mri_mech* mech, const mri_fast_opts* opts, void* workspace,
              size_t workspace_bytes, int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed,

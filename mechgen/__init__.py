@@ -342,6 +342,38 @@ MECH_SMALL = dict(n_species=9, n_reactions=21, elements=("H", "O", "N"), n_third
                   max_atoms=4, max_count=[3, 3, 2])
 MECH_MEDIUM = dict(n_species=40, n_reactions=170, elements=("C", "H", "O", "N"), n_thirdbody=12,
                    n_troe=8, max_atoms=6, max_count=[2, 4, 3, 2])
+MECH_LARGE = dict(n_species=80, n_reactions=350, elements=("C", "H", "O", "N"), n_thirdbody=24,
+                  n_troe=16, max_atoms=8, max_count=[3, 6, 3, 2])
+
+
+@dataclasses.dataclass
+class ReactorBatch:
+    """Independent constant-pressure 0-D reactors on several mechanisms, advanced
+    together over one interval Hstage with fast substeps of about h (no slow
+    forcing: K = 0)."""
+    groups: list            # [(Mechanism, y0 [ncell, n], p [ncell])]
+    method: int
+    Hstage: float
+    h: float
+    newton_rtol: float
+    ramp: int
+
+
+def reactor_batch(seed: int = 0, n_reactors: int = 4096, T_range=(1000.0, 2200.0)) -> ReactorBatch:
+    """4096 0-D reactors split evenly over a 9-species / 21-reaction, a 40 / 170 and
+    an 80 / 350 mechanism (the last two with third-body and falloff reactions);
+    T uniform in T_range, p in [0.5, 2] atm, Dirichlet(1) mass fractions."""
+    rng = np.random.default_rng(6000 + seed)
+    specs = [(1000 + seed, MECH_SMALL), (3000 + seed, MECH_MEDIUM), (5000 + seed, MECH_LARGE)]
+    sizes = [n_reactors // 3 + (1 if i < n_reactors % 3 else 0) for i in range(3)]
+    groups = []
+    for (mseed, spec), nc in zip(specs, sizes):
+        mech = make_mechanism(mseed, **spec)
+        Y = _dirichlet(rng, nc, mech.n_species)
+        T = rng.uniform(T_range[0], T_range[1], nc)
+        p = P_ATM * rng.uniform(0.5, 2.0, nc)
+        groups.append((mech, np.ascontiguousarray(np.concatenate([Y, T[:, None]], axis=1)), p))
+    return ReactorBatch(groups, 3, 1e-7, 1e-8, 1e-10, 12)
 
 
 def workload(name: str, seed: int = 0, cells_per_side: int | None = None) -> Workload:

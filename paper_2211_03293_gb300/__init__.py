@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ct.CDLL(LIB_PATH)
 
 MRI_OK, MRI_EINVAL, MRI_ENEWTON, MRI_ECUDA, MRI_ETIMEOUT, MRI_ENOMEM = 0, -1, -2, -3, -4, -5
-MRI_CELL_OK, MRI_CELL_ENEWTON, MRI_CELL_EINPUT = 0, 1, 2
+MRI_CELL_OK, MRI_CELL_ENEWTON, MRI_CELL_EINPUT, MRI_CELL_TIMEOUT = 0, 1, 2, 3
 MRI_SDIRK2, MRI_SDIRK3 = 2, 3
 MRI_KW3 = 1
 MRI_JAC_PER_SUBSTEP = 0
@@ -35,7 +35,16 @@ MRI_PREC_FP32_LU = 1
 class mri_fast_opts(ct.Structure):
     _fields_ = [("method", ct.c_int), ("newton_rtol", ct.c_double), ("newton_atol_Y", ct.c_double),
                 ("newton_atol_T", ct.c_double), ("max_newton", ct.c_int), ("jac_policy", ct.c_int),
-                ("precision", ct.c_int), ("ramp", ct.c_int)]
+                ("precision", ct.c_int), ("ramp", ct.c_int), ("warps_per_block", ct.c_int),
+                ("blocks_per_sm", ct.c_int), ("time_budget_s", ct.c_double)]
+
+
+class mri_stage_group(ct.Structure):
+    _fields_ = [("mech", ct.c_void_p), ("y", ct.c_void_p), ("p", ct.c_void_p), ("ncell", ct.c_int),
+                ("phi", ct.c_void_p), ("K", ct.c_int), ("cell_status", ct.c_void_p), ("cell_stats", ct.c_void_p)]
+
+
+MRI_MAX_GROUPS = 8
 
 
 class mri_grid(ct.Structure):
@@ -54,6 +63,10 @@ _lib.mri_fast_opts_default.argtypes = [ct.POINTER(mri_fast_opts)]
 _lib.mri_fast_opts_default.restype = None
 _lib.mri_stage_fast.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, ct.c_double, ct.c_double, ct.c_double, _vp,
                                 ct.POINTER(mri_fast_opts), _vp, _vp, _vp, _vp]
+_lib.mri_stage_fast_shape.argtypes = [_vp, ct.POINTER(mri_fast_opts), ct.c_int, ct.c_int, ct.POINTER(ct.c_int),
+                                      ct.POINTER(ct.c_int), ct.POINTER(ct.c_size_t)]
+_lib.mri_stage_fast_batch.argtypes = [ct.POINTER(mri_stage_group), ct.c_int, ct.c_double, ct.c_double, ct.c_double,
+                                      ct.POINTER(mri_fast_opts), _vp, _vp]
 _lib.mri_slow_rhs.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, _vp]
 _lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_workspace_size.restype = ct.c_size_t
@@ -75,7 +88,8 @@ _lib.mri_status_str.restype = ct.c_char_p
 EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_default", "mri_stage_fast",
             "mri_slow_rhs", "mri_step_workspace_size", "mri_step", "mri_fast_rhs", "mri_fast_jac",
             "mri_lu_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling",
-            "mri_step_noalloc", "mri_probe_fp64_fma", "mri_probe_exp")
+            "mri_step_noalloc", "mri_probe_fp64_fma", "mri_probe_exp", "mri_stage_fast_shape",
+            "mri_stage_fast_batch")
 
 
 class MriError(RuntimeError):
@@ -169,6 +183,28 @@ def mri_stage_fast(y, p, phi, t0, Hstage, h, mech: Mech, opts: mri_fast_opts, ce
     rc = _lib.mri_stage_fast(_f64(y), _f64(p), ncell, _f64(phi), K, t0, Hstage, h, mech.handle, ct.byref(opts),
                              _i32(cell_status), _i32(cell_stats), _i32(n_failed), _stream(stream))
     return _check(rc, "mri_stage_fast")
+
+
+def mri_stage_fast_batch(groups, t0, Hstage, h, opts: mri_fast_opts, n_failed=None, stream=None) -> int:
+    """One launch over several mechanisms.  groups: sequence of dicts with keys mech
+    (Mech), y, p and optionally phi, cell_status, cell_stats (device tensors)."""
+    arr = (mri_stage_group * len(groups))()
+    for i, g in enumerate(groups):
+        phi = g.get("phi")
+        arr[i] = mri_stage_group(g["mech"].handle, _f64(g["y"]), _f64(g["p"]), g["y"].shape[0], _f64(phi),
+                                 0 if phi is None else phi.shape[1], _i32(g.get("cell_status")),
+                                 _i32(g.get("cell_stats")))
+    rc = _lib.mri_stage_fast_batch(arr, len(groups), t0, Hstage, h, ct.byref(opts), _i32(n_failed), _stream(stream))
+    return _check(rc, "mri_stage_fast_batch")
+
+
+def mri_stage_fast_shape(mech: Mech, opts: mri_fast_opts, ncell: int, K: int):
+    """(warps per CTA, CTAs, shared bytes per CTA) of mri_stage_fast's launch; raises
+    MriError if the requested shape does not fit."""
+    w, b, s = ct.c_int(), ct.c_int(), ct.c_size_t()
+    _check(_lib.mri_stage_fast_shape(mech.handle, ct.byref(opts), ncell, K, ct.byref(w), ct.byref(b), ct.byref(s)),
+           "mri_stage_fast_shape")
+    return w.value, b.value, s.value
 
 
 def mri_slow_rhs(y, fS, g: mri_grid, t=0.0, stream=None) -> int:

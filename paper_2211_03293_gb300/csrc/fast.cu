@@ -9,6 +9,9 @@
 // arithmetic of the state, residual, rates and factorisation is FP64.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "fastmath.cuh"
 #include "internal.cuh"
@@ -117,7 +120,7 @@ __device__ void stage_table(unsigned char* dst, const unsigned char* src, int by
 // ------------------------------------------------------------------ chemistry
 
 struct Scal {        // warp-uniform per-evaluation scalars
-  double T, invT, lnT, S, rho, invrho, Ctot, cpm, Q;
+  double T, invT, lnT, S, invS, rho, invrho, Ctot, cpm, Q;
 };
 
 // dst[k] = sum_r nu_kr src[r] for every species, balanced over the lanes: lane l
@@ -165,9 +168,6 @@ __device__ __forceinline__ void rxn_eval(const Tab& t, const WS& w, int r, doubl
   const double lnkinf = fma(t.b[r], lnT, t.lnA[r]) - t.Ta[r] * invT;
   double kf = exp_tab(lnkinf, t.exp2t);
   if (type == 2) kf *= w.tro[kTroeSlots * tr + 9];
-  // 1 / K_c = prod_reactants E * prod_products 1/E * (p_atm/RT)^(-dn)
-  const double kinv = (w.E[i0] * w.E[i1]) * (w.E[i2] * w.Einv[j0]) * (w.Einv[j1] * w.Einv[j2]) * w.c0p[dn + 2];
-  const double kr = kf * kinv;
   double M = 1.0;
   if (type == 1) {
     const int row = t.rrow[r] & 0xffff;
@@ -175,10 +175,19 @@ __device__ __forceinline__ void rxn_eval(const Tab& t, const WS& w, int r, doubl
     for (int e = t.eptr[row]; e < t.eptr[row + 1]; ++e) M = fma(t.eval[e], w.C[t.eidx[e]], M);
   }
   const double fwd = w.C[i0] * w.C[i1] * w.C[i2];
+  // 1 / K_c = prod_reactants E * prod_products 1/E * (p_atm/RT)^(-dn).  Without the
+  // Jacobian the product factors come premultiplied by their concentrations
+  // (CE_k = C_k / E_k, in the 1/E array), so k_r prod C^nu'' = k_f Er prod CE.
+  const double Er = (w.E[i0] * w.E[i1]) * (w.E[i2] * w.c0p[dn + 2]);
+  if (!JAC) {
+    o.q = M * (kf * fma(-Er, w.Einv[j0] * w.Einv[j1] * w.Einv[j2], fwd));
+    return;
+  }
+  const double kr = kf * (Er * (w.Einv[j0] * w.Einv[j1] * w.Einv[j2]));
   const double rev = w.C[j0] * w.C[j1] * w.C[j2];
   const double base = fma(kf, fwd, -kr * rev);
   o.q = M * base;
-  if (JAC) {
+  {
     double dlnkf_dT = fma(t.Ta[r], invT, t.b[r]) * invT;
     if (type == 2) dlnkf_dT += w.tro[kTroeSlots * tr + 10];
     const double snh = (w.hh[j0] + w.hh[j1] + w.hh[j2]) - (w.hh[i0] + w.hh[i1] + w.hh[i2]);
@@ -209,10 +218,14 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
   double part = 0.0;
   for (int k = lane; k < Ns; k += 32) part = fma(Z[k], t.invW[k], part);
   const double S = warp_sum(part);
-  const double invT = 1.0 / T;
+  // 1/T, 1/S and 1/p in one division: lane 0 inverts T, lane 1 S, lane 2 p
+  const double dv = 1.0 / ((lane == 0) ? T : (lane == 1) ? S : p);
+  const double invT = __shfl_sync(0xffffffffu, dv, 0);
+  const double invS = __shfl_sync(0xffffffffu, dv, 1);
+  const double invp = __shfl_sync(0xffffffffu, dv, 2);
   const double lnT = log(T);
-  const double rho = p / (kRu * T * S);
-  const double invrho = kRu * T * S / p;
+  const double rho = (p * (1.0 / kRu)) * (invT * invS);
+  const double invrho = (kRu * T) * (S * invp);
   double ctot = 0.0;
   for (int k = lane; k < Ns; k += 32) {
     double c = rho * Z[k] * t.invW[k];
@@ -230,7 +243,7 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     w.hh[k] = hv;
     w.g[k] = g;
     w.E[k] = e;
-    w.Einv[k] = 1.0 / e;
+    w.Einv[k] = JAC ? 1.0 / e : c / e;   // 1/E for the Jacobian's k_r, else C/E
   }
   if (lane == 0) { w.C[Ns] = 1.0; w.g[Ns] = 0.0; w.hh[Ns] = 0.0; w.E[Ns] = 1.0; w.Einv[Ns] = 1.0; }
   if (lane < 5) {
@@ -331,7 +344,7 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     qp = fma(w.hh[k], w.wd[k], qp);
     cpp = fma(Z[k] * t.invW[k], w.cp[k], cpp);
   }
-  s.T = T; s.invT = invT; s.lnT = lnT; s.S = S; s.rho = rho; s.invrho = invrho; s.Ctot = Ctot;
+  s.T = T; s.invT = invT; s.lnT = lnT; s.S = S; s.invS = invS; s.rho = rho; s.invrho = invrho; s.Ctot = Ctot;
   s.Q = warp_sum(qp);
   s.cpm = warp_sum(cpp);
   __syncwarp();
@@ -433,7 +446,7 @@ __device__ __forceinline__ void chem_jac(const Tab& t, const WS& w, const double
   const double dQT = warp_sum(dqt);
   const double dCPM = warp_sum(dcpm);
   __syncwarp();
-  const double invS = 1.0 / s.S;
+  const double invS = s.invS;
   const MT inv_rhoS = (MT)(s.invrho * invS);
   const double Phi = T * s.invrho;
   const double invcpm = 1.0 / s.cpm;
@@ -576,6 +589,8 @@ struct StageArgs {
   const unsigned char* table;
   Layout L;
   int ncell, K, n_sub, ramp, max_newton, nstage, sticky, jac_policy, ws_stride;
+  int* queue;            // work-queue counter (zeroed before the launch)
+  unsigned long long budget_ns;   // 0: no time budget
   double Hs, hh, rtol, atol_Y, atol_T;
   double A[3][3], c[3], gamma;
 };
@@ -641,20 +656,39 @@ __device__ __forceinline__ void newton_solve(const WS& w, int n, int lane) {
   }
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Lane 0 takes the next cell from the launch's queue counter, unless the warp's time
+// budget is spent (then ncell: no cell); the index is broadcast to the warp.
+__device__ __forceinline__ int next_cell(const StageArgs& a, unsigned long long t_start, int lane) {
+  int c = a.ncell;
+  if (lane == 0 && (a.budget_ns == 0 || globaltimer_ns() - t_start < a.budget_ns)) c = atomicAdd(a.queue, 1);
+  return __shfl_sync(0xffffffffu, c, 0);
+}
+
+// The cells of one stage launch, for one warp: after the CTA has staged the
+// mechanism tables at smem and the SDIRK tableau at sA / sc, the warp takes cells from
+// the launch's queue and integrates each over the stage (Eq. 3 with the forcing
+// polynomial r_i): n_sub SDIRK substeps (plus the start-up ramp), each stage solved by
+// Newton's method with the factorised matrix I - h gamma J.
 template <bool PREC32>
-__global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double sA[3][3], sc[3];    // SDIRK tableau, indexed by the runtime stage
-  stage_table(smem, a.table, a.L.bytes);
-  if (threadIdx.x < 9) sA[threadIdx.x / 3][threadIdx.x % 3] = a.A[threadIdx.x / 3][threadIdx.x % 3];
-  if (threadIdx.x < 3) sc[threadIdx.x] = a.c[threadIdx.x];
-  __syncthreads();
+__device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* smem, const double (*sA)[3],
+                                            const double* sc, int warp, int lane) {
   const Tab t(smem, a.L);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const WS w(reinterpret_cast<double*>(smem + a.L.bytes) + (size_t)warp * a.ws_stride, a.L, PREC32, a.K);
   const int n = t.n, Ns = t.Ns, S = a.nstage;
   const int total_sub = a.n_sub + (a.ramp > 0 ? a.ramp : 0);
-  for (int cell = blockIdx.x * nw + warp; cell < a.ncell; cell += gridDim.x * nw) {
+  // Persistent warps take cells from a device work queue, so that cells of uneven
+  // stiffness (Newton and Jacobian counts vary severalfold across a front) balance.
+  // With a time budget a warp stops taking cells once it has run that long, so the
+  // cells taken are always a prefix of the range.
+  const unsigned long long t_start = a.budget_ns ? globaltimer_ns() : 0ull;
+  int cell = next_cell(a, t_start, lane);
+  for (; cell < a.ncell; ) {
     double* yc = a.y + (size_t)cell * n;
     const double p = a.p[cell];
     int bad = 0;
@@ -713,10 +747,27 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
         // redone with a fresh Jacobian at the current iterate (a full Newton step;
         // the residual is reused).  Start-up substeps use full Newton throughout.
         // The converged stage value does not depend on the matrix policy.
-        const bool startup = startup_sub;
+        // If Newton fails from the predicted start, the stage is solved once more
+        // with full Newton from the previous stage value (the substep start for the
+        // first stage): far from the fast manifold a large F_prev can throw the
+        // predicted start out of Newton's region of convergence.
+        bool startup = startup_sub;
         bool fresh = (i == 0) && need && !predicted;   // matrix evaluated at the starting iterate
         bool conv = false;
         double prev = 0.0;
+        for (int attempt = 0; attempt < 2 && !conv; ++attempt) {
+        if (attempt == 1) {
+          if (!predicted) break;      // the start was already the previous stage value
+          for (int k = lane; k < n; k += 32) {   // Z_{i-1} = y_n + h sum_{j<i} a_{i-1,j} F_j
+            double z = w.y0[k];
+            for (int j = 0; j < i; ++j) z = fma(hk * sA[i - 1][j], w.F(j)[k], z);
+            w.Z[k] = z;
+          }
+          __syncwarp();
+          startup = true;
+          fresh = false;
+          prev = 0.0;
+        }
         for (int it = 0; it < a.max_newton; ++it) {
           Scal s;
           chem_eval<false>(t, w, w.Z, p, s, lane);
@@ -770,6 +821,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
           }
           prev = nrm;
         }
+        }
         if (!conv) { status = MRI_CELL_ENEWTON; break; }
         double* Fi = (i < S - 1) ? w.F(i) : w.Fl;
         for (int k = lane; k < n; k += 32) Fi[k] = (w.Z[k] - w.base[k]) * inv_hg;
@@ -792,7 +844,55 @@ __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a)
       if (a.n_failed && status != MRI_CELL_OK) atomicAdd(a.n_failed, 1);
     }
     __syncwarp();
+    cell = next_cell(a, t_start, lane);
   }
+}
+
+template <bool PREC32>
+__global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sA[3][3], sc[3];    // SDIRK tableau, indexed by the runtime stage
+  stage_table(smem, a.table, a.L.bytes);
+  if (threadIdx.x < 9) sA[threadIdx.x / 3][threadIdx.x % 3] = a.A[threadIdx.x / 3][threadIdx.x % 3];
+  if (threadIdx.x < 3) sc[threadIdx.x] = a.c[threadIdx.x];
+  __syncthreads();
+  stage_cells<PREC32>(a, smem, sA, sc, threadIdx.x >> 5, threadIdx.x & 31);
+}
+
+// Several mechanisms in one launch: CTAs [block0[g], block0[g+1]) serve group g, each
+// with its own staged tables, workspace layout and queue.  The group's arguments are
+// copied to shared memory so that the hot loop reads them from there.
+struct BatchArgs {
+  StageArgs g[MRI_MAX_GROUPS];
+  int block0[MRI_MAX_GROUPS + 1];
+  int warps[MRI_MAX_GROUPS];
+  int ngroups;
+};
+static_assert(sizeof(BatchArgs) <= 4096, "batch arguments must fit the classic kernel parameter space");
+static_assert(sizeof(StageArgs) + 12 * sizeof(double) <= 1024, "static shared memory of the stage kernels");
+
+template <bool PREC32>
+__global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_batch_kernel(const __grid_constant__ BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sA[3][3], sc[3];
+  __shared__ StageArgs sa;
+  int gi = 0;
+  while (gi + 1 < b.ngroups && (int)blockIdx.x >= b.block0[gi + 1]) ++gi;
+  if (threadIdx.x == 0) sa = b.g[gi];
+  stage_table(smem, b.g[gi].table, b.g[gi].L.bytes);
+  if (threadIdx.x < 9) sA[threadIdx.x / 3][threadIdx.x % 3] = b.g[gi].A[threadIdx.x / 3][threadIdx.x % 3];
+  if (threadIdx.x < 3) sc[threadIdx.x] = b.g[gi].c[threadIdx.x];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp < b.warps[gi]) stage_cells<PREC32>(sa, smem, sA, sc, warp, threadIdx.x & 31);
+}
+
+// Cells the budget left untaken: [min(counter, ncell), ncell).
+__global__ void mark_untaken_kernel(const int* queue, int ncell, int32_t* status, int32_t* n_failed) {
+  const int first = min(*queue, ncell);
+  for (int c = first + blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
+    if (status) status[c] = MRI_CELL_TIMEOUT;
+  if (n_failed && blockIdx.x == 0 && threadIdx.x == 0 && ncell > first) atomicAdd(n_failed, ncell - first);
 }
 
 // ------------------------------------------------------------------ per-kernel entry kernels
@@ -873,19 +973,65 @@ int device_smem_limit() {
   return v > 0 ? v : 48 * 1024;
 }
 
-// Warps per CTA and grid for a warp-per-cell kernel with `per_warp` bytes of workspace.
+// Raise a kernel's dynamic shared memory limit to the device's opt-in maximum, once per
+// kernel and device, so that later launches (also those recorded by a stream capture)
+// make no attribute call.
+static bool allow_full_smem(const void* fn) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done)
+    if (d.first == fn && d.second == dev) return true;
+  // the opt-in limit covers static and dynamic shared memory together
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           device_smem_limit() - (int)fa.sharedSizeBytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  done.emplace_back(fn, dev);
+  return true;
+}
+
+static int device_sm_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  return v > 0 ? v : 48 * 1024;
+}
+
+// Warps per CTA and grid for a warp-per-cell kernel with `per_warp` bytes of workspace
+// after the staged table.  wpb / bps: requested warps per CTA and CTAs per SM (0 =
+// automatic).  The grid is persistent: at most bps CTAs per SM.
 static bool plan_launch(const Layout& L, int ncell, int& warps, int& blocks, size_t& smem, bool prec32 = false,
-                        int K = 0) {
-  const int limit = device_smem_limit();
+                        int K = 0, int wpb = 0, int bps = 0) {
+  constexpr long long kStaticSmem = 1024;    // the kernels' static shared arrays (tableau, batch arguments)
+  constexpr long long kReservedPerCta = 1024;   // shared memory the SM keeps per resident CTA
+  const int per_cta_sm = bps > 0 ? bps : 1;
+  long long cap = device_smem_limit();
+  const long long share = (long long)device_sm_smem() / per_cta_sm - kReservedPerCta;
+  if (share < cap) cap = share;
   const size_t per_warp = (size_t)ws_offsets(L, prec32, K).total * 8;
-  int wmax = (int)((limit - L.bytes) / (long long)per_warp);
-  if (wmax < 1) return false;
+  long long room = cap - kStaticSmem - (long long)L.bytes;
+  int wmax = room > 0 ? (int)(room / (long long)per_warp) : 0;
   if (wmax > kMaxWarps) wmax = kMaxWarps;
-  const int sms = device_sm_count();
-  int want = (ncell + sms - 1) / sms;
-  warps = want < 1 ? 1 : (want > wmax ? wmax : want);
+  if (wmax < 1) return false;
+  const int slots = device_sm_count() * per_cta_sm;
+  if (wpb > 0) {
+    if (wpb > wmax) return false;
+    warps = wpb;
+  } else {
+    int want = (ncell + slots - 1) / slots;
+    warps = want < 1 ? 1 : (want > wmax ? wmax : want);
+  }
   blocks = (ncell + warps - 1) / warps;
-  if (blocks > sms) blocks = sms;
+  if (blocks > slots) blocks = slots;
   if (blocks < 1) blocks = 1;
   smem = (size_t)L.bytes + (size_t)warps * per_warp;
   return true;
@@ -917,11 +1063,11 @@ static void sdirk_table(int method, StageArgs& a) {
   }
 }
 
-int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double Hs, double h,
-                      const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status, int32_t* stats,
-                      int32_t* n_failed, cudaStream_t st, bool sticky) {
-  if (ncell == 0) return MRI_OK;
-  StageArgs a{};
+// Arguments of one stage launch over the cells of one mechanism.
+static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, const double* phi, int K,
+                           double Hs, double h, const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status,
+                           int32_t* stats, int32_t* n_failed, bool sticky) {
+  a = StageArgs{};
   a.sticky = sticky ? 1 : 0;
   a.y = y; a.p = p; a.phi = phi; a.status = status; a.stats = stats; a.n_failed = n_failed;
   a.table = static_cast<const unsigned char*>(m.d_table);
@@ -939,21 +1085,119 @@ int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, 
   a.jac_policy = o.jac_policy;
   a.rtol = o.newton_rtol; a.atol_Y = o.newton_atol_Y; a.atol_T = o.newton_atol_T;
   sdirk_table(o.method, a);
+  a.ws_stride = ws_offsets(m.L, o.precision == MRI_PREC_FP32_LU, K).total;
+  a.budget_ns = o.time_budget_s > 0 ? (unsigned long long)std::ceil(o.time_budget_s * 1e9) : 0ull;
+  return MRI_OK;
+}
+
+// Each launch takes its own counter of the mechanism's ring, so that launches in
+// flight on different streams do not share one (up to kQueueSlots of them); the
+// counter is zeroed in stream order before the launch.
+static int take_queue(const Mech& m, StageArgs& a, cudaStream_t st) {
+  Mech& mm = const_cast<Mech&>(m);
+  a.queue = mm.d_queue + (__atomic_fetch_add(&mm.queue_next, 1u, __ATOMIC_RELAXED) % kQueueSlots);
+  return cudaMemsetAsync(a.queue, 0, sizeof(int), st) == cudaSuccess ? MRI_OK : MRI_ECUDA;
+}
+
+int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double Hs, double h,
+                      const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status, int32_t* stats,
+                      int32_t* n_failed, cudaStream_t st, bool sticky) {
+  if (ncell == 0) return MRI_OK;
+  StageArgs a;
+  int rc = fill_stage_args(a, y, p, ncell, phi, K, Hs, h, m, o, ramp, status, stats, n_failed, sticky);
+  if (rc != MRI_OK) return rc;
   const bool prec32 = (o.precision == MRI_PREC_FP32_LU);
-  a.ws_stride = ws_offsets(m.L, prec32, K).total;
   int warps, blocks;
   size_t smem;
-  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32, K)) return MRI_EINVAL;
+  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32, K, o.warps_per_block, o.blocks_per_sm))
+    return MRI_EINVAL;
+  if ((rc = take_queue(m, a, st)) != MRI_OK) return rc;
   if (prec32) {
-    if (cudaFuncSetAttribute(stage_fast_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return MRI_ECUDA;
+    if (!allow_full_smem((const void*)stage_fast_kernel<true>)) return MRI_ECUDA;
     stage_fast_kernel<true><<<blocks, warps * 32, smem, st>>>(a);
   } else {
-    if (cudaFuncSetAttribute(stage_fast_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return MRI_ECUDA;
+    if (!allow_full_smem((const void*)stage_fast_kernel<false>)) return MRI_ECUDA;
     stage_fast_kernel<false><<<blocks, warps * 32, smem, st>>>(a);
+  }
+  if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
+  if (a.budget_ns) {
+    const int nb = (ncell + 255) / 256 < 1024 ? (ncell + 255) / 256 : 1024;
+    mark_untaken_kernel<<<nb, 256, 0, st>>>(a.queue, ncell, status, n_failed);
+    if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
+  }
+  return MRI_OK;
+}
+
+// Estimated FP64 work per cell-substep of a mechanism, for splitting the SMs of a
+// mixed launch: about ten Newton iterations of rates (~40 flops per reaction) and
+// triangular solves (2 n^2), plus one LU factorisation (2/3 n^3).
+static double cell_cost(const Layout& L) {
+  const double n = L.n, R = L.R;
+  return 10.0 * (40.0 * R + 2.0 * n * n) + (2.0 / 3.0) * n * n * n;
+}
+
+int launch_stage_fast_batch(const mri_stage_group* groups, int ngroups, double Hs, double h, const mri_fast_opts& o,
+                            int32_t* n_failed, cudaStream_t st) {
+  const bool prec32 = (o.precision == MRI_PREC_FP32_LU);
+  BatchArgs b{};
+  int gidx[MRI_MAX_GROUPS];
+  double load[MRI_MAX_GROUPS];
+  int nb = 0, maxw = 1;
+  size_t maxsmem = 0;
+  double total = 0.0;
+  for (int g = 0; g < ngroups; ++g) {
+    const mri_stage_group& G = groups[g];
+    if (G.ncell == 0) continue;
+    const Mech& m = *reinterpret_cast<const Mech*>(G.mech);
+    StageArgs& a = b.g[nb];
+    int rc = fill_stage_args(a, G.y, G.p, G.ncell, G.phi, G.K, Hs, h, m, o, o.ramp, G.cell_status, G.cell_stats,
+                             n_failed, false);
+    if (rc != MRI_OK) return rc;
+    int w, bl;
+    size_t sm;
+    // as many warps as one SM's shared memory holds for this mechanism
+    if (!plan_launch(m.L, 1 << 30, w, bl, sm, prec32, G.K, 0, 1)) return MRI_EINVAL;
+    b.warps[nb] = w;
+    if (w > maxw) maxw = w;
+    if (sm > maxsmem) maxsmem = sm;
+    load[nb] = (double)G.ncell * cell_cost(m.L) / w;
+    total += load[nb];
+    gidx[nb] = g;
+    ++nb;
+  }
+  if (nb == 0) return MRI_OK;
+  // CTAs (one per SM) in proportion to each group's work per warp, at least one each and
+  // no more than its cells need
+  const int sms = device_sm_count();
+  int blocks[MRI_MAX_GROUPS], used = 0;
+  for (int i = 0; i < nb; ++i) {
+    const int cap = (groups[gidx[i]].ncell + b.warps[i] - 1) / b.warps[i];
+    int k = (int)std::floor(load[i] / total * (sms - nb)) + 1;
+    blocks[i] = k < cap ? k : cap;
+    used += blocks[i];
+  }
+  for (bool grew = true; used < sms && grew;) {   // hand out what rounding left, largest load first
+    grew = false;
+    int best = -1;
+    for (int i = 0; i < nb; ++i) {
+      const int cap = (groups[gidx[i]].ncell + b.warps[i] - 1) / b.warps[i];
+      if (blocks[i] < cap && (best < 0 || load[i] / blocks[i] > load[best] / blocks[best])) best = i;
+    }
+    if (best >= 0) { blocks[best]++; used++; grew = true; }
+  }
+  b.ngroups = nb;
+  b.block0[0] = 0;
+  for (int i = 0; i < nb; ++i) b.block0[i + 1] = b.block0[i] + blocks[i];
+  for (int i = 0; i < nb; ++i) {
+    int rc = take_queue(*reinterpret_cast<const Mech*>(groups[gidx[i]].mech), b.g[i], st);
+    if (rc != MRI_OK) return rc;
+  }
+  if (prec32) {
+    if (!allow_full_smem((const void*)stage_fast_batch_kernel<true>)) return MRI_ECUDA;
+    stage_fast_batch_kernel<true><<<b.block0[nb], maxw * 32, maxsmem, st>>>(b);
+  } else {
+    if (!allow_full_smem((const void*)stage_fast_batch_kernel<false>)) return MRI_ECUDA;
+    stage_fast_batch_kernel<false><<<b.block0[nb], maxw * 32, maxsmem, st>>>(b);
   }
   return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
 }
@@ -970,7 +1214,9 @@ bool fast_opts_ok(const mri_fast_opts* o) {
          std::isfinite(o->newton_atol_Y) && std::isfinite(o->newton_atol_T) && o->max_newton >= 1 &&
          o->max_newton <= 100 && (o->jac_policy == MRI_JAC_PER_SUBSTEP || o->jac_policy == MRI_JAC_LAZY) &&
          (o->precision == MRI_PREC_FP64 || o->precision == MRI_PREC_FP32_LU) &&
-         o->ramp >= 0 && o->ramp <= 40;
+         o->ramp >= 0 && o->ramp <= 40 && o->warps_per_block >= 0 && o->warps_per_block <= kMaxWarps &&
+         o->blocks_per_sm >= 0 && o->blocks_per_sm <= 8 && o->time_budget_s >= 0 &&
+         o->time_budget_s <= 1e6;
 }
 
 int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* phi, int K, double Hstage,
@@ -997,6 +1243,9 @@ extern "C" void mri_fast_opts_default(mri_fast_opts* o) {
   o->jac_policy = MRI_JAC_PER_SUBSTEP;
   o->precision = MRI_PREC_FP64;
   o->ramp = 0;
+  o->warps_per_block = 0;
+  o->blocks_per_sm = 0;
+  o->time_budget_s = 0.0;
 }
 
 extern "C" int mri_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double t0,
@@ -1009,6 +1258,38 @@ extern "C" int mri_stage_fast(double* y, const double* p, int ncell, const doubl
                                      cell_status, cell_stats, n_failed, static_cast<cudaStream_t>(stream), false);
 }
 
+extern "C" int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, double t0, double Hstage, double h,
+                                    const mri_fast_opts* opts, int32_t* n_failed, void* stream) {
+  (void)t0;
+  if (!groups || ngroups < 1 || ngroups > MRI_MAX_GROUPS || !mri::fast_opts_ok(opts)) return MRI_EINVAL;
+  if (opts->warps_per_block != 0 || opts->blocks_per_sm > 1 || opts->time_budget_s != 0.0) return MRI_EINVAL;
+  if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MRI_ECUDA;
+  for (int g = 0; g < ngroups; ++g) {
+    const mri_stage_group& G = groups[g];
+    if (!G.mech || G.ncell < 0 || G.K < 0 || G.K > mri::kMaxK) return MRI_EINVAL;
+    if (G.ncell > 0 && (!G.y || !G.p || (G.K > 0 && !G.phi))) return MRI_EINVAL;
+    if (reinterpret_cast<const Mech*>(G.mech)->device != dev) return MRI_EINVAL;
+  }
+  return mri::launch_stage_fast_batch(groups, ngroups, Hstage, h, *opts, n_failed, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int mri_stage_fast_shape(const mri_mech* mech, const mri_fast_opts* opts, int ncell, int K,
+                                    int* warps_per_block, int* blocks, size_t* smem_bytes) {
+  if (!mech || !mri::fast_opts_ok(opts) || ncell < 1 || K < 0 || K > mri::kMaxK) return MRI_EINVAL;
+  const Mech* m = reinterpret_cast<const Mech*>(mech);
+  int w = 0, b = 0;
+  size_t s = 0;
+  if (!mri::plan_launch(m->L, ncell, w, b, s, opts->precision == MRI_PREC_FP32_LU, K, opts->warps_per_block,
+                        opts->blocks_per_sm))
+    return MRI_EINVAL;
+  if (warps_per_block) *warps_per_block = w;
+  if (blocks) *blocks = b;
+  if (smem_bytes) *smem_bytes = s;
+  return MRI_OK;
+}
+
 extern "C" int mri_fast_rhs(const double* y, const double* p, int ncell, const mri_mech* mech, double* f,
                             void* stream) {
   if (!mech || ncell < 0 || (ncell > 0 && (!y || !p || !f))) return MRI_EINVAL;
@@ -1017,8 +1298,7 @@ extern "C" int mri_fast_rhs(const double* y, const double* p, int ncell, const m
   int warps, blocks;
   size_t smem;
   if (!mri::plan_launch(m->L, ncell, warps, blocks, smem)) return MRI_EINVAL;
-  if (cudaFuncSetAttribute(mri::rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return MRI_ECUDA;
+  if (!mri::allow_full_smem((const void*)mri::rhs_kernel)) return MRI_ECUDA;
   mri::rhs_kernel<<<blocks, warps * 32, smem, static_cast<cudaStream_t>(stream)>>>(
       y, p, ncell, f, static_cast<const unsigned char*>(m->d_table), m->L);
   return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
@@ -1032,8 +1312,7 @@ extern "C" int mri_fast_jac(const double* y, const double* p, int ncell, const m
   int warps, blocks;
   size_t smem;
   if (!mri::plan_launch(m->L, ncell, warps, blocks, smem)) return MRI_EINVAL;
-  if (cudaFuncSetAttribute(mri::jac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return MRI_ECUDA;
+  if (!mri::allow_full_smem((const void*)mri::jac_kernel)) return MRI_ECUDA;
   mri::jac_kernel<<<blocks, warps * 32, smem, static_cast<cudaStream_t>(stream)>>>(
       y, p, ncell, J, static_cast<const unsigned char*>(m->d_table), m->L);
   return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
@@ -1052,8 +1331,7 @@ extern "C" int mri_lu_solve_batched(double* A, double* b, int n, int nbatch, int
   const int cap = mri::device_sm_count() * 4;
   if (blocks > cap) blocks = cap;
   const size_t smem = per * warps;
-  if (cudaFuncSetAttribute(mri::lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return MRI_ECUDA;
+  if (!mri::allow_full_smem((const void*)mri::lu_kernel)) return MRI_ECUDA;
   mri::lu_kernel<<<blocks, warps * 32, smem, static_cast<cudaStream_t>(stream)>>>(A, b, n, ld, nbatch, info);
   return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
 }

@@ -63,9 +63,13 @@ struct Layout {
   int ws_doubles32;       // doubles per cell (warp), mixed-precision form, K = kMaxK
 };
 
+constexpr int kQueueSlots = 256;   // work-queue counters per mechanism (one per launch in flight)
+
 struct Mech {             // what mri_mech points at
   Layout L;
   void* d_table = nullptr;   // device copy of the table
+  int* d_queue = nullptr;    // kQueueSlots work-queue counters
+  unsigned queue_next = 0;   // next counter to hand out (round robin)
   int device = -1;
 };
 
@@ -133,10 +137,17 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = f
   w.piv = o; o += nv / 2 + 1;   // int32 pivots
   o = round_up(o, 2);
   w.q = o; o += L.rv;
-  w.kfw = o; o += L.rv;
-  w.krw = o; o += L.rv;
-  w.dqdT = o; o += L.rv;
-  w.tbs = o; o += L.rv;
+  if (prec32 && 4 * L.rv <= w.y0 - w.M) {
+    // mixed form: the FP64 per-reaction Jacobian inputs are dead once their FP32
+    // copies exist, before the FP32 Newton matrix is assembled, so they share its
+    // storage (the previous factorisation is being replaced at that point)
+    w.kfw = w.M; w.krw = w.M + L.rv; w.dqdT = w.M + 2 * L.rv; w.tbs = w.M + 3 * L.rv;
+  } else {
+    w.kfw = o; o += L.rv;
+    w.krw = o; o += L.rv;
+    w.dqdT = o; o += L.rv;
+    w.tbs = o; o += L.rv;
+  }
   w.E = o; o += L.nsv;
   w.Einv = o; o += L.nsv;
   // the Jacobian's DC and column-sum vectors reuse E and 1/E, which only the rate

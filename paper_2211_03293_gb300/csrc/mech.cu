@@ -434,7 +434,13 @@ extern "C" int mri_mech_load(const void* blob, size_t nbytes, mri_mech** out) {
     delete m;
     return MRI_ECUDA;
   }
+  if (cudaMalloc(&m->d_queue, sizeof(int) * mri::kQueueSlots) != cudaSuccess) {
+    cudaFree(m->d_table);
+    delete m;
+    return MRI_ECUDA;
+  }
   if (cudaMemcpy(m->d_table, table.data(), table.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(m->d_queue);
     cudaFree(m->d_table);
     delete m;
     return MRI_ECUDA;
@@ -447,6 +453,7 @@ extern "C" void mri_mech_free(mri_mech* mech) {
   if (!mech) return;
   mri::Mech* m = reinterpret_cast<mri::Mech*>(mech);
   if (m->d_table) cudaFree(m->d_table);
+  if (m->d_queue) cudaFree(m->d_queue);
   delete m;
 }
 

@@ -173,7 +173,7 @@ extern "C" int mri_step(double* y, const double* p, const mri_grid* grid, double
   (void)t;
   if (!mri::grid_ok(grid) || !mech || !opts || !y || !p || mri_method != MRI_KW3) return MRI_EINVAL;
   if (!(H > 0) || !(h > 0) || !std::isfinite(H) || !std::isfinite(h)) return MRI_EINVAL;
-  if (!mri::fast_opts_ok(opts)) return MRI_EINVAL;
+  if (!mri::fast_opts_ok(opts) || opts->time_budget_s != 0.0) return MRI_EINVAL;
   const mri::Mech* m = reinterpret_cast<const mri::Mech*>(mech);
   const int n = m->L.n;
   const size_t need = mri_step_workspace_size(grid, n);

@@ -48,6 +48,7 @@ def test_defaults_and_status_strings(lib):
     o = lib.mri_fast_opts_default()
     assert (o.method, o.newton_rtol, o.newton_atol_Y, o.newton_atol_T, o.max_newton, o.ramp) == (
         3, 1e-10, 1e-20, 1e-10, 10, 0)
+    assert (o.jac_policy, o.precision, o.warps_per_block, o.blocks_per_sm, o.time_budget_s) == (0, 0, 0, 0, 0.0)
     assert lib.mri_status_str(0) == "ok"
     assert "Newton" in lib.mri_status_str(-2)
 
@@ -79,10 +80,25 @@ def test_stage_argument_validation_on_host(lib):
     bad = lib.mri_fast_opts_default(method=4)
     assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, fake, ct.byref(bad), None, None, None,
                             None) == lib.MRI_EINVAL
-    for kw in (dict(max_newton=0), dict(max_newton=101), dict(newton_rtol=0.0), dict(ramp=41), dict(precision=7)):
+    for kw in (dict(max_newton=0), dict(max_newton=101), dict(newton_rtol=0.0), dict(ramp=41), dict(precision=7),
+               dict(warps_per_block=17), dict(warps_per_block=-1), dict(blocks_per_sm=9),
+               dict(time_budget_s=-1.0), dict(time_budget_s=float("nan"))):
         bad = lib.mri_fast_opts_default(**kw)
         assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, fake, ct.byref(bad), None, None, None,
                                 None) == lib.MRI_EINVAL
+    # the mixed-mechanism launch: group count and launch-shape options are checked first
+    grp = (lib.mri_stage_group * 9)()
+    assert L.mri_stage_fast_batch(None, 1, 0.0, 1e-8, 1e-9, ct.byref(o), None, None) == lib.MRI_EINVAL
+    assert L.mri_stage_fast_batch(grp, 0, 0.0, 1e-8, 1e-9, ct.byref(o), None, None) == lib.MRI_EINVAL
+    assert L.mri_stage_fast_batch(grp, 9, 0.0, 1e-8, 1e-9, ct.byref(o), None, None) == lib.MRI_EINVAL
+    for kw in (dict(warps_per_block=2), dict(blocks_per_sm=2), dict(time_budget_s=1.0)):
+        bad = lib.mri_fast_opts_default(**kw)
+        assert L.mri_stage_fast_batch(grp, 1, 0.0, 1e-8, 1e-9, ct.byref(bad), None, None) == lib.MRI_EINVAL
+    # a whole MRI step takes no time budget
+    g = lib.grid(4, 1, 1, 1e-4, (1, 0, 0), 1e-5, 2)
+    budget = lib.mri_fast_opts_default(time_budget_s=1.0)
+    assert L.mri_step(fake, fake, ct.byref(g), 0.0, 1e-7, 1e-9, lib.MRI_KW3, fake, ct.byref(budget), fake,
+                      1 << 30, None, None, None, None) == lib.MRI_EINVAL
     g = lib.grid(4, 1, 1, 1e-4, (1, 0, 0), 1e-5, 3)   # order 3 does not exist
     assert L.mri_slow_rhs(fake, fake, 10, ct.byref(g), 0.0, None) == lib.MRI_EINVAL
     assert L.mri_lu_solve_batched(fake, fake, 0, 1, None, None) == lib.MRI_EINVAL

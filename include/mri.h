@@ -154,6 +154,34 @@ int mri_stage_fast(double* y, const double* p, int ncell, const double* phi, int
                    const mri_fast_opts* opts, int32_t* cell_status, int32_t* cell_stats,
                    int32_t* n_failed, void* stream);
 
+/* ---- Newton starts and the learned form's guess ---------------------------- */
+#define MRI_START_PREDICTOR 0   /* base + h gamma F_prev once a stage derivative is known,
+                                   else the previous stage value (mri_stage_fast) */
+#define MRI_START_PREVIOUS 1    /* always the previous stage value (y_n for the first stage) */
+#define MRI_START_GUESS 2       /* the caller's predicted states at the substep ends,
+                                   interpolated linearly to the stage's time */
+#define MRI_START_GUESS_FIRST 3 /* the guess where the predictor has no derivative yet
+                                   (the first SDIRK stage of the call), else the predictor */
+
+/* mri_stage_fast with a chosen start for every Newton iteration and, for the
+ * MRI_START_GUESS modes, predicted states guess [ncell][guess_steps][n] (device)
+ * at the ends of the call's substeps: guess_steps must equal the call's substep
+ * count n_sub = max(1, ceil(Hstage/h (1 - 1e-12))).  The Newton start of an SDIRK
+ * stage at time theta in substep j (theta/hh - j = f in [0, 1)) is
+ * (1 - f) guess[j-1] + f guess[j], with guess[-1] the input state (for example
+ * the learned form's prediction, mri_mlp.h).  The start changes the
+ * Newton path, not the stage equations: every stage value is still accepted only
+ * by the FP64 residual and WRMS test, and where Newton does not converge from the
+ * chosen start the stage is solved again with full Newton from the previous stage
+ * value; n_fallback (device int32, nullable, added to) counts those restarts.  The
+ * paper's explicit fast methods need no Newton start; this is part of the learned
+ * form.  Other arguments, results and codes as mri_stage_fast. */
+int mri_stage_fast_guided(double* y, const double* p, int ncell, const double* phi, int K, double t0,
+                          double Hstage, double h, const double* guess, int guess_steps, int start,
+                          const mri_mech* mech,
+                          const mri_fast_opts* opts, int32_t* cell_status, int32_t* cell_stats,
+                          int32_t* n_failed, int32_t* n_fallback, void* stream);
+
 /* ---- several mechanisms in one launch ------------------------------------ */
 #define MRI_MAX_GROUPS 8
 

@@ -22,6 +22,11 @@ int mri_probe_fp64_fma(double* scratch, long long scratch_doubles, int iters, do
  * so that its accuracy can be checked against libm.  Returns 0, -1 or -3. */
 int mri_probe_exp(const double* x, double* y, long long n, void* stream);
 
+/* The FP64 natural logarithm the rate kernels use (table-driven, after Tang,
+ * 1990, see fastmath.cuh), y[i] = log(x[i]) on the device, for the same check.
+ * Returns 0, -1 or -3. */
+int mri_probe_log(const double* x, double* y, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ MRI_JAC_PER_SUBSTEP = 0
 MRI_JAC_LAZY = 1
 MRI_PREC_FP64 = 0
 MRI_PREC_FP32_LU = 1
+MRI_START_PREDICTOR, MRI_START_PREVIOUS, MRI_START_GUESS, MRI_START_GUESS_FIRST = 0, 1, 2, 3
 
 
 class mri_fast_opts(ct.Structure):
@@ -67,6 +68,26 @@ _lib.mri_stage_fast_shape.argtypes = [_vp, ct.POINTER(mri_fast_opts), ct.c_int, 
                                       ct.POINTER(ct.c_int), ct.POINTER(ct.c_size_t)]
 _lib.mri_stage_fast_batch.argtypes = [ct.POINTER(mri_stage_group), ct.c_int, ct.c_double, ct.c_double, ct.c_double,
                                       ct.POINTER(mri_fast_opts), _vp, _vp]
+_lib.mri_mlp_create.argtypes = [ct.POINTER(ct.c_int), ct.c_int, ct.c_int, _vp, ct.POINTER(_vp)]
+_lib.mri_mlp_free.argtypes = [_vp]
+_lib.mri_mlp_free.restype = None
+_lib.mri_mlp_num_params.argtypes = [_vp]
+_lib.mri_mlp_num_params.restype = ct.c_longlong
+_lib.mri_mlp_params.argtypes = [_vp, _vp, _vp]
+_lib.mri_mlp_forward.argtypes = [_vp, _vp, ct.c_int, _vp, _vp]
+_lib.mri_mlp_grad.argtypes = [_vp, _vp, _vp, _vp, ct.c_int, _vp, _vp, _vp]
+_lib.mri_mlp_grad_copy.argtypes = [_vp, _vp, _vp]
+_lib.mri_mlp_adam.argtypes = [_vp, ct.c_float, ct.c_int, _vp]
+_lib.mri_mlp_status.argtypes = [_vp]
+_lib.mri_gemm_bf16.argtypes = [_vp, ct.c_int, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _vp, ct.c_int, _vp, _vp]
+_lib.mri_stage_fast_guided.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, ct.c_double, ct.c_double, ct.c_double,
+                                       _vp, ct.c_int, ct.c_int, _vp, ct.POINTER(mri_fast_opts), _vp, _vp, _vp, _vp,
+                                       _vp]
+_lib.mri_learned_features.argtypes = [_vp, _vp, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_double, _vp, _vp, _vp,
+                                      ct.c_int, _vp]
+_lib.mri_learned_targets.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, ct.c_int, _vp]
+_lib.mri_learned_guess.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, _vp]
+_lib.mri_probe_log.argtypes = [_vp, _vp, ct.c_longlong, _vp]
 _lib.mri_slow_rhs.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, _vp]
 _lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_workspace_size.restype = ct.c_size_t
@@ -89,7 +110,10 @@ EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_de
             "mri_slow_rhs", "mri_step_workspace_size", "mri_step", "mri_fast_rhs", "mri_fast_jac",
             "mri_lu_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling",
             "mri_step_noalloc", "mri_probe_fp64_fma", "mri_probe_exp", "mri_stage_fast_shape",
-            "mri_stage_fast_batch")
+            "mri_stage_fast_batch", "mri_mlp_create", "mri_mlp_free", "mri_mlp_num_params", "mri_mlp_params",
+            "mri_mlp_forward", "mri_mlp_grad", "mri_mlp_grad_copy", "mri_mlp_adam", "mri_mlp_status",
+            "mri_gemm_bf16", "mri_stage_fast_guided", "mri_learned_features", "mri_learned_targets",
+            "mri_learned_guess", "mri_probe_log")
 
 
 class MriError(RuntimeError):
@@ -185,6 +209,19 @@ def mri_stage_fast(y, p, phi, t0, Hstage, h, mech: Mech, opts: mri_fast_opts, ce
     return _check(rc, "mri_stage_fast")
 
 
+def mri_stage_fast_guided(y, p, phi, t0, Hstage, h, mech: Mech, opts: mri_fast_opts, start=MRI_START_PREDICTOR,
+                          guess=None, cell_status=None, cell_stats=None, n_failed=None, n_fallback=None,
+                          stream=None) -> int:
+    """mri_stage_fast with a chosen Newton start; guess: [ncell][n_sub][n] float64 (MRI_START_GUESS*)."""
+    ncell = y.shape[0]
+    K = 0 if phi is None else phi.shape[1]
+    G = 0 if guess is None else guess.shape[1]
+    rc = _lib.mri_stage_fast_guided(_f64(y), _f64(p), ncell, _f64(phi), K, t0, Hstage, h, _f64(guess), G, start,
+                                    mech.handle, ct.byref(opts), _i32(cell_status), _i32(cell_stats), _i32(n_failed),
+                                    _i32(n_fallback), _stream(stream))
+    return _check(rc, "mri_stage_fast_guided")
+
+
 def mri_stage_fast_batch(groups, t0, Hstage, h, opts: mri_fast_opts, n_failed=None, stream=None) -> int:
     """One launch over several mechanisms.  groups: sequence of dicts with keys mech
     (Mech), y, p and optionally phi, cell_status, cell_stats (device tensors)."""
@@ -266,6 +303,14 @@ def mri_probe_exp(x, y, stream=None) -> int:
     return rc
 
 
+def mri_probe_log(x, y, stream=None) -> int:
+    """y = log(x) with the kernels' own FP64 logarithm (float64 device tensors)."""
+    rc = _lib.mri_probe_log(_f64(x), _f64(y), x.numel(), _stream(stream))
+    if rc != 0:
+        raise MriError(rc, "mri_probe_log")
+    return rc
+
+
 def mri_fast_rhs(y, p, mech: Mech, f, stream=None) -> int:
     return _check(_lib.mri_fast_rhs(_f64(y), _f64(p), y.shape[0], mech.handle, _f64(f), _stream(stream)),
                   "mri_fast_rhs")
@@ -279,3 +324,111 @@ def mri_fast_jac(y, p, mech: Mech, J, stream=None) -> int:
 def mri_lu_solve_batched(A, b, info=None, stream=None) -> int:
     return _check(_lib.mri_lu_solve_batched(_f64(A), _f64(b), A.shape[-1], A.shape[0], _i32(info), _stream(stream)),
                   "mri_lu_solve_batched")
+
+
+# ----------------------------------------------------------------------------- learned form
+
+def _f32(t):
+    import torch
+    if t is not None and t.dtype != torch.float32:
+        raise TypeError("float32 tensor expected")
+    return _ptr(t)
+
+
+def _bf16(t):
+    import torch
+    if t is not None and t.dtype != torch.bfloat16:
+        raise TypeError("bfloat16 tensor expected")
+    return _ptr(t)
+
+
+class Mlp:
+    """Owner of an ``mri_mlp`` handle: network parameters, Adam state and scratch."""
+
+    def __init__(self, dims, batch_max, init_params=None):
+        import numpy as np
+        d = (ct.c_int * len(dims))(*dims)
+        h = _vp()
+        buf = None
+        if init_params is not None:
+            buf = np.ascontiguousarray(init_params, dtype=np.float32)
+        rc = _lib.mri_mlp_create(d, len(dims) - 1, batch_max,
+                                 None if buf is None else buf.ctypes.data_as(_vp), ct.byref(h))
+        _check(rc, "mri_mlp_create")
+        self.handle, self.dims, self.batch_max = h, list(dims), batch_max
+        self.n_params = _lib.mri_mlp_num_params(h)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.mri_mlp_free(h)
+            self.handle = None
+
+
+def mri_mlp_create(dims, batch_max, init_params=None) -> Mlp:
+    return Mlp(dims, batch_max, init_params)
+
+
+def mri_mlp_free(mlp: Mlp) -> None:
+    mlp.__del__()
+
+
+def mri_mlp_num_params(mlp: Mlp) -> int:
+    return int(_lib.mri_mlp_num_params(mlp.handle))
+
+
+def mri_mlp_params(mlp: Mlp, new=None):
+    """The FP32 master parameters (numpy copy); with ``new``, replace them after copying."""
+    import numpy as np
+    out = np.empty(mlp.n_params, dtype=np.float32)
+    src = None if new is None else np.ascontiguousarray(new, dtype=np.float32)
+    _check(_lib.mri_mlp_params(mlp.handle, out.ctypes.data_as(_vp), None if src is None else src.ctypes.data_as(_vp)),
+           "mri_mlp_params")
+    return out
+
+
+def mri_mlp_forward(mlp: Mlp, x, y, stream=None) -> int:
+    return _check(_lib.mri_mlp_forward(mlp.handle, _f32(x), x.shape[0], _f32(y), _stream(stream)), "mri_mlp_forward")
+
+
+def mri_mlp_grad(mlp: Mlp, x, t, w_out, y, loss=None, stream=None) -> int:
+    return _check(_lib.mri_mlp_grad(mlp.handle, _f32(x), _f32(t), _f32(w_out), x.shape[0], _f32(y), _f32(loss),
+                                    _stream(stream)), "mri_mlp_grad")
+
+
+def mri_mlp_grad_copy(mlp: Mlp, dst, stream=None) -> int:
+    return _check(_lib.mri_mlp_grad_copy(mlp.handle, _f32(dst), _stream(stream)), "mri_mlp_grad_copy")
+
+
+def mri_mlp_adam(mlp: Mlp, lr, step, stream=None) -> int:
+    return _check(_lib.mri_mlp_adam(mlp.handle, float(lr), int(step), _stream(stream)), "mri_mlp_adam")
+
+
+def mri_mlp_status(mlp: Mlp) -> int:
+    return int(_lib.mri_mlp_status(mlp.handle))
+
+
+def mri_gemm_bf16(A, B, C, err, stream=None) -> int:
+    """C [M][N] fp32 = A [M][K] bf16 @ B [N][K]^T (bf16); err: int32 device flag."""
+    M, K = A.shape
+    N = B.shape[0]
+    return _check(_lib.mri_gemm_bf16(_bf16(A), A.stride(0), _bf16(B), B.stride(0), M, N, K, _f32(C), C.stride(0),
+                                     _i32(err), _stream(stream)), "mri_gemm_bf16")
+
+
+def mri_learned_features(y, p, phi, Hstage, mean, inv_std, x, stream=None) -> int:
+    K = 0 if phi is None else phi.shape[1]
+    return _check(_lib.mri_learned_features(_f64(y), _f64(p), _f64(phi), K, y.shape[0], y.shape[1], Hstage, _f32(mean),
+                                            _f32(inv_std), _f32(x), x.shape[1], _stream(stream)),
+                  "mri_learned_features")
+
+
+def mri_learned_targets(y_in, y_seq, tmean, tinv_std, t, stream=None) -> int:
+    return _check(_lib.mri_learned_targets(_f64(y_in), _f64(y_seq), y_seq.shape[1], y_in.shape[0], y_in.shape[1],
+                                           _f32(tmean), _f32(tinv_std), _f32(t), t.shape[1], _stream(stream)),
+                  "mri_learned_targets")
+
+
+def mri_learned_guess(y_in, yhat, G, tmean, tstd, guess, stream=None) -> int:
+    return _check(_lib.mri_learned_guess(_f64(y_in), _f32(yhat), yhat.shape[1], G, y_in.shape[0], y_in.shape[1],
+                                         _f32(tmean), _f32(tstd), _f64(guess), _stream(stream)), "mri_learned_guess")

@@ -21,7 +21,7 @@ namespace mri {
 // ------------------------------------------------------------------ views
 
 struct Tab {
-  const double *cp, *hh, *ss, *h5, *s6, *dcp, *W, *invW, *lnA, *b, *Ta, *eval, *troe, *nu, *exp2t, *tcv;
+  const double *cp, *hh, *ss, *h5, *s6, *dcp, *W, *invW, *lnA, *b, *Ta, *eval, *troe, *nu, *exp2t, *logt, *tcv;
   const float *nu32, *W32, *invW32, *dcp32, *tcv32;
   const uint64_t *rxn, *cent, *rsp;
   const int32_t *rrow, *eptr, *eidx, *cptr, *tbl, *trx, *tcptr, *tcr, *gent, *gsptr, *gslot;
@@ -42,6 +42,7 @@ struct Tab {
     troe = reinterpret_cast<const double*>(s + L.o_troe);
     nu = reinterpret_cast<const double*>(s + L.o_nu) + 3;   // nu[v] for v in -3..4
     exp2t = reinterpret_cast<const double*>(s + L.o_exp2);
+    logt = reinterpret_cast<const double*>(s + L.o_logt);
     nu32 = reinterpret_cast<const float*>(s + L.o_nu32) + 3;
     W32 = reinterpret_cast<const float*>(s + L.o_W32);
     invW32 = reinterpret_cast<const float*>(s + L.o_invW32);
@@ -223,7 +224,7 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
   const double invT = __shfl_sync(0xffffffffu, dv, 0);
   const double invS = __shfl_sync(0xffffffffu, dv, 1);
   const double invp = __shfl_sync(0xffffffffu, dv, 2);
-  const double lnT = log(T);
+  const double lnT = log_tab(T, t.logt);
   const double rho = (p * (1.0 / kRu)) * (invT * invS);
   const double invrho = (kRu * T) * (S * invp);
   double ctot = 0.0;
@@ -283,7 +284,7 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
       x = fma(1.0 - tp[3], q[1], fma(tp[3], q[2], q[3]));
       q[6] = x;
     }
-    q[7 + kind] = log10(x);   // q[7] = log10 Fc, q[8] = log10 Pr
+    q[7 + kind] = log_tab(x, t.logt) * (1.0 / kLn10);   // q[7] = log10 Fc, q[8] = log10 Pr
   }
   __syncwarp();
   // falloff, phase 3: broadening F, factor Pr/(1+Pr) F, and its derivatives
@@ -294,14 +295,21 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     const double nn = fma(-1.27, logFc, 0.75);
     const double u = q[8] + c;
     const double den = fma(-0.14, u, nn);
-    const double invden = 1.0 / den;
-    const double f1 = u * invden;
-    const double g1 = fma(f1, f1, 1.0);
-    const double invg = 1.0 / g1;
-    const double logF = logFc * invg;
-    const double invPr1 = 1.0 / (1.0 + Pr);
-    q[9] = Pr * invPr1 * exp_tab(logF * kLn10, t.exp2t);
-    if (JAC) {
+    if (!JAC) {
+      // log F = log Fc den^2 / (den^2 + u^2) and the factor Pr/(1+Pr) F, with one
+      // division for both quotients
+      const double d2 = den * den, s2 = fma(u, u, d2), P1 = 1.0 + Pr;
+      const double inv = 1.0 / (s2 * P1);
+      const double logF = (logFc * d2) * (P1 * inv);
+      q[9] = (Pr * s2) * inv * exp_tab(logF * kLn10, t.exp2t);
+    } else {
+      const double invden = 1.0 / den;
+      const double f1 = u * invden;
+      const double g1 = fma(f1, f1, 1.0);
+      const double invg = 1.0 / g1;
+      const double logF = logFc * invg;
+      const double invPr1 = 1.0 / (1.0 + Pr);
+      q[9] = Pr * invPr1 * exp_tab(logF * kLn10, t.exp2t);
       const int r = t.trx[tr];
       const double* tp = t.troe + 8 * tr;
       const double dlnkinf_dT = fma(t.Ta[r], invT, t.b[r]) * invT;
@@ -590,6 +598,9 @@ struct StageArgs {
   Layout L;
   int ncell, K, n_sub, ramp, max_newton, nstage, sticky, jac_policy, ws_stride;
   int* queue;            // work-queue counter (zeroed before the launch)
+  const double* guess;   // [ncell][n_sub][n] predicted substep ends (MRI_START_GUESS*), else null
+  int start;             // MRI_START_*
+  int32_t* n_fallback;   // counts Newton restarts from the previous stage value (nullable)
   unsigned long long budget_ns;   // 0: no time budget
   double Hs, hh, rtol, atol_Y, atol_T;
   double A[3][3], c[3], gamma;
@@ -611,15 +622,24 @@ __device__ __forceinline__ void substep_geometry(int s, int ramp, double hh, dou
 }
 
 // WRMS norm of the Newton correction d with weights from the updated iterate Z + d.
+// The norm only steers the iteration (a tolerance test and contraction-rate
+// estimates), so it is formed in FP32 from the FP64 vectors: 1e-7 relative on a
+// number compared with 1.  Corrections beyond the FP32 range give Inf, which the
+// iteration treats like an FP64 overflow.
 __device__ __forceinline__ double wrms_update(const double* d, const double* Z, int n, double rtol, double atolY, double atolT,
                               int lane) {
-  double acc = 0.0;
+  float acc = 0.0f;
+  const float rt = (float)rtol, aY = (float)atolY, aT = (float)atolT;
   for (int k = lane; k < n; k += 32) {
-    const double wgt = fma(rtol, fabs(Z[k] + d[k]), (k == n - 1) ? atolT : atolY);
-    const double v = d[k] / wgt;
-    acc = fma(v, v, acc);
+    const float dk = (float)d[k];
+    const float wgt = fmaf(rt, fabsf((float)Z[k] + dk), (k == n - 1) ? aT : aY);
+    const float v = dk / wgt;
+    acc = fmaf(v, v, acc);
   }
-  return sqrt(warp_sum(acc) / n);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  const double nrm = (double)sqrtf(acc / (float)n);
+  return isnan(nrm) ? (double)INFINITY : nrm;
 }
 
 // Jacobian at Z, M = I - hg J, LU.  Returns the LU info (0 = ok).  PREC32: the
@@ -726,10 +746,21 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
       }
       for (int i = 0; i < S && status == MRI_CELL_OK; ++i) {
         const double rh = (tau + sc[i] * hk) / a.Hs;
-        // Newton starts from base + h gamma F_prev, F_prev being the derivative of the
-        // previous stage (of the previous substep for the first stage): the stage
-        // equation with the new derivative replaced by the last one known.
-        const bool predicted = (i > 0) || have_Fl;
+        // Start of Newton (a.start):
+        //  MRI_START_PREDICTOR: base + h gamma F_prev, F_prev being the derivative of
+        //    the previous stage (of the previous substep for the first stage): the
+        //    stage equation with the new derivative replaced by the last one known;
+        //    the previous stage value while no derivative is known yet;
+        //  MRI_START_PREVIOUS: the previous stage value (y_n for the first stage);
+        //  MRI_START_GUESS: the caller's predicted stage output interpolated to the
+        //    stage time, y_in + rhohat (guess - y_in);
+        //  MRI_START_GUESS_FIRST: the guess where the predictor has no derivative.
+        int src;   // 0 predictor, 1 previous stage value, 2 guess
+        if (a.start == MRI_START_PREVIOUS) src = 1;
+        else if (a.start == MRI_START_GUESS) src = 2;
+        else if ((i > 0) || have_Fl) src = 0;
+        else src = (a.start == MRI_START_GUESS_FIRST) ? 2 : 1;
+        const bool predicted = (src != 1);
         const double* Fp = (i > 0) ? w.F(i - 1) : w.Fl;
         for (int k = lane; k < n; k += 32) {
           double rv = 0.0;
@@ -738,7 +769,21 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
           double bs = w.y0[k];
           for (int j = 0; j < i; ++j) bs = fma(hk * sA[i][j], w.F(j)[k], bs);
           w.base[k] = bs;   // stage base y_n + h sum_j a_ij F_j
-          w.Z[k] = predicted ? fma(hg, Fp[k], bs) : bs;
+          double z;
+          if (src == 0) {
+            z = fma(hg, Fp[k], bs);
+          } else if (src == 1) {        // Z_{i-1} = y_n + h sum_{j<i} a_{i-1,j} F_j
+            z = w.y0[k];
+            for (int j = 0; j < i; ++j) z = fma(hk * sA[i - 1][j], w.F(j)[k], z);
+          } else {                      // between the predicted substep ends j-1 and j
+            const double th = (tau + sc[i] * hk) / a.hh;
+            int j = (int)th;
+            if (j > a.n_sub - 1) j = a.n_sub - 1;
+            const double* gc = a.guess + (size_t)cell * a.n_sub * n;
+            const double lo = (j == 0) ? yc[k] : gc[(size_t)(j - 1) * n + k];
+            z = fma(th - (double)j, gc[(size_t)j * n + k] - lo, lo);
+          }
+          w.Z[k] = z;
         }
         __syncwarp();
         // Modified Newton: the matrix of the substep start is reused while it
@@ -752,12 +797,13 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
         // first stage): far from the fast manifold a large F_prev can throw the
         // predicted start out of Newton's region of convergence.
         bool startup = startup_sub;
-        bool fresh = (i == 0) && need && !predicted;   // matrix evaluated at the starting iterate
+        bool fresh = (i == 0) && need && !predicted;   // matrix evaluated at the starting iterate (y_n)
         bool conv = false;
         double prev = 0.0;
         for (int attempt = 0; attempt < 2 && !conv; ++attempt) {
         if (attempt == 1) {
           if (!predicted) break;      // the start was already the previous stage value
+          if (a.n_fallback && lane == 0) atomicAdd(a.n_fallback, 1);
           for (int k = lane; k < n; k += 32) {   // Z_{i-1} = y_n + h sum_{j<i} a_{i-1,j} F_j
             double z = w.y0[k];
             for (int j = 0; j < i; ++j) z = fma(hk * sA[i - 1][j], w.F(j)[k], z);
@@ -815,7 +861,9 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
           // with an older matrix converges linearly with rate rho = nrm / prev; its
           // remaining error is about rho * nrm, which must also be small, so that the
           // accepted iterate matches the exact stage solution far inside the tolerance.
-          if (full_step ? (nrm <= 1.0) : (it > 0 && nrm <= 1.0 && nrm * (nrm / prev) <= kNewtonSafety)) {
+          // (a correction that is exactly zero has nothing left to converge)
+          if (nrm == 0.0 ||
+              (full_step ? (nrm <= 1.0) : (it > 0 && nrm <= 1.0 && nrm * (nrm / prev) <= kNewtonSafety))) {
             conv = true;
             break;
           }
@@ -1101,11 +1149,15 @@ static int take_queue(const Mech& m, StageArgs& a, cudaStream_t st) {
 
 int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double Hs, double h,
                       const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status, int32_t* stats,
-                      int32_t* n_failed, cudaStream_t st, bool sticky) {
+                      int32_t* n_failed, cudaStream_t st, bool sticky, const double* guess, int start,
+                      int32_t* n_fallback) {
   if (ncell == 0) return MRI_OK;
   StageArgs a;
   int rc = fill_stage_args(a, y, p, ncell, phi, K, Hs, h, m, o, ramp, status, stats, n_failed, sticky);
   if (rc != MRI_OK) return rc;
+  a.guess = guess;
+  a.start = start;
+  a.n_fallback = n_fallback;
   const bool prec32 = (o.precision == MRI_PREC_FP32_LU);
   int warps, blocks;
   size_t smem;
@@ -1256,6 +1308,25 @@ extern "C" int mri_stage_fast(double* y, const double* p, int ncell, const doubl
   if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
   return mri::mri_stage_fast_checked(y, p, ncell, phi, K, Hstage, h, *reinterpret_cast<const Mech*>(mech), *opts,
                                      cell_status, cell_stats, n_failed, static_cast<cudaStream_t>(stream), false);
+}
+
+extern "C" int mri_stage_fast_guided(double* y, const double* p, int ncell, const double* phi, int K, double t0,
+                                     double Hstage, double h, const double* guess, int guess_steps, int start,
+                                     const mri_mech* mech, const mri_fast_opts* opts, int32_t* cell_status,
+                                     int32_t* cell_stats, int32_t* n_failed, int32_t* n_fallback, void* stream) {
+  (void)t0;
+  if (!mech || !mri::fast_opts_ok(opts) || ncell < 0 || K < 0 || K > mri::kMaxK) return MRI_EINVAL;
+  if (start < MRI_START_PREDICTOR || start > MRI_START_GUESS_FIRST) return MRI_EINVAL;
+  if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
+  if (start == MRI_START_GUESS || start == MRI_START_GUESS_FIRST) {
+    double nsub = std::ceil(Hstage / h * (1.0 - 1e-12));
+    if (!(nsub >= 1.0)) nsub = 1.0;
+    if (ncell > 0 && (!guess || (double)guess_steps != nsub)) return MRI_EINVAL;
+  }
+  if (ncell > 0 && (!y || !p || (K > 0 && !phi))) return MRI_EINVAL;
+  return mri::launch_stage_fast(y, p, ncell, phi, K, Hstage, h, *reinterpret_cast<const Mech*>(mech), *opts,
+                                opts->ramp, cell_status, cell_stats, n_failed, static_cast<cudaStream_t>(stream),
+                                false, guess, start, n_fallback);
 }
 
 extern "C" int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, double t0, double Hstage, double h,

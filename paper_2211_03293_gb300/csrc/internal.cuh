@@ -50,6 +50,7 @@ struct Layout {
   int o_tcv, o_tcv32;     // double / float [ntc]: alpha_rl - 1
   int o_trx;              // int32 [n_troe]: reaction index of each falloff row
   int o_exp2;             // double [32]: 2^(j/32), the table of the exponential (fastmath.cuh)
+  int o_logt;             // double [260]: 1/F, log F, ln2 split: the table of the logarithm (fastmath.cuh)
   int o_nu;               // double [8]: the small integers -3..4 as doubles (index v + 3), so kernels
                           // turn stoichiometric integers into doubles with a load, not a conversion
   // FP32 copies of the constants the mixed-precision Jacobian reads
@@ -174,7 +175,8 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = f
 // launch helpers implemented in fast.cu / slow.cu
 int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double Hs, double h,
                       const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status, int32_t* stats,
-                      int32_t* n_failed, cudaStream_t st, bool sticky);
+                      int32_t* n_failed, cudaStream_t st, bool sticky, const double* guess = nullptr,
+                      int start = MRI_START_PREDICTOR, int32_t* n_fallback = nullptr);
 bool fast_opts_ok(const mri_fast_opts* o);
 // mri_stage_fast after the pointer checks; sticky = write only failing statuses
 int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* phi, int K, double Hstage,

@@ -6,6 +6,7 @@
 #include <new>
 #include <vector>
 
+#include "fastmath.cuh"
 #include "internal.cuh"
 
 namespace mri {
@@ -268,6 +269,7 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
   L.o_tcv32 = S.add((ntc + 1) * 4);
   L.o_trx = S.add((size_t)(B.n_troe > 0 ? B.n_troe : 1) * 4);
   L.o_exp2 = S.add(32 * 8);
+  L.o_logt = S.add(kLogTabDoubles * 8);
   L.o_nu = S.add(8 * 8);
   L.o_nu32 = S.add(8 * 4);
   L.o_W32 = S.add(nsv * 4);
@@ -395,6 +397,7 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
     if (B.rtype[r] == 2) trx[B.troe_row[r]] = r;
   double* e2 = S.at<double>(L.o_exp2);
   for (int j = 0; j < 32; ++j) e2[j] = (double)std::exp2l((long double)j / 32.0L);
+  fill_log_table(S.at<double>(L.o_logt));
   double* nu = S.at<double>(L.o_nu);
   for (int i = 0; i < 8; ++i) nu[i] = (double)(i - 3);
   float* nu32 = S.at<float>(L.o_nu32);

@@ -33,7 +33,30 @@ __global__ void exp_probe_kernel(const double* x, double* y, long long n, Exp2Ta
     y[i] = mri::exp_tab(x[i], s);
 }
 
+struct LogTable {
+  double v[mri::kLogTabDoubles];
+};
+
+__global__ void log_probe_kernel(const double* x, double* y, long long n, LogTable tab) {
+  __shared__ double s[mri::kLogTabDoubles];
+  for (int i = threadIdx.x; i < mri::kLogTabDoubles; i += blockDim.x) s[i] = tab.v[i];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = mri::log_tab(x[i], s);
+}
+
 }  // namespace
+
+extern "C" int mri_probe_log(const double* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return -1;
+  if (n == 0) return 0;
+  LogTable tab;
+  mri::fill_log_table(tab.v);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  log_probe_kernel<<<(int)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n, tab);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
 
 extern "C" int mri_probe_exp(const double* x, double* y, long long n, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return -1;

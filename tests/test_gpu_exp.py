@@ -1,6 +1,7 @@
-"""Accuracy of the kernels' own FP64 exponential (table-driven, after Tang 1989)
-against libm on the host: at most 1 ulp on the ranges the rates use, and the
-library exp's results (overflow, underflow, NaN) outside |x| < 700."""
+"""Accuracy of the kernels' own FP64 exponential and logarithm (table-driven,
+after Tang 1989 and 1990) against libm on the host: at most 1 ulp (exp) and 2 ulp
+(log, 1 ulp before the last rounding) on the ranges the rates use, and the library's results for the special
+arguments each hands to the library function."""
 import numpy as np
 import pytest
 
@@ -32,6 +33,35 @@ def test_exp_special_arguments(mri):
     mri.mri_probe_exp(xd, yd)
     y = yd.cpu().numpy()
     ref = torch.exp(xd).cpu().numpy()
+    np.testing.assert_array_equal(np.isnan(y), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    np.testing.assert_array_equal(y[ok], ref[ok])
+
+
+def test_log_accuracy(mri):
+    import torch
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(200.0, 6000.0, 200000), 10.0 ** rng.uniform(-300, 300, 200000),
+                        rng.uniform(0.99, 1.01, 100000), rng.uniform(1.0, 2.0, 100000),
+                        [1.0, 2.0, 0.5, 1.0 + 2 ** -52, 1.0 - 2 ** -53, 1.5, 3.0, 1e300, 2.3e-308, 1000.0]])
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.empty_like(xd)
+    mri.mri_probe_log(xd, yd)
+    y = yd.cpu().numpy()
+    ref = np.log(x)
+    nz = ref != 0
+    assert ulp_err(y[nz], ref[nz]).max() <= 2.0
+    assert np.all(y[~nz] == 0.0)
+
+
+def test_log_special_arguments(mri):
+    import torch
+    x = np.array([0.0, -0.0, -1.0, 1e-310, 4.9e-324, np.inf, -np.inf, np.nan])
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.empty_like(xd)
+    mri.mri_probe_log(xd, yd)
+    y = yd.cpu().numpy()
+    ref = torch.log(xd).cpu().numpy()
     np.testing.assert_array_equal(np.isnan(y), np.isnan(ref))
     ok = ~np.isnan(ref)
     np.testing.assert_array_equal(y[ok], ref[ok])

@@ -47,7 +47,8 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS_NOMINAL = FP64_DFMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ * 1e6 / 1e12
 # nominal cost of one exp or log in the algorithmic flop count
 FLOPS_PER_TRANSCENDENTAL = 20.0
-FORMS = {0: "plain FP64", 1: "mixed: FP32 Newton matrix and LU, FP64 rates, residual and update"}
+FORMS = {0: "plain FP64", 1: "mixed: FP32 Newton matrix and LU, FP64 rates, residual and update",
+         2: "learned: mixed form with Newton started from a bf16 MLP's prediction where the predictor has none"}
 
 
 # ----------------------------------------------------------------------------- flop model
@@ -192,6 +193,7 @@ class Bench:
         self.stats = torch.zeros((self.ncell, 4), dtype=torch.int32, device=dev)
         self.status = torch.zeros(self.ncell, dtype=torch.int32, device=dev)
         self.nfail = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.nfallback = torch.zeros(1, dtype=torch.int32, device=dev)
         self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)    # 256 MB > 129 MB L2
         probe = torch.empty(N_SM * 8 * 256 * 4, dtype=torch.float64, device=dev)
         self.fp64_peak_tflops = 2.0 * mri.mri_probe_fp64_fma(probe, iters=4096) / 1e12
@@ -247,32 +249,79 @@ class Bench:
         del graph
         return ms, sub
 
-    def step(self, y, prec, first, ev_stage):
-        """One MRI slow step through the ABI; CUDA events around each fast stage."""
+    def step(self, y, prec, first, ev_stage, model=None):
+        """One MRI slow step through the ABI; CUDA events around each fast stage.
+        With a learned model every stage first evaluates the network (features,
+        forward pass, guess) and starts Newton from its guess where the analytic
+        predictor has no derivative yet."""
         mri, c, G, w = self.mri, self.c, self.G, self.w
         for i in range(1, 4):
             mri.mri_slow_rhs(y, self.fS[i - 1], self.grid, stream=self.stream)
             mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=self.stream)
             o = self.opts(prec, w.ramp if (first and i == 1) else 0)
+            Hs = (c[i] - c[i - 1]) * w.H
+            if model is not None:
+                guess = model.guess(y, self.p, self.phi, Hs, w.h, stream=self.stream)
             if ev_stage is not None:
                 ev_stage[i - 1][0].record(self.stream)
-            mri.mri_stage_fast(y, self.p, self.phi, 0.0, (c[i] - c[i - 1]) * w.H, w.h, self.mech, o,
-                               cell_status=self.status, cell_stats=self.stats, n_failed=self.nfail,
-                               stream=self.stream)
+            if model is None:
+                mri.mri_stage_fast(y, self.p, self.phi, 0.0, Hs, w.h, self.mech, o, cell_status=self.status,
+                                   cell_stats=self.stats, n_failed=self.nfail, stream=self.stream)
+            else:
+                mri.mri_stage_fast_guided(y, self.p, self.phi, 0.0, Hs, w.h, self.mech, o,
+                                          start=mri.MRI_START_GUESS_FIRST, guess=guess, cell_status=self.status,
+                                          cell_stats=self.stats, n_failed=self.nfail, n_fallback=self.nfallback,
+                                          stream=self.stream)
             if ev_stage is not None:
                 ev_stage[i - 1][1].record(self.stream)
 
-    def gate(self, prec):
+    def train_learned(self, prec):
+        """The learned form's network, trained by the library's kernels on the
+        substep-end states the plain solver produces over the first MRI steps of the
+        workload (the start-up step excluded).  Returns (model, training report)."""
+        from paper_2211_03293_gb300.learned import LearnedStart, stage_substep_states
+        torch, mri, c, G, w, args = self.torch, self.mri, self.c, self.G, self.w, self.args
+        t0 = time.time()
+        model = LearnedStart(self.n, g_max=5, batch=4096, infer_batch=self.ncell)
+        y = torch.tensor(w.y0, device=self.dev)
+        with torch.cuda.stream(self.stream):
+            for s in range(1 + args.learn_steps):
+                for i in range(1, 4):
+                    mri.mri_slow_rhs(y, self.fS[i - 1], self.grid, stream=self.stream)
+                    mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=self.stream)
+                    Hs = (c[i] - c[i - 1]) * w.H
+                    o = self.opts(prec, w.ramp if (s == 0 and i == 1) else 0)
+                    y_in = y.clone()
+                    seq, _ = stage_substep_states(y, self.p, self.phi, Hs, w.h, self.mech, o, stream=self.stream)
+                    if s > 0:
+                        model.add(y_in, self.p, self.phi.clone(), Hs, seq)
+            torch.cuda.synchronize()
+            t_data = time.time() - t0
+            hist = model.fit(epochs=args.learn_epochs, lr=2e-3, stream=self.stream)
+        torch.cuda.synchronize()
+        rep = {"examples": int(sum(r[0].shape[0] for r in model.records)), "epochs": args.learn_epochs,
+               "loss_first": hist[0], "loss_last": hist[-1], "data_s": round(t_data, 2),
+               "train_s": round(time.time() - t0 - t_data, 2), "network": model.dims,
+               "start": "MRI_START_GUESS_FIRST (network where the analytic predictor has no derivative yet)"}
+        return model, rep
+
+    def gate(self, prec, model=None):
         """Relative error of the first fast stage of the full-size workload (forcing
-        f^S(y0) from the oracle) on 32 sampled cells against the CPU oracle."""
+        f^S(y0) from the oracle) on 32 sampled cells against the CPU oracle, with the
+        maximum and RMS per field (mass fractions above 1e-10, and T)."""
         import oracle
         torch, mri, w = self.torch, self.mri, self.w
         fS = oracle.slow_rhs(w.y0, w.grid)
         y = torch.tensor(w.y0, device=self.dev)
         ph = torch.tensor(fS[:, None, :].copy(), device=self.dev)
         with torch.cuda.stream(self.stream):
-            mri.mri_stage_fast(y, self.p, ph, 0.0, w.H / 3, w.h, self.mech, self.opts(prec, w.ramp),
-                               stream=self.stream)
+            if model is None:
+                mri.mri_stage_fast(y, self.p, ph, 0.0, w.H / 3, w.h, self.mech, self.opts(prec, w.ramp),
+                                   stream=self.stream)
+            else:
+                guess = model.guess(y, self.p, ph, w.H / 3, w.h, stream=self.stream)
+                mri.mri_stage_fast_guided(y, self.p, ph, 0.0, w.H / 3, w.h, self.mech, self.opts(prec, w.ramp),
+                                          start=mri.MRI_START_GUESS_FIRST, guess=guess, stream=self.stream)
         self.stream.synchronize()
         rng = np.random.default_rng(11)
         idx = np.sort(rng.choice(self.ncell, min(32, self.ncell), replace=False))
@@ -281,20 +330,34 @@ class Bench:
         got = y.cpu().numpy()[idx]
         scale = np.abs(ref)
         scale[:, :-1] = np.maximum(scale[:, :-1], 1e-10)
-        err = float(np.max(np.abs(got - ref) / scale))
-        return {"cells": int(len(idx)), "max_rel_err": err, "tolerance": GATE_TOL, "passed": err <= GATE_TOL}
+        rel = np.abs(got - ref) / scale
+        err = float(np.max(rel))
+        big = ref[:, :-1] > 1e-10
+        ry, rt = rel[:, :-1][big], rel[:, -1]
+        fields = {"Y_max": float(ry.max()), "Y_rms": float(np.sqrt(np.mean(ry ** 2))), "T_max": float(rt.max()),
+                  "T_rms": float(np.sqrt(np.mean(rt ** 2)))}
+        return {"cells": int(len(idx)), "max_rel_err": err, "tolerance": GATE_TOL, "passed": err <= GATE_TOL,
+                "per_field": fields}
 
-    def run_form(self, prec):
+    def run_form(self, form):
+        """Time one form: 0 plain FP64, 1 mixed precision, 2 learned start on the mixed
+        form (network inference inside the timed steps)."""
         torch, mri, args, w = self.torch, self.mri, self.args, self.w
+        prec = 1 if form == 2 else form
+        model, learn = self.train_learned(prec) if form == 2 else (None, None)
         y = torch.tensor(w.y0, device=self.dev)
         with torch.cuda.stream(self.stream):
             for s in range(args.warmup):
-                self.step(y, prec, s == 0, None)
+                self.step(y, prec, s == 0, None, model)
             self.stream.synchronize()
-            launch = self.autotune(y, prec) if args.autotune else None
+            launch = self.autotune(y, prec) if (args.autotune and form != 2) else None
+            if form == 2 and args.autotune and prec in self.shape:
+                launch = {"warps_per_block": self.shape[prec][0], "blocks_per_sm": max(self.shape[prec][1], 1),
+                          "autotuned": "shape of the mixed form"}
             self.stream.synchronize()
             warm_fail = int(self.nfail.item())
             self.stats.zero_()
+            self.nfallback.zero_()
             y_start = y.clone()          # the e2e leg replays the timed steps from this state
             step_events, stage_events = [], []
             if self.world > 1:
@@ -309,7 +372,7 @@ class Bench:
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                       for _ in range(3)]
                 e0.record(self.stream)
-                self.step(y, prec, args.warmup == 0 and s == 0, ev)
+                self.step(y, prec, args.warmup == 0 and s == 0, ev, model)
                 e1.record(self.stream)
                 step_events.append((e0, e1))
                 stage_events.append(ev)
@@ -322,7 +385,9 @@ class Bench:
         st = self.stats.cpu().numpy().astype(np.int64)
         substeps, newton, njac = int(st[:, 0].sum()), int(st[:, 1].sum()), int(st[:, 2].sum())
         failed = int(self.nfail.item()) - warm_fail
-        graph_ms, graph_sub = self.graph_steps(y_start.clone(), prec) if args.graph else (None, None)
+        fallbacks = int(self.nfallback.item())
+        graph_ms, graph_sub = (self.graph_steps(y_start.clone(), prec) if (args.graph and form != 2)
+                               else (None, None))
 
         # end to end through the public C-ABI call with host buffers: the same K steps
         # from the same state, each step copying the state in from pinned host memory
@@ -343,8 +408,13 @@ class Bench:
                 e0.record(self.stream)
                 y.copy_(y_host, non_blocking=True)
                 self.p.copy_(p_host, non_blocking=True)
-                mri.mri_step(y, self.p, self.grid, s * w.H, w.H, w.h, self.mech, self.opts(prec), ws,
-                             cell_stats=e2e_stats, stream=self.stream)
+                if model is None:
+                    mri.mri_step(y, self.p, self.grid, s * w.H, w.H, w.h, self.mech, self.opts(prec), ws,
+                                 cell_stats=e2e_stats, stream=self.stream)
+                else:
+                    saved, self.stats = self.stats, e2e_stats
+                    self.step(y, prec, False, None, model)
+                    self.stats = saved
                 y_host.copy_(y, non_blocking=True)
                 e1.record(self.stream)
                 e1.synchronize()
@@ -352,11 +422,14 @@ class Bench:
         e2e_sub = int(e2e_stats[:, 0].sum().item())
         fm = flop_model(w.mech)
         f64, f32 = algorithmic_flops(fm, newton, njac, prec)
-        return dict(prec=prec, total_ms=float(sum(step_ms)), substeps=substeps, newton=newton, njac=njac,
-                    failed=failed, clocks=clocks, stage_total_ms=float(np.sum(stage_ms)),
+        # kernels per step: 3 x (stencil, forcing, stage) [+ 3 x (features, input conversion,
+        # 4 GEMMs, guess) for the learned form]
+        per_step = 9 + (18 if model is not None else 0)
+        return dict(prec=prec, form=form, total_ms=float(sum(step_ms)), substeps=substeps, newton=newton,
+                    njac=njac, failed=failed, clocks=clocks, stage_total_ms=float(np.sum(stage_ms)),
                     stage_launches=3 * args.steps, flops64=f64, flops32=f32, e2e_ms=float(sum(e2e_ms)),
-                    e2e_substeps=e2e_sub, launches=9 * args.steps, launch=launch, graph_ms=graph_ms,
-                    graph_substeps=graph_sub)
+                    e2e_substeps=e2e_sub, launches=per_step * args.steps, launch=launch, graph_ms=graph_ms,
+                    graph_substeps=graph_sub, model=model, learn=learn, fallbacks=fallbacks)
 
 
 def cpu_baseline_sample(ncells_sample, seed=0, nthreads=None, repeats=1):
@@ -433,7 +506,11 @@ def main():
                     help="shrink the box (profiling captures only; the bench line is for 32^3)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline and the gate (profiling captures)")
     ap.add_argument("--jac", type=int, default=1, help="Newton matrix policy: 0 per substep, 1 lazy")
-    ap.add_argument("--prec", type=int, default=None, help="time one form only: 0 plain FP64, 1 mixed precision")
+    ap.add_argument("--prec", type=int, default=None,
+                    help="time one form only: 0 plain FP64, 1 mixed precision, 2 learned start (mixed)")
+    ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip the learned form")
+    ap.add_argument("--learn-steps", type=int, default=3, help="MRI steps of training data for the learned form")
+    ap.add_argument("--learn-epochs", type=int, default=40, help="training epochs of the learned form")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the automatic launch shape instead of timing the candidates")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
@@ -448,7 +525,7 @@ def main():
 
     import torch
     b = Bench(args, world)
-    forms = [args.prec] if args.prec is not None else [0, 1]
+    forms = [args.prec] if args.prec is not None else ([0, 1, 2] if args.learned else [0, 1])
     results = {}
     for prec in forms:
         r = b.run_form(prec)
@@ -460,7 +537,8 @@ def main():
         t, work = t.cpu().numpy(), work.cpu().numpy()
         r["value"] = work[0] / (t[0] * 1e-3)
         r["e2e_value"] = work[1] / (t[1] * 1e-3)
-        r["gate"] = None if (args.no_cpu or rank != 0) else b.gate(prec)
+        r["gate"] = None if (args.no_cpu or rank != 0) else b.gate(r["prec"], r["model"])
+        r["model"] = None
         results[prec] = r
     if rank != 0:
         return
@@ -493,7 +571,7 @@ def main():
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head == 0 else "f64+f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 1: "f64+f32", 2: "f64+f32+bf16"}[head], "data": "synthetic",
         "config": {"workload": "box32: 32^3 periodic box, 40 species / 170 reactions (12 third-body, 8 Troe), "
                                "MRI3 (Knoth-Wolke MIS) + SDIRK3 fast, H = 5e-8 s, h = H/10, Newton rtol 1e-10, "
                                "4th-order slow stencil; one step = one MRI slow step",
@@ -514,8 +592,12 @@ def main():
         "forms": {FORMS[p]: {"value": results[p]["value"], "e2e": results[p]["e2e_value"],
                              "roofline_frac": roofline(results[p])["frac"], "gate": results[p]["gate"],
                              "newton_per_substep": results[p]["newton"] / max(results[p]["substeps"], 1),
+                             "jac_per_substep": results[p]["njac"] / max(results[p]["substeps"], 1),
                              "launch": results[p]["launch"] and {k: v for k, v in results[p]["launch"].items()
                                                                  if k != "autotuned"},
+                             "learned": results[p]["learn"] and dict(
+                                 results[p]["learn"], newton_fallbacks=results[p]["fallbacks"],
+                                 accept_rate=1.0 - results[p]["fallbacks"] / max(3 * results[p]["substeps"], 1)),
                              "cuda_graph": None if results[p]["graph_ms"] is None else {
                                  "value": results[p]["graph_substeps"] / (results[p]["graph_ms"] * 1e-3),
                                  "ms_per_step": results[p]["graph_ms"] / args.steps,

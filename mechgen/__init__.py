@@ -382,7 +382,9 @@ def workload(name: str, seed: int = 0, cells_per_side: int | None = None) -> Wor
     steps.  ``box32``: 32^3 periodic box, 40 species / 170 reactions (12
     third-body, 8 falloff), 4th-order slow stencil, SDIRK3, Newton tolerance
     1e-10, H = 5e-8 s, h = H/10, 20 slow steps (``cells_per_side`` shrinks it for
-    tests).  ``box64``: the same at 64^3."""
+    tests).  ``box64``: the same at 64^3.  ``front128``: the same mechanism and
+    method on a 128^3 box with a planar flame front in x (300 -> 2300 K, width 8
+    cells), where the per-cell Newton and Jacobian counts vary widely."""
     if name == "line64":
         mech = make_mechanism(1000 + seed, **MECH_SMALL)
         nx = cells_per_side or 64
@@ -390,6 +392,13 @@ def workload(name: str, seed: int = 0, cells_per_side: int | None = None) -> Wor
         y0, p = field_1d_tanh(2000 + seed, nx, mech.n_species, dx)
         grid = dict(nx=nx, ny=1, nz=1, dx=dx, u=(1.0, 0.0, 0.0), D=1e-5, order=2)
         return Workload(name, mech, y0, p, grid, 2, 1e-7, 1e-9, 10, 1e-10, 10)
+    if name == "front128":
+        mech = make_mechanism(3000 + seed, **MECH_MEDIUM)
+        m = cells_per_side or 128
+        dx = 1e-4
+        y0, p = field_3d_front(5000 + seed, m, m, m, mech.n_species, dx)
+        grid = dict(nx=m, ny=m, nz=m, dx=dx, u=(1.0, 1.0, 1.0), D=1e-5, order=4)
+        return Workload(name, mech, y0, p, grid, 3, 5e-8, 5e-9, 20, 1e-10, 16)
     if name in ("box32", "box64"):
         mech = make_mechanism(3000 + seed, **MECH_MEDIUM)
         m = cells_per_side or (32 if name == "box32" else 64)

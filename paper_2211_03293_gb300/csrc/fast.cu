@@ -725,6 +725,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
     double M_hg = 0.0;     // h gamma of the factorised Newton matrix (0: none yet)
     int M_age = 0;         // substeps since its Jacobian was evaluated
     bool have_Fl = false;  // w.Fl holds the last stage derivative of the previous substep
+    double hk_prev = 0.0;  // size of the previous substep
     for (int sidx = 0; sidx < total_sub && status == MRI_CELL_OK; ++sidx) {
       double tau, hk;
       substep_geometry(sidx, a.ramp, a.hh, tau, hk);
@@ -747,10 +748,11 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
       for (int i = 0; i < S && status == MRI_CELL_OK; ++i) {
         const double rh = (tau + sc[i] * hk) / a.Hs;
         // Start of Newton (a.start):
-        //  MRI_START_PREDICTOR: base + h gamma F_prev, F_prev being the derivative of
-        //    the previous stage (of the previous substep for the first stage): the
-        //    stage equation with the new derivative replaced by the last one known;
-        //    the previous stage value while no derivative is known yet;
+        //  MRI_START_PREDICTOR: base + h gamma F_pred, the stage equation with the new
+        //    stage derivative replaced by its linear extrapolation in time from the
+        //    last two known ones (the last one alone where only one is known; the
+        //    previous substep's for the first stage); the previous stage value while
+        //    no derivative is known yet;
         //  MRI_START_PREVIOUS: the previous stage value (y_n for the first stage);
         //  MRI_START_GUESS: the caller's predicted stage output interpolated to the
         //    stage time, y_in + rhohat (guess - y_in);
@@ -762,6 +764,23 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
         else src = (a.start == MRI_START_GUESS_FIRST) ? 2 : 1;
         const bool predicted = (src != 1);
         const double* Fp = (i > 0) ? w.F(i - 1) : w.Fl;
+        // second point of the extrapolation and its weight: F_pred = Fp + coef (Fp - Fq).
+        // For the first stage the previous substep's second-to-last stage derivative
+        // (still in F(S-2)) serves when that substep had the same size; for the second
+        // stage the derivative at the substep start, Fl; then the two stages before.
+        // Start-up substeps keep the last derivative alone: far from the fast manifold
+        // the extrapolated start can lead Newton to another root of the stage equation.
+        const double* Fq = nullptr;
+        double coef = 0.0;
+        if (startup_sub) {
+        } else if (i == 0) {
+          if (have_Fl && hk == hk_prev && S >= 2) { Fq = w.F(S - 2); coef = sc[0] / (1.0 - sc[S - 2]); }
+        } else if (i == 1) {
+          if (have_Fl) { Fq = w.Fl; coef = (sc[1] - sc[0]) / sc[0]; }
+        } else {
+          Fq = w.F(i - 2);
+          coef = (sc[i] - sc[i - 1]) / (sc[i - 1] - sc[i - 2]);
+        }
         for (int k = lane; k < n; k += 32) {
           double rv = 0.0;
           for (int j = a.K - 1; j >= 0; --j) rv = fma(rv, rh, w.phi[j * w.nv + k]);
@@ -771,7 +790,8 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
           w.base[k] = bs;   // stage base y_n + h sum_j a_ij F_j
           double z;
           if (src == 0) {
-            z = fma(hg, Fp[k], bs);
+            const double fp = Fp[k];
+            z = fma(hg, Fq ? fma(coef, fp - Fq[k], fp) : fp, bs);
           } else if (src == 1) {        // Z_{i-1} = y_n + h sum_{j<i} a_{i-1,j} F_j
             z = w.y0[k];
             for (int j = 0; j < i; ++j) z = fma(hk * sA[i - 1][j], w.F(j)[k], z);
@@ -879,6 +899,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
       for (int k = lane; k < n; k += 32) w.y0[k] = w.Z[k];
       __syncwarp();
       have_Fl = true;
+      hk_prev = hk;
       nsub++;
     }
     if (status != MRI_CELL_EINPUT)

@@ -51,9 +51,10 @@ class LearnedStart:
     """Network (inputs 2n + 2 features, 3 x 256 SiLU, outputs g_max n substep-end
     increments) with the standardisation of its inputs and outputs."""
 
-    def __init__(self, n, g_max, hidden=256, layers=3, batch=4096, seed=0):
+    def __init__(self, n, g_max, hidden=256, layers=3, batch=4096, seed=0, infer_batch=None):
         import torch
         self.n, self.g_max, self.batch = n, g_max, batch
+        self.infer_batch = infer_batch or batch
         self.n_in = _pad16(2 * n + 2)
         self.n_out = _pad16(g_max * n)
         self.dims = [self.n_in] + [hidden] * layers + [self.n_out]
@@ -62,7 +63,7 @@ class LearnedStart:
         for i, o in zip(self.dims[:-1], self.dims[1:]):
             params.append(rng.standard_normal((o, i)).astype(np.float32).ravel() * np.float32(np.sqrt(1.0 / i)))
             params.append(np.zeros(o, dtype=np.float32))
-        self.net = Mlp(self.dims, batch, np.concatenate(params))
+        self.net = Mlp(self.dims, max(batch, self.infer_batch), np.concatenate(params))
         dev = torch.device("cuda")
         f32 = dict(dtype=torch.float32, device=dev)
         self.fmean = torch.zeros(self.n_in, **f32)
@@ -155,10 +156,13 @@ class LearnedStart:
         G = n_substeps(Hstage, h)
         dev = y_in.device
         out = torch.empty((ncell, G, self.n), dtype=torch.float64, device=dev)
-        x = torch.empty((min(ncell, self.batch), self.n_in), dtype=torch.float32, device=dev)
-        yh = torch.empty((min(ncell, self.batch), self.n_out), dtype=torch.float32, device=dev)
-        for c0 in range(0, ncell, self.batch):
-            c1 = min(ncell, c0 + self.batch)
+        chunk = min(ncell, self.infer_batch)
+        if getattr(self, "_xbuf", None) is None or self._xbuf.shape[0] < chunk:
+            self._xbuf = torch.empty((chunk, self.n_in), dtype=torch.float32, device=dev)
+            self._ybuf = torch.empty((chunk, self.n_out), dtype=torch.float32, device=dev)
+        x, yh = self._xbuf, self._ybuf
+        for c0 in range(0, ncell, chunk):
+            c1 = min(ncell, c0 + chunk)
             m = c1 - c0
             ph = None if phi is None else phi[c0:c1]
             mri_learned_features(y_in[c0:c1], p[c0:c1], ph, Hstage, self.fmean, self.finv, x[:m], stream=stream)

@@ -111,7 +111,7 @@ typedef struct {
   /* Launch shape of the persistent kernel (one warp per cell at a time; warps take
    * cells from a device work queue).  They change the cost only, never a result. */
   int warps_per_block;   /* 0 = automatic (as many as the shared memory holds, at most
-                            16); else 1..16, rejected (MRI_EINVAL) if they do not fit */
+                            12); else 1..12, rejected (MRI_EINVAL) if they do not fit */
   int blocks_per_sm;     /* 0 = automatic (1); else 1..8 resident CTAs per SM, each
                             with 1/blocks_per_sm of the SM's shared memory */
   double time_budget_s;  /* 0 = none.  > 0: warps stop taking new cells once this much

@@ -22,6 +22,11 @@ int mri_probe_fp64_fma(double* scratch, long long scratch_doubles, int iters, do
  * so that its accuracy can be checked against libm.  Returns 0, -1 or -3. */
 int mri_probe_exp(const double* x, double* y, long long n, void* stream);
 
+/* exp(x) and exp(-x) from one argument reduction, as the rate kernels form the
+ * species factors exp(-g/RT) and their inverses: y[i] = exp(x[i]), z[i] =
+ * exp(-x[i]).  Returns 0, -1 or -3. */
+int mri_probe_exp_pair(const double* x, double* y, double* z, long long n, void* stream);
+
 /* The FP64 natural logarithm the rate kernels use (table-driven, after Tang,
  * 1990, see fastmath.cuh), y[i] = log(x[i]) on the device, for the same check.
  * Returns 0, -1 or -3. */

@@ -88,6 +88,7 @@ _lib.mri_learned_features.argtypes = [_vp, _vp, _vp, ct.c_int, ct.c_int, ct.c_in
 _lib.mri_learned_targets.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, ct.c_int, _vp]
 _lib.mri_learned_guess.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, _vp]
 _lib.mri_probe_log.argtypes = [_vp, _vp, ct.c_longlong, _vp]
+_lib.mri_probe_exp_pair.argtypes = [_vp, _vp, _vp, ct.c_longlong, _vp]
 _lib.mri_slow_rhs.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, _vp]
 _lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_workspace_size.restype = ct.c_size_t
@@ -113,7 +114,7 @@ EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_de
             "mri_stage_fast_batch", "mri_mlp_create", "mri_mlp_free", "mri_mlp_num_params", "mri_mlp_params",
             "mri_mlp_forward", "mri_mlp_grad", "mri_mlp_grad_copy", "mri_mlp_adam", "mri_mlp_status",
             "mri_gemm_bf16", "mri_stage_fast_guided", "mri_learned_features", "mri_learned_targets",
-            "mri_learned_guess", "mri_probe_log")
+            "mri_learned_guess", "mri_probe_log", "mri_probe_exp_pair")
 
 
 class MriError(RuntimeError):
@@ -300,6 +301,14 @@ def mri_probe_exp(x, y, stream=None) -> int:
     rc = _lib.mri_probe_exp(_f64(x), _f64(y), x.numel(), _stream(stream))
     if rc != 0:
         raise MriError(rc, "mri_probe_exp")
+    return rc
+
+
+def mri_probe_exp_pair(x, y, z, stream=None) -> int:
+    """y = exp(x), z = exp(-x) from the kernels' shared argument reduction."""
+    rc = _lib.mri_probe_exp_pair(_f64(x), _f64(y), _f64(z), x.numel(), _stream(stream))
+    if rc != 0:
+        raise MriError(rc, "mri_probe_exp_pair")
     return rc
 
 

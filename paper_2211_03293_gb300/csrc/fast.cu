@@ -121,7 +121,7 @@ __device__ void stage_table(unsigned char* dst, const unsigned char* src, int by
 // ------------------------------------------------------------------ chemistry
 
 struct Scal {        // warp-uniform per-evaluation scalars
-  double T, invT, lnT, S, invS, rho, invrho, Ctot, cpm, Q;
+  double T, invT, lnT, S, invS, rho, invrho, Ctot, cpm, invcpm, Q;
 };
 
 // dst[k] = sum_r nu_kr src[r] for every species, balanced over the lanes: lane l
@@ -227,9 +227,10 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
   const double lnT = log_tab(T, t.logt);
   const double rho = (p * (1.0 / kRu)) * (invT * invS);
   const double invrho = (kRu * T) * (S * invp);
-  double ctot = 0.0;
+  double ctot = 0.0, cpp = 0.0;
   for (int k = lane; k < Ns; k += 32) {
-    double c = rho * Z[k] * t.invW[k];
+    const double zw = Z[k] * t.invW[k];
+    const double c = rho * zw;
     w.C[k] = c;
     ctot += c;
     double cpv = fma(fma(fma(fma(t.cp[4 * nsv + k], T, t.cp[3 * nsv + k]), T, t.cp[2 * nsv + k]), T,
@@ -239,12 +240,14 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     double sv = fma(fma(fma(fma(t.ss[4 * nsv + k], T, t.ss[3 * nsv + k]), T, t.ss[2 * nsv + k]), T,
                         t.ss[nsv + k]), T, fma(t.ss[k], lnT, t.s6[k]));
     const double g = hv - sv;
-    const double e = exp_tab(-g, t.exp2t);
+    double e, einv;
+    exp_pair(-g, t.exp2t, e, einv);
+    cpp = fma(zw, cpv, cpp);
     w.cp[k] = cpv;
     w.hh[k] = hv;
     w.g[k] = g;
     w.E[k] = e;
-    w.Einv[k] = JAC ? 1.0 / e : c / e;   // 1/E for the Jacobian's k_r, else C/E
+    w.Einv[k] = JAC ? einv : c * einv;   // 1/E for the Jacobian's k_r, else C/E
   }
   if (lane == 0) { w.C[Ns] = 1.0; w.g[Ns] = 0.0; w.hh[Ns] = 0.0; w.E[Ns] = 1.0; w.Einv[Ns] = 1.0; }
   if (lane < 5) {
@@ -254,6 +257,7 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     w.c0p[lane] = v;
   }
   const double Ctot = warp_sum(ctot);
+  const double cpm = warp_sum(cpp);
   __syncwarp();
   // falloff, phase 1: exp(ln k0 - ln k_inf), e^{-T/T***}, e^{-T/T*}, e^{-T**/T}
   for (int e = lane; e < 4 * NT; e += 32) {
@@ -287,8 +291,36 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     q[7 + kind] = log_tab(x, t.logt) * (1.0 / kLn10);   // q[7] = log10 Fc, q[8] = log10 Pr
   }
   __syncwarp();
-  // falloff, phase 3: broadening F, factor Pr/(1+Pr) F, and its derivatives
-  for (int tr = lane; tr < NT; tr += 32) {
+  // falloff, phase 3: broadening F, factor Pr/(1+Pr) F, and its derivatives.  Without
+  // the Jacobian and with fewer than 32 falloff reactions, lane NT (idle in this pass)
+  // inverts the mixture heat capacity in the same division instruction.
+  double invcpm;
+  if (!JAC && NT < 32) {
+    double den_in = cpm, d2 = 0.0, s2 = 0.0, P1 = 0.0, logFc = 0.0, Pr = 0.0;
+    double* q = w.tro + kTroeSlots * (lane < NT ? lane : 0);
+    if (lane < NT) {
+      logFc = q[7];
+      Pr = q[5];
+      const double c = fma(-0.67, logFc, -0.4);
+      const double nn = fma(-1.27, logFc, 0.75);
+      const double u = q[8] + c;
+      const double den = fma(-0.14, u, nn);
+      d2 = den * den;
+      s2 = fma(u, u, d2);
+      P1 = 1.0 + Pr;
+      den_in = s2 * P1;
+    }
+    const double inv = 1.0 / den_in;
+    if (lane < NT) {
+      // log F = log Fc den^2 / (den^2 + u^2) and the factor Pr/(1+Pr) F share the division
+      const double logF = (logFc * d2) * (P1 * inv);
+      q[9] = (Pr * s2) * inv * exp_tab(logF * kLn10, t.exp2t);
+    }
+    invcpm = __shfl_sync(0xffffffffu, inv, NT);
+  } else {
+    invcpm = 1.0 / cpm;
+  }
+  for (int tr = lane; tr < NT && (JAC || NT >= 32); tr += 32) {
     double* q = w.tro + kTroeSlots * tr;
     const double logFc = q[7], Pr = q[5];
     const double c = fma(-0.67, logFc, -0.4);
@@ -347,14 +379,12 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     gather_species(t, w, w.dqdT, w.DT, lane);
     gather_species(t, w, w.tbs, w.tbk, lane);
   }
-  double qp = 0.0, cpp = 0.0;
-  for (int k = lane; k < Ns; k += 32) {
-    qp = fma(w.hh[k], w.wd[k], qp);
-    cpp = fma(Z[k] * t.invW[k], w.cp[k], cpp);
-  }
+  double qp = 0.0;
+  for (int k = lane; k < Ns; k += 32) qp = fma(w.hh[k], w.wd[k], qp);
   s.T = T; s.invT = invT; s.lnT = lnT; s.S = S; s.invS = invS; s.rho = rho; s.invrho = invrho; s.Ctot = Ctot;
   s.Q = warp_sum(qp);
-  s.cpm = warp_sum(cpp);
+  s.cpm = cpm;
+  s.invcpm = invcpm;
   __syncwarp();
 }
 
@@ -362,7 +392,7 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
 __device__ __forceinline__ void chem_rhs_out(const Tab& t, const WS& w, const Scal& s, double* f, int lane) {
   const int Ns = t.Ns;
   for (int k = lane; k < Ns; k += 32) f[k] = w.wd[k] * t.W[k] * s.invrho;
-  if (lane == 0) f[Ns] = -s.T * s.Q * s.invrho / s.cpm;
+  if (lane == 0) f[Ns] = -(s.T * s.Q) * (s.invrho * s.invcpm);
   __syncwarp();
 }
 
@@ -457,7 +487,7 @@ __device__ __forceinline__ void chem_jac(const Tab& t, const WS& w, const double
   const double invS = s.invS;
   const MT inv_rhoS = (MT)(s.invrho * invS);
   const double Phi = T * s.invrho;
-  const double invcpm = 1.0 / s.cpm;
+  const double invcpm = s.invcpm;
   const double PQc = Phi * s.Q * invcpm;
   // species rows: J_kj = (W_k / W_j)(D_kj - (DC_k - wdot_k)/(rho S)), J_kT = (W_k/rho)(DT_k - (DC_k - wdot_k)/T)
   for (int e = lane; e < Ns * Ns; e += 32) {

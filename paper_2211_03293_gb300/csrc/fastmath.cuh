@@ -49,6 +49,33 @@ __device__ __forceinline__ double exp_tab(double x, const double* __restrict__ t
   return __hiloint2double(__double2hiint(v) + (N >> 5) * 1048576, __double2loint(v));
 }
 
+// exp(x) and exp(-x) from one argument reduction (the method of exp_tab): with
+// x = N ln2/32 + r, exp(x) = 2^(N>>5) 2^((N&31)/32) e^r and exp(-x) = 2^((-N)>>5)
+// 2^(((-N)&31)/32) e^-r, and e^(+-r) - 1 = E(r) +- O(r) from the even and odd parts
+// of the same degree-6 Taylor polynomial.  |x| >= 700 and NaN take the library exp.
+__device__ __forceinline__ void exp_pair(double x, const double* __restrict__ tab32, double& ep, double& em) {
+  const int hx = __double2hiint(x) & 0x7fffffff;
+  if (hx >= 0x4085E000) {
+    ep = exp(x);
+    em = exp(-x);
+    return;
+  }
+  const double t = fma(x, kExpInvL, kExpShift);
+  const int N = __double2loint(t);
+  const double kd = t - kExpShift;
+  double r = fma(-kd, kExpL1, x);
+  r = fma(-kd, kExpL2, r);
+  const double r2 = r * r;
+  const double ev = r2 * fma(fma(r2, 1.0 / 720.0, 1.0 / 24.0), r2, 0.5);   // r^2/2 + r^4/24 + r^6/720
+  const double od = r * fma(fma(r2, 1.0 / 120.0, 1.0 / 6.0), r2, 1.0);     // r + r^3/6 + r^5/120
+  const int Nm = -N;
+  const double sp = tab32[N & 31], sm = tab32[Nm & 31];
+  const double vp = fma(sp, ev + od, sp);
+  const double vm = fma(sm, ev - od, sm);
+  ep = __hiloint2double(__double2hiint(vp) + (N >> 5) * 1048576, __double2loint(vp));
+  em = __hiloint2double(__double2hiint(vm) + (Nm >> 5) * 1048576, __double2loint(vm));
+}
+
 // table: [0, 129) 1/F, [129, 258) log(F) leading, [258, 387) log(F) trailing, then
 // ln2 leading and trailing
 constexpr int kLogTabDoubles = 389;

@@ -14,7 +14,7 @@ constexpr double kLn10 = 2.30258509299404568401799145468;
 constexpr int kMaxSpecies = 127;
 constexpr int kMaxReactions = 1023;
 constexpr int kMaxK = 4;                     // forcing polynomial terms
-constexpr int kMaxWarps = 16;                // warps (cells in flight) per CTA
+constexpr int kMaxWarps = 12;                // warps (cells in flight) per CTA
 constexpr int kTroeSlots = 12;               // per-cell doubles of one falloff reaction's intermediates
 
 // Byte offsets of the sections of the mechanism table.  The table is one

@@ -33,6 +33,14 @@ __global__ void exp_probe_kernel(const double* x, double* y, long long n, Exp2Ta
     y[i] = mri::exp_tab(x[i], s);
 }
 
+__global__ void exp_pair_probe_kernel(const double* x, double* y, double* z, long long n, Exp2Table tab) {
+  __shared__ double s[32];
+  if (threadIdx.x < 32) s[threadIdx.x] = tab.v[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    mri::exp_pair(x[i], s, y[i], z[i]);
+}
+
 struct LogTable {
   double v[mri::kLogTabDoubles];
 };
@@ -46,6 +54,17 @@ __global__ void log_probe_kernel(const double* x, double* y, long long n, LogTab
 }
 
 }  // namespace
+
+extern "C" int mri_probe_exp_pair(const double* x, double* y, double* z, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y || !z))) return -1;
+  if (n == 0) return 0;
+  Exp2Table tab;
+  for (int j = 0; j < 32; ++j) tab.v[j] = (double)std::exp2l((long double)j / 32.0L);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  exp_pair_probe_kernel<<<(int)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, z, n, tab);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
 
 extern "C" int mri_probe_log(const double* x, double* y, long long n, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return -1;

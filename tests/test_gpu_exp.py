@@ -65,3 +65,21 @@ def test_log_special_arguments(mri):
     np.testing.assert_array_equal(np.isnan(y), np.isnan(ref))
     ok = ~np.isnan(ref)
     np.testing.assert_array_equal(y[ok], ref[ok])
+
+
+def test_exp_pair_accuracy(mri):
+    """exp(x) and exp(-x) from one reduction, as the species factors are formed."""
+    import torch
+    rng = np.random.default_rng(2)
+    x = np.concatenate([rng.uniform(-699, 699, 200000), rng.uniform(-50, 50, 100000), rng.uniform(-1e-6, 1e-6, 1000),
+                        [0.0, 1.0, -1.0, 699.0, -699.0], [705.0, -705.0, 800.0, np.nan]])
+    xd = torch.tensor(x, device="cuda")
+    yd, zd = torch.empty_like(xd), torch.empty_like(xd)
+    mri.mri_probe_exp_pair(xd, yd, zd)
+    y, z = yd.cpu().numpy(), zd.cpu().numpy()
+    body = np.abs(x) < 700
+    assert ulp_err(y[body], np.exp(x[body])).max() <= 1.0
+    assert ulp_err(z[body], np.exp(-x[body])).max() <= 1.0
+    ref_y, ref_z = torch.exp(xd).cpu().numpy(), torch.exp(-xd).cpu().numpy()
+    np.testing.assert_array_equal(y[~body], ref_y[~body])
+    np.testing.assert_array_equal(z[~body], ref_z[~body])

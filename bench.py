@@ -460,6 +460,20 @@ def cpu_baseline_sample(ncells_sample, seed=0, nthreads=None, repeats=1):
     return cs / tt, nthreads, cs, tt
 
 
+def whole_job_rates(times_ms, work, world, device):
+    """Whole-job throughput of every leg: the work of all ranks over the slowest
+    rank's time (max over ranks of the time, sum over ranks of the work).  Returns
+    (rates, (times, work)) with the reduced values."""
+    import torch
+    t = torch.tensor(times_ms, dtype=torch.float64, device=device)
+    w = torch.tensor(work, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(w, op=torch.distributed.ReduceOp.SUM)
+    t, w = t.cpu().numpy(), w.cpu().numpy()
+    return [float(wi / (ti * 1e-3)) for ti, wi in zip(t, w)], (t, w)
+
+
 def dist_init(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -529,14 +543,8 @@ def main():
     results = {}
     for prec in forms:
         r = b.run_form(prec)
-        t = torch.tensor([r["total_ms"], r["e2e_ms"]], dtype=torch.float64, device="cuda")
-        work = torch.tensor([r["substeps"], r["e2e_substeps"]], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            torch.distributed.all_reduce(work, op=torch.distributed.ReduceOp.SUM)
-        t, work = t.cpu().numpy(), work.cpu().numpy()
-        r["value"] = work[0] / (t[0] * 1e-3)
-        r["e2e_value"] = work[1] / (t[1] * 1e-3)
+        (r["value"], r["e2e_value"]), _ = whole_job_rates([r["total_ms"], r["e2e_ms"]],
+                                                          [r["substeps"], r["e2e_substeps"]], world, "cuda")
         r["gate"] = None if (args.no_cpu or rank != 0) else b.gate(r["prec"], r["model"])
         r["model"] = None
         results[prec] = r

@@ -186,6 +186,7 @@ class Bench:
         self.c, self.G = mri.mri_method_coupling(mri.MRI_KW3)
         self.stream = torch.cuda.Stream(device=self.dev)
         self.shape = {}
+        self.cache = {}
         dev = self.dev
         self.p = torch.tensor(w.p, device=dev)
         self.fS = torch.empty((3, self.ncell, self.n), dtype=torch.float64, device=dev)
@@ -205,9 +206,11 @@ class Bench:
     def opts(self, prec, ramp=0):
         w = self.w
         wpb, bps = self.shape.get(prec, (0, 0))
-        return self.mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, ramp=ramp,
-                                              jac_policy=self.args.jac, precision=prec, warps_per_block=wpb,
-                                              blocks_per_sm=bps)
+        o = self.mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, ramp=ramp,
+                                           jac_policy=self.args.jac, precision=prec, warps_per_block=wpb,
+                                           blocks_per_sm=bps)
+        cache = self.cache.get(prec)
+        return o if cache is None else self.mri.with_matrix_cache(o, cache)
 
     def autotune(self, y, prec):
         """Pick the launch shape of the fast stage by timing the candidates on the
@@ -345,6 +348,9 @@ class Bench:
         torch, mri, args, w = self.torch, self.mri, self.args, self.w
         prec = 1 if form == 2 else form
         model, learn = self.train_learned(prec) if form == 2 else (None, None)
+        if args.matrix_cache and args.jac == 1:
+            self.cache[prec] = torch.zeros(mri.mri_matrix_cache_size(self.mech, self.ncell, prec),
+                                           dtype=torch.uint8, device=self.dev)
         y = torch.tensor(w.y0, device=self.dev)
         with torch.cuda.stream(self.stream):
             for s in range(args.warmup):
@@ -354,6 +360,10 @@ class Bench:
             if form == 2 and args.autotune and prec in self.shape:
                 launch = {"warps_per_block": self.shape[prec][0], "blocks_per_sm": max(self.shape[prec][1], 1),
                           "autotuned": "shape of the mixed form"}
+            if prec in self.cache:
+                self.cache[prec].zero_()      # the autotuner's trial runs leave no matrices behind
+                for s in range(1):            # one more untimed step refills the cache
+                    self.step(y, prec, False, None, model)
             self.stream.synchronize()
             warm_fail = int(self.nfail.item())
             self.stats.zero_()
@@ -523,6 +533,8 @@ def main():
     ap.add_argument("--prec", type=int, default=None,
                     help="time one form only: 0 plain FP64, 1 mixed precision, 2 learned start (mixed)")
     ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip the learned form")
+    ap.add_argument("--no-matrix-cache", dest="matrix_cache", action="store_false",
+                    help="refactorise the Newton matrix at the start of every stage instead of keeping it")
     ap.add_argument("--learn-steps", type=int, default=3, help="MRI steps of training data for the learned form")
     ap.add_argument("--learn-epochs", type=int, default=40, help="training epochs of the learned form")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -584,7 +596,9 @@ def main():
                                "MRI3 (Knoth-Wolke MIS) + SDIRK3 fast, H = 5e-8 s, h = H/10, Newton rtol 1e-10, "
                                "4th-order slow stencil; one step = one MRI slow step",
                    "cells": b.ncell, "unknowns_per_cell": b.n, "form": FORMS[head],
-                   "jac_policy": ["per-substep", "lazy"][args.jac],
+                   "jac_policy": ["per-substep", "lazy"][args.jac] + (" + matrix cache across calls"
+                                                                      if args.matrix_cache and args.jac == 1
+                                                                      else ""),
                    "reduced_for_profiling": args.cells_per_side is not None,
                    "l2": "256 MB buffer written between timed steps",
                    "launch": r["launch"],

@@ -121,11 +121,22 @@ typedef struct {
                             state, get status MRI_CELL_TIMEOUT and count in n_failed,
                             so a caller resumes by calling again on that tail.
                             mri_step rejects a budget. */
+  /* Newton-matrix cache (nullable): a device buffer of mri_matrix_cache_size bytes
+   * in which each cell's factorised Newton matrix, its h gamma and age survive from
+   * one call to the next, so that MRI_JAC_LAZY reuses it across the stages and
+   * steps of a run instead of refactorising at the start of every call.  The
+   * caller zeroes it once (a zeroed entry is empty), keeps the cell order fixed
+   * between calls that share it, and uses one cache per mechanism and precision;
+   * entries of another n or precision are ignored.  Like the lazy policy itself it
+   * changes the cost, not the converged results.  Calls that share a cache must
+   * not overlap on the GPU.  mri_stage_fast_batch rejects a cache. */
+  void* matrix_cache;
+  size_t matrix_cache_bytes;
 } mri_fast_opts;
 
 /* Fill opts with the defaults (SDIRK3, rtol 1e-10, atol_Y 1e-20, atol_T 1e-10 K,
  * 10 Newton iterations, per-substep Jacobian, FP64, no ramp, automatic launch
- * shape, no time budget). */
+ * shape, no time budget, no matrix cache). */
 void mri_fast_opts_default(mri_fast_opts* opts);
 
 /* One MRI stage of the fast partition for every cell (Eq. 3):
@@ -217,6 +228,10 @@ int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, double t0, 
  * counterpart.  Returns MRI_EINVAL if the requested shape does not fit. */
 int mri_stage_fast_shape(const mri_mech* mech, const mri_fast_opts* opts, int ncell, int K,
                          int* warps_per_block, int* blocks, size_t* smem_bytes);
+
+/* Bytes of the Newton-matrix cache (mri_fast_opts.matrix_cache) for ncell cells of
+ * a mechanism in a precision form (0 on bad arguments). */
+size_t mri_matrix_cache_size(const mri_mech* mech, int ncell, int precision);
 
 /* ---- slow partition ---------------------------------------------------- */
 typedef struct {

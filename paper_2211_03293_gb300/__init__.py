@@ -37,7 +37,8 @@ class mri_fast_opts(ct.Structure):
     _fields_ = [("method", ct.c_int), ("newton_rtol", ct.c_double), ("newton_atol_Y", ct.c_double),
                 ("newton_atol_T", ct.c_double), ("max_newton", ct.c_int), ("jac_policy", ct.c_int),
                 ("precision", ct.c_int), ("ramp", ct.c_int), ("warps_per_block", ct.c_int),
-                ("blocks_per_sm", ct.c_int), ("time_budget_s", ct.c_double)]
+                ("blocks_per_sm", ct.c_int), ("time_budget_s", ct.c_double), ("matrix_cache", ct.c_void_p),
+                ("matrix_cache_bytes", ct.c_size_t)]
 
 
 class mri_stage_group(ct.Structure):
@@ -89,6 +90,8 @@ _lib.mri_learned_targets.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp
 _lib.mri_learned_guess.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, _vp]
 _lib.mri_probe_log.argtypes = [_vp, _vp, ct.c_longlong, _vp]
 _lib.mri_probe_exp_pair.argtypes = [_vp, _vp, _vp, ct.c_longlong, _vp]
+_lib.mri_matrix_cache_size.argtypes = [_vp, ct.c_int, ct.c_int]
+_lib.mri_matrix_cache_size.restype = ct.c_size_t
 _lib.mri_slow_rhs.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, _vp]
 _lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_workspace_size.restype = ct.c_size_t
@@ -114,7 +117,8 @@ EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_de
             "mri_stage_fast_batch", "mri_mlp_create", "mri_mlp_free", "mri_mlp_num_params", "mri_mlp_params",
             "mri_mlp_forward", "mri_mlp_grad", "mri_mlp_grad_copy", "mri_mlp_adam", "mri_mlp_status",
             "mri_gemm_bf16", "mri_stage_fast_guided", "mri_learned_features", "mri_learned_targets",
-            "mri_learned_guess", "mri_probe_log", "mri_probe_exp_pair")
+            "mri_learned_guess", "mri_probe_log", "mri_probe_exp_pair",
+            "mri_matrix_cache_size")
 
 
 class MriError(RuntimeError):
@@ -195,6 +199,19 @@ class Mech:
         if h:
             _lib.mri_mech_free(h)
             self.handle = None
+
+
+def mri_matrix_cache_size(mech: Mech, ncell: int, precision: int = MRI_PREC_FP64) -> int:
+    return int(_lib.mri_matrix_cache_size(mech.handle, ncell, precision))
+
+
+def with_matrix_cache(opts: mri_fast_opts, cache) -> mri_fast_opts:
+    """A copy of opts that keeps Newton matrices in `cache` (a zeroed uint8 device
+    tensor of mri_matrix_cache_size bytes) between calls."""
+    o = mri_fast_opts.from_buffer_copy(opts)
+    o.matrix_cache = cache.data_ptr()
+    o.matrix_cache_bytes = cache.numel() * cache.element_size()
+    return o
 
 
 def mri_mech_load(blob: bytes) -> Mech:

@@ -631,6 +631,8 @@ struct StageArgs {
   const double* guess;   // [ncell][n_sub][n] predicted substep ends (MRI_START_GUESS*), else null
   int start;             // MRI_START_*
   int32_t* n_fallback;   // counts Newton restarts from the previous stage value (nullable)
+  unsigned char* mcache; // Newton-matrix cache entries (nullable), mc_stride bytes per cell
+  size_t mc_stride;
   unsigned long long budget_ns;   // 0: no time budget
   double Hs, hh, rtol, atol_Y, atol_T;
   double A[3][3], c[3], gamma;
@@ -754,6 +756,31 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
     int nsub = 0, nnewton = 0, njac = 0;
     double M_hg = 0.0;     // h gamma of the factorised Newton matrix (0: none yet)
     int M_age = 0;         // substeps since its Jacobian was evaluated
+    // the cell's factorised matrix from an earlier call, when the cache holds one
+    unsigned char* mce = (a.mcache && a.jac_policy == MRI_JAC_LAZY && status == MRI_CELL_OK)
+                             ? a.mcache + (size_t)cell * a.mc_stride : nullptr;
+    if (mce) {
+      const McHeader* hd = reinterpret_cast<const McHeader*>(mce);
+      if (hd->tag == kMcTag && hd->n == n && hd->prec == (PREC32 ? 1 : 0)) {
+        const int nm = n * w.ld;
+        if (PREC32) {
+          const float* src = reinterpret_cast<const float*>(mce + sizeof(McHeader));
+          for (int e = lane; e < nm; e += 32) w.M32[e] = src[e];
+          for (int e = lane; e < n; e += 32) w.dinv32[e] = src[nm + e];
+          const int* ps = reinterpret_cast<const int*>(src + nm + n);
+          for (int e = lane; e < n; e += 32) w.piv[e] = ps[e];
+        } else {
+          const double* src = reinterpret_cast<const double*>(mce + sizeof(McHeader));
+          for (int e = lane; e < nm; e += 32) w.M[e] = src[e];
+          for (int e = lane; e < n; e += 32) w.dinv[e] = src[nm + e];
+          const int* ps = reinterpret_cast<const int*>(src + nm + n);
+          for (int e = lane; e < n; e += 32) w.piv[e] = ps[e];
+        }
+        M_hg = hd->hg;
+        M_age = hd->age;
+      }
+      __syncwarp();
+    }
     bool have_Fl = false;  // w.Fl holds the last stage derivative of the previous substep
     double hk_prev = 0.0;  // size of the previous substep
     for (int sidx = 0; sidx < total_sub && status == MRI_CELL_OK; ++sidx) {
@@ -931,6 +958,34 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
       have_Fl = true;
       hk_prev = hk;
       nsub++;
+    }
+    if (mce && status == MRI_CELL_OK && M_hg != 0.0) {   // keep the matrix for the next call
+      McHeader* hd = reinterpret_cast<McHeader*>(mce);
+      if (njac > 0) {
+        const int nm = n * w.ld;
+        if (PREC32) {
+          float* dst = reinterpret_cast<float*>(mce + sizeof(McHeader));
+          for (int e = lane; e < nm; e += 32) dst[e] = w.M32[e];
+          for (int e = lane; e < n; e += 32) dst[nm + e] = w.dinv32[e];
+          int* pd = reinterpret_cast<int*>(dst + nm + n);
+          for (int e = lane; e < n; e += 32) pd[e] = w.piv[e];
+        } else {
+          double* dst = reinterpret_cast<double*>(mce + sizeof(McHeader));
+          for (int e = lane; e < nm; e += 32) dst[e] = w.M[e];
+          for (int e = lane; e < n; e += 32) dst[nm + e] = w.dinv[e];
+          int* pd = reinterpret_cast<int*>(dst + nm + n);
+          for (int e = lane; e < n; e += 32) pd[e] = w.piv[e];
+        }
+      }
+      if (lane == 0) {
+        hd->hg = M_hg;
+        hd->age = M_age;
+        hd->n = n;
+        hd->prec = PREC32 ? 1 : 0;
+        hd->tag = kMcTag;
+      }
+    } else if (mce && lane == 0) {
+      reinterpret_cast<McHeader*>(mce)->tag = 0;       // a failed cell leaves no matrix behind
     }
     if (status != MRI_CELL_EINPUT)
       for (int k = lane; k < n; k += 32) yc[k] = w.y0[k];
@@ -1186,6 +1241,11 @@ static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, 
   sdirk_table(o.method, a);
   a.ws_stride = ws_offsets(m.L, o.precision == MRI_PREC_FP32_LU, K).total;
   a.budget_ns = o.time_budget_s > 0 ? (unsigned long long)std::ceil(o.time_budget_s * 1e9) : 0ull;
+  if (o.matrix_cache) {
+    a.mc_stride = mc_stride(m.L, o.precision == MRI_PREC_FP32_LU);
+    if (o.matrix_cache_bytes < a.mc_stride * (size_t)ncell) return MRI_EINVAL;
+    a.mcache = static_cast<unsigned char*>(o.matrix_cache);
+  }
   return MRI_OK;
 }
 
@@ -1349,6 +1409,13 @@ extern "C" void mri_fast_opts_default(mri_fast_opts* o) {
   o->warps_per_block = 0;
   o->blocks_per_sm = 0;
   o->time_budget_s = 0.0;
+  o->matrix_cache = nullptr;
+  o->matrix_cache_bytes = 0;
+}
+
+extern "C" size_t mri_matrix_cache_size(const mri_mech* mech, int ncell, int precision) {
+  if (!mech || ncell < 0 || (precision != MRI_PREC_FP64 && precision != MRI_PREC_FP32_LU)) return 0;
+  return mri::mc_stride(reinterpret_cast<const Mech*>(mech)->L, precision == MRI_PREC_FP32_LU) * (size_t)ncell;
 }
 
 extern "C" int mri_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double t0,
@@ -1384,7 +1451,8 @@ extern "C" int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, 
                                     const mri_fast_opts* opts, int32_t* n_failed, void* stream) {
   (void)t0;
   if (!groups || ngroups < 1 || ngroups > MRI_MAX_GROUPS || !mri::fast_opts_ok(opts)) return MRI_EINVAL;
-  if (opts->warps_per_block != 0 || opts->blocks_per_sm > 1 || opts->time_budget_s != 0.0) return MRI_EINVAL;
+  if (opts->warps_per_block != 0 || opts->blocks_per_sm > 1 || opts->time_budget_s != 0.0 || opts->matrix_cache)
+    return MRI_EINVAL;
   if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return MRI_ECUDA;

@@ -64,6 +64,21 @@ struct Layout {
   int ws_doubles32;       // doubles per cell (warp), mixed-precision form, K = kMaxK
 };
 
+// Newton-matrix cache entry: header, then the factorised matrix (n * ld values), the
+// diagonal inverses (n values) and the pivots (n int32), in the form's precision.
+struct McHeader {
+  double hg;
+  int age, tag, n, prec;
+  int pad[2];
+};
+constexpr int kMcTag = 0x4D434143;   // marks a filled entry (a zeroed entry is empty)
+
+__host__ __device__ inline size_t mc_stride(const Layout& L, bool prec32) {
+  const size_t vb = prec32 ? 4 : 8;
+  const size_t b = sizeof(McHeader) + (size_t)L.n * L.ld * vb + (size_t)L.n * vb + (size_t)L.n * 4;
+  return (b + 127) / 128 * 128;
+}
+
 constexpr int kQueueSlots = 256;   // work-queue counters per mechanism (one per launch in flight)
 
 struct Mech {             // what mri_mech points at

@@ -49,6 +49,7 @@ def test_defaults_and_status_strings(lib):
     assert (o.method, o.newton_rtol, o.newton_atol_Y, o.newton_atol_T, o.max_newton, o.ramp) == (
         3, 1e-10, 1e-20, 1e-10, 10, 0)
     assert (o.jac_policy, o.precision, o.warps_per_block, o.blocks_per_sm, o.time_budget_s) == (0, 0, 0, 0, 0.0)
+    assert (o.matrix_cache, o.matrix_cache_bytes) == (None, 0)
     assert lib.mri_status_str(0) == "ok"
     assert "Newton" in lib.mri_status_str(-2)
 
@@ -91,7 +92,8 @@ def test_stage_argument_validation_on_host(lib):
     assert L.mri_stage_fast_batch(None, 1, 0.0, 1e-8, 1e-9, ct.byref(o), None, None) == lib.MRI_EINVAL
     assert L.mri_stage_fast_batch(grp, 0, 0.0, 1e-8, 1e-9, ct.byref(o), None, None) == lib.MRI_EINVAL
     assert L.mri_stage_fast_batch(grp, 9, 0.0, 1e-8, 1e-9, ct.byref(o), None, None) == lib.MRI_EINVAL
-    for kw in (dict(warps_per_block=2), dict(blocks_per_sm=2), dict(time_budget_s=1.0)):
+    for kw in (dict(warps_per_block=2), dict(blocks_per_sm=2), dict(time_budget_s=1.0),
+               dict(matrix_cache=0x1000, matrix_cache_bytes=1 << 20)):
         bad = lib.mri_fast_opts_default(**kw)
         assert L.mri_stage_fast_batch(grp, 1, 0.0, 1e-8, 1e-9, ct.byref(bad), None, None) == lib.MRI_EINVAL
     # a whole MRI step takes no time budget

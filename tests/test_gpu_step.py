@@ -99,3 +99,36 @@ def test_full_size_box32_first_stage_sampled_and_step_properties(mri, orc):
     E = w.mech.elem / w.mech.W[:, None]
     np.testing.assert_allclose((out[:, :-1] @ E).sum(0), (w.y0[:, :-1] @ E).sum(0), rtol=1e-11)
     assert np.all(ss[:, 0] == (4 + w.ramp) + 5 + 3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_matrix_cache_keeps_results_and_saves_jacobians(mri, prec):
+    """Three MRI steps of the 8^3 box with the Newton-matrix cache against the same
+    steps without it: the same stage solutions (to the Newton tolerance) with fewer
+    Jacobian evaluations; an undersized cache is rejected."""
+    import torch
+    w = mechgen.workload("box32", cells_per_side=8)
+    kw = dict(method=3, ramp=w.ramp, jac_policy=1, precision=prec)
+    plain, st0, ss0, nf0 = gpu_steps(mri, w, 3, kw)
+    gm = mri.mri_mech_load(w.mech.to_blob())
+    nc = w.y0.shape[0]
+    cache = torch.zeros(mri.mri_matrix_cache_size(gm, nc, prec), dtype=torch.uint8, device="cuda")
+    g = w.grid
+    grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
+    y = torch.tensor(w.y0, device="cuda")
+    p = torch.tensor(w.p, device="cuda")
+    ws = torch.empty(mri.mri_step_workspace_size(grid, w.mech.n) // 8, dtype=torch.float64, device="cuda")
+    st = torch.zeros(nc, dtype=torch.int32, device="cuda")
+    ss = torch.zeros((nc, 4), dtype=torch.int32, device="cuda")
+    for s in range(3):
+        o = mri.with_matrix_cache(mri.mri_fast_opts_default(**dict(kw, ramp=kw["ramp"] if s == 0 else 0)), cache)
+        mri.mri_step(y, p, grid, s * w.H, w.H, w.h, gm, o, ws, cell_status=st, cell_stats=ss)
+    torch.cuda.synchronize()
+    got, ss = y.cpu().numpy(), ss.cpu().numpy()
+    assert np.all(st.cpu().numpy() == 0) and nf0 == 0
+    assert_parity(got, plain, rtol=1e-10, what="matrix cache vs none")
+    assert ss[:, 2].sum() < ss0[:, 2].sum()
+    assert np.all(ss[:, 0] == ss0[:, 0])
+    small = mri.with_matrix_cache(mri.mri_fast_opts_default(**kw), cache[: cache.numel() // 2])
+    with pytest.raises(mri.MriError):
+        mri.mri_stage_fast(y, p, None, 0.0, w.H / 3, w.h, gm, small)

@@ -10,10 +10,14 @@ three stage forcings, three fast stages) through the C ABI.
 
 Metric: fast-chemistry cell-steps per second, a cell-step being one SDIRK
 substep of one cell (all its stages and Newton iterations), counted from the
-kernels' own per-cell counters.  Two forms are timed: the plain FP64 path and
-the mixed-precision path (FP32 Newton matrix / LU, FP64 rates and residual).
-Each form is gated against the CPU oracle (sampled cells of a full-size stage,
-relative error <= 1e-6); the headline is the fastest form that passes.
+kernels' own per-cell counters.  Three forms are timed: the plain FP64 path,
+the mixed-precision path (FP32 Newton matrix / LU, FP64 rates and residual) and
+the learned start on the mixed path (a bf16 network trained on the first steps
+predicts Newton starts; its inference is inside the timed steps).  Each form
+uses the persistent kernel's autotuned launch shape and keeps Newton matrices
+across calls, and is gated against the CPU oracle (sampled cells of a full-size
+stage, relative error <= 1e-6, per-field maxima and RMS reported); the headline
+is the fastest form that passes.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch one process per GPU with torch.distributed.run; every rank
@@ -47,6 +51,13 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS_NOMINAL = FP64_DFMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ * 1e6 / 1e12
 # nominal cost of one exp or log in the algorithmic flop count
 FLOPS_PER_TRANSCENDENTAL = 20.0
+# DRAM bytes (read + write) per cell and fast-stage launch of stage_fast_kernel with the
+# Newton-matrix cache in use, from the ncu captures summarised in
+# profiles/stage_fast_fp64_box16.md and profiles/stage_fast_mixed_box16.md (4096-cell
+# launches; traffic grows with the cells processed, so a launch over `cells` moves
+# cells times this).  Keep in step with the kernel: a changed kernel needs a new
+# capture before these figures are reported again.
+STAGE_DRAM_BYTES_PER_CELL = {0: (60843520 + 2679552) / 4096, 1: (32546304 + 1792) / 4096}
 FORMS = {0: "plain FP64", 1: "mixed: FP32 Newton matrix and LU, FP64 rates, residual and update",
          2: "learned: mixed form with Newton started from a bf16 MLP's prediction where the predictor has none"}
 
@@ -573,8 +584,13 @@ def main():
         per_launch = r["flops64"] / r["stage_launches"]
         avg_s = r["stage_total_ms"] * 1e-3 / r["stage_launches"]
         ach = per_launch / avg_s / 1e12
+        per_cell = STAGE_DRAM_BYTES_PER_CELL.get(r["prec"]) if args.matrix_cache and args.jac == 1 else None
+        traffic = None if per_cell is None else per_cell * b.ncell
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": "stage_fast_kernel", "fp64_flops_per_launch": per_launch,
+                "traffic": traffic, "traffic_unit": "bytes per launch (DRAM read + write)",
+                "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 4096-cell launch, "
+                                 "scaled to the launch's cells",
+                "kernel": "stage_fast_kernel", "fp64_flops_per_launch": per_launch,
                 "fp32_flops_per_launch": r["flops32"] / r["stage_launches"], "avg_launch_ms": avg_s * 1e3,
                 "peak_basis": "FP64 FMA pipe rate measured in this run (mri_probe_fp64_fma; the pipe issues 2 "
                               "DFMA/clk/SM, %.4f TFLOP/s at 2070 MHz); MEASURED_PEAKS.json has no FP64 entry"

@@ -1,12 +1,14 @@
 // The fast-partition hot path: chemistry right-hand side, analytic Jacobian,
 // warp-cooperative dense LU and the SDIRK / Newton substep driver.
 //
-// Organisation: one warp owns one grid cell for a whole MRI stage.  The
+// Organisation: a persistent grid (one CTA per SM) whose warps take cells from a
+// device work queue; a warp owns one grid cell for a whole MRI stage.  The
 // mechanism table lives in shared memory (one copy per CTA); each warp has a
 // private shared-memory workspace with the cell's n x n Newton matrix and the
 // vectors of the stage.  Lanes split reactions (rates), species (sums over
-// reactions), Jacobian columns (assembly) and matrix rows/entries (LU).  All
-// arithmetic of the state, residual, rates and factorisation is FP64.
+// reactions), Jacobian columns (assembly) and matrix rows/entries (LU).  The state,
+// residual and rates are FP64; the Newton matrix, its LU and the triangular solves
+// are FP64 or, in the mixed-precision form (PREC32), FP32.
 #include <cmath>
 #include <cstdio>
 #include <mutex>

@@ -107,12 +107,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-  return v;
-}
-
 // Copy the mechanism table (global) into shared memory with 16-byte loads.
 __device__ void stage_table(unsigned char* dst, const unsigned char* src, int bytes) {
   const int4* s = reinterpret_cast<const int4*>(src);

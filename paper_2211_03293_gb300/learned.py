@@ -15,7 +15,7 @@ import math
 
 import numpy as np
 
-from . import (MRI_START_PREDICTOR, Mlp, mri_fast_opts, mri_learned_features, mri_learned_guess,
+from . import (Mlp, mri_fast_opts, mri_learned_features, mri_learned_guess,
                mri_learned_targets, mri_mlp_adam, mri_mlp_forward, mri_mlp_grad, mri_stage_fast)
 
 
@@ -70,7 +70,6 @@ class LearnedStart:
         self.finv = torch.ones(self.n_in, **f32)
         self.tmean = torch.zeros(self.n_out, **f32)
         self.tstd = torch.ones(self.n_out, **f32)
-        self.tinv = torch.ones(self.n_out, **f32)
         self.w_out = torch.zeros(self.n_out, **f32)
         self.records = []
         self.step = 0
@@ -111,7 +110,6 @@ class LearnedStart:
         self.finv = torch.tensor(1.0 / fs, dtype=torch.float32, device=dev)
         self.tmean = torch.tensor(tm, dtype=torch.float32, device=dev)
         self.tstd = torch.tensor(ts, dtype=torch.float32, device=dev)
-        self.tinv = torch.tensor(1.0 / ts, dtype=torch.float32, device=dev)
         w = np.zeros(self.n_out)
         w[:used_out] = 1.0
         self.w_out = torch.tensor(w, dtype=torch.float32, device=dev)

@@ -22,7 +22,8 @@ _ip = ct.POINTER(ct.c_int32)
 
 class Opts(ct.Structure):
     _fields_ = [("method", ct.c_int), ("rtol", ct.c_double), ("atol_Y", ct.c_double),
-                ("atol_T", ct.c_double), ("max_newton", ct.c_int), ("ramp", ct.c_int)]
+                ("atol_T", ct.c_double), ("max_newton", ct.c_int), ("ramp", ct.c_int), ("adaptive", ct.c_int),
+                ("ctrl_rtol", ct.c_double), ("ctrl_atol_Y", ct.c_double), ("ctrl_atol_T", ct.c_double)]
 
 
 class Grid(ct.Structure):
@@ -81,8 +82,9 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def opts(method=3, rtol=1e-10, atol_Y=1e-20, atol_T=1e-10, max_newton=10, ramp=0) -> Opts:
-    return Opts(method, rtol, atol_Y, atol_T, max_newton, ramp)
+def opts(method=3, rtol=1e-10, atol_Y=1e-20, atol_T=1e-10, max_newton=10, ramp=0, adaptive=0, ctrl_rtol=1e-6,
+         ctrl_atol_Y=1e-12, ctrl_atol_T=1e-6) -> Opts:
+    return Opts(method, rtol, atol_Y, atol_T, max_newton, ramp, adaptive, ctrl_rtol, ctrl_atol_Y, ctrl_atol_T)
 
 
 def grid(g: dict) -> Grid:
@@ -201,6 +203,13 @@ def sdirk_tableau(method):
     assert lib().orc_sdirk_tableau(method, _d(A), _d(b), _d(c), ct.byref(s)) == 0
     s = s.value
     return A[: s * s].reshape(s, s), b[:s], c[:s]
+
+
+def sdirk_embedded(method):
+    """(bhat, q): embedded weights of the adaptive controller's error estimate."""
+    bhat, q = np.zeros(3), ct.c_int32()
+    assert lib().orc_sdirk_embedded(method, _d(bhat), ct.byref(q)) == 0
+    return bhat[:method], q.value
 
 
 def mri_tableau():

@@ -373,6 +373,8 @@ struct Tableau {
   double A[3][3] = {};
   double c[3] = {};
   double gamma = 0.0;
+  double bhat[3] = {};   // embedded weights (one order lower) for the error estimate
+  int q = 0;             // order of the estimate's leading term: the controller uses err^(-1/q)
 };
 
 Tableau sdirk(int method) {
@@ -383,6 +385,9 @@ Tableau sdirk(int method) {
     t.A[0][0] = g;
     t.A[1][0] = 1.0 - g; t.A[1][1] = g;
     t.c[0] = g; t.c[1] = 1.0;
+    // first-order embedded weights (1, 0): the estimate is h gamma (F_2 - F_1)
+    t.bhat[0] = 1.0; t.bhat[1] = 0.0;
+    t.q = 2;
   } else if (method == 3) {
     // gamma: the root in (0, 1) of g^3 - 3 g^2 + 3/2 g - 1/6 = 0 with L-stability (~0.4358665)
     double g = 0.4358665215;
@@ -398,6 +403,12 @@ Tableau sdirk(int method) {
     t.A[2][1] = (6.0 * g * g - 20.0 * g + 5.0) / 4.0;
     t.A[2][2] = g;
     t.c[0] = g; t.c[1] = (1.0 + g) / 2.0; t.c[2] = 1.0;
+    // second-order embedded weights on the first two stages: sum bhat = 1 and
+    // bhat . c = 1/2 with bhat_3 = 0
+    t.bhat[1] = (0.5 - t.c[0]) / (t.c[1] - t.c[0]);
+    t.bhat[0] = 1.0 - t.bhat[1];
+    t.bhat[2] = 0.0;
+    t.q = 3;
   }
   return t;
 }
@@ -436,7 +447,7 @@ double wrms(int n, const double* d, const double* z, double rtol, const double* 
 // by full Newton from the previous stage value; F_i of a converged stage is taken from
 // the stage equation.  Returns 0, or 1 when a stage does not converge.
 int sdirk_step(const Problem& P, const Tableau& tab, double t, double h, double* y, const Forcing& fo,
-               double tau, double Hs, const orc_opts& o, StepStats& st) {
+               double tau, double Hs, const orc_opts& o, StepStats& st, double* err_out = nullptr) {
   const int n = P.n;
   std::vector<double> F((size_t)tab.s * n), Z(y, y + n), base(n), f(n), G(n), Mx((size_t)n * n), d(n);
   std::vector<int> piv(n);
@@ -474,7 +485,34 @@ int sdirk_step(const Problem& P, const Tableau& tab, double t, double h, double*
     for (int q = 0; q < n; ++q) F[(size_t)i * n + q] = (Z[q] - base[q]) / (h * tab.gamma);
   }
   for (int q = 0; q < n; ++q) y[q] = Z[q];   // stiffly accurate: y_{n+1} = Z_s
+  if (err_out) {
+    // local error estimate: h sum_i (b_i - bhat_i) F_i with b_i = a_{s,i}, in the WRMS norm
+    // of the controller's tolerances at the new state
+    double acc = 0.0;
+    for (int q = 0; q < n; ++q) {
+      double e = 0.0;
+      for (int i = 0; i < tab.s; ++i) e += (tab.A[tab.s - 1][i] - tab.bhat[i]) * F[(size_t)i * n + q];
+      e *= h;
+      const double wgt = o.ctrl_rtol * std::fabs(y[q]) + (q == n - 1 ? o.ctrl_atol_T : o.ctrl_atol_Y);
+      acc += (e / wgt) * (e / wgt);
+    }
+    *err_out = std::sqrt(acc / n);
+  }
   return 0;
+}
+
+// Step-size factor of the adaptive controller: the largest of 4, 2, 1, 1/2 not above
+// 0.9 err^(-1/q), else 1/4.  Powers of two keep every substep size and offset a
+// dyadic multiple of the initial substep.
+double ctrl_factor(double err, int q) {
+  const double F[4] = {4.0, 2.0, 1.0, 0.5};
+  for (int k = 0; k < 4; ++k) {
+    const double th = 0.9 / F[k];
+    double thq = th;
+    for (int j = 1; j < q; ++j) thq *= th;
+    if (err <= thq) return F[k];
+  }
+  return 0.25;
 }
 
 int n_substeps(double Hs, double h) {
@@ -487,8 +525,12 @@ int n_substeps(double Hs, double h) {
 // size hh = Hs/n_sub.  With ramp = R > 0 the first substep is replaced by the start-up
 // sequence hh 2^-R, hh 2^-R, hh 2^(1-R), ..., hh 2^-1 (sizes sum to hh exactly), which
 // lets Newton follow a state far from the fast manifold onto it.
+int fast_stage_adaptive(const Problem& P, const Tableau& tab, double t0, double Hs, double h, double* y,
+                        const Forcing& fo, const orc_opts& o, int32_t* stats);
+
 int fast_stage_unit(const Problem& P, const Tableau& tab, double t0, double Hs, double h, double* y,
                     const Forcing& fo, const orc_opts& o, int32_t* stats) {
+  if (o.adaptive) return fast_stage_adaptive(P, tab, t0, Hs, h, y, fo, o, stats);
   int n_sub = n_substeps(Hs, h);
   double hh = Hs / n_sub;
   std::vector<double> tau, hs;   // substep offsets within the stage and sizes
@@ -518,6 +560,49 @@ int fast_stage_unit(const Problem& P, const Tableau& tab, double t0, double Hs, 
       break;
     }
     done++;
+  }
+  if (stats) {
+    stats[0] += done; stats[1] += st.newton; stats[2] += st.jac; stats[3] += status;
+  }
+  return status;
+}
+
+// Fast IVP over one MRI stage with adaptive substeps: start from the uniform substep
+// Hs/n_sub; after each SDIRK step accept it when the embedded error estimate is at
+// most 1 (next size factor from ctrl_factor), else repeat it with the factor (1/2 or
+// 1/4); a step whose Newton iteration fails is repeated at 1/4 of the size.  The last
+// step ends exactly at Hs; sizes never exceed Hs.  The cell fails (keeping its last
+// accepted state) when a step falls below Hs 2^-40 or after 10000 attempts.
+int fast_stage_adaptive(const Problem& P, const Tableau& tab, double t0, double Hs, double h, double* y,
+                        const Forcing& fo, const orc_opts& o, int32_t* stats) {
+  const int n_sub = n_substeps(Hs, h);
+  double hc = Hs / n_sub;
+  const double h_floor = std::ldexp(Hs, -40);
+  double t = 0.0;
+  StepStats st;
+  int status = 0, done = 0, attempts = 0;
+  std::vector<double> save(P.n);
+  while (t < Hs) {
+    if (hc < h_floor || attempts >= 10000) { status = 1; break; }
+    ++attempts;
+    const bool last = (t + hc >= Hs * (1.0 - 1e-12));
+    const double hk = last ? Hs - t : hc;
+    std::copy(y, y + P.n, save.begin());
+    double err = 0.0;
+    if (sdirk_step(P, tab, t0 + t, hk, y, fo, t, Hs, o, st, &err) != 0) {
+      std::copy(save.begin(), save.end(), y);
+      hc = hk * 0.25;
+      continue;
+    }
+    const double fac = ctrl_factor(err, tab.q);
+    if (err <= 1.0) {
+      t = last ? Hs : t + hk;
+      done++;
+      hc = std::min(hk * fac, Hs);
+    } else {
+      std::copy(save.begin(), save.end(), y);
+      hc = hk * fac;
+    }
   }
   if (stats) {
     stats[0] += done; stats[1] += st.newton; stats[2] += st.jac; stats[3] += status;
@@ -835,6 +920,14 @@ int orc_sdirk_tableau(int method, double* A, double* b, double* c, int* s) {
     b[i] = t.A[t.s - 1][i];
     for (int j = 0; j < t.s; ++j) A[i * t.s + j] = t.A[i][j];
   }
+  return 0;
+}
+
+int orc_sdirk_embedded(int method, double* bhat, int* q) {
+  if (method != 2 && method != 3) return -1;
+  Tableau t = sdirk(method);
+  for (int i = 0; i < t.s; ++i) bhat[i] = t.bhat[i];
+  *q = t.q;
   return 0;
 }
 

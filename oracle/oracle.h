@@ -23,7 +23,8 @@
  *   - fast integrator: L-stable SDIRK2 / SDIRK3 (Alexander 1977) with full
  *     Newton (fresh analytic Jacobian and LU with partial pivoting every
  *     iteration), fixed substeps n_i = ceil(dc_i H / h), optionally a geometric
- *     start-up sequence in place of the first substep;
+ *     start-up sequence in place of the first substep; or (adaptive) substep
+ *     sizes from an embedded error estimate with a power-of-two controller;
  *   - slow partition: periodic central advection-diffusion, 2nd or 4th order,
  *     same u and D for every component (Sec. 3.1 for the 2nd-order form).
  *
@@ -47,6 +48,10 @@ typedef struct {
   int max_newton;      /* Newton iterations per stage before the cell fails */
   int ramp;            /* >0: first substep of the stage replaced by a geometric start-up
                           sequence of ramp+1 substeps (hh 2^-ramp, hh 2^-ramp, ..., hh/2) */
+  int adaptive;        /* 1: substep sizes chosen by the embedded error estimate (ramp ignored) */
+  double ctrl_rtol;    /* adaptive: local error tolerance, relative */
+  double ctrl_atol_Y;  /* adaptive: absolute, mass fractions */
+  double ctrl_atol_T;  /* adaptive: absolute, temperature [K] */
 } orc_opts;
 
 typedef struct {
@@ -73,6 +78,9 @@ int orc_jac_cs(const void* mech, const double* y, double p, double* J);
 
 int orc_lu_solve(int n, double* A, int* piv, double* b);
 int orc_sdirk_tableau(int method, double* A, double* b, double* c, int* s);
+/* embedded weights of the adaptive error estimate (one order lower than the method)
+   and the estimate's order q (the controller scales steps by err^(-1/q)) */
+int orc_sdirk_embedded(int method, double* bhat, int* q);
 int orc_mri_tableau(double* A, double* c, int* s);
 /* coupling coefficients of the MIS form: G[i*s + j] multiplies f^S(Y_j) in the
    constant forcing of stage i (i = 1..s-1, zero-based) */

@@ -289,6 +289,37 @@ class Bench:
             if ev_stage is not None:
                 ev_stage[i - 1][1].record(self.stream)
 
+    def adaptive_steps(self, y_start, prec, tol=1e-6):
+        """The same K steps from the same state with adaptive substeps (controller
+        tolerance tol): device time per MRI step and accepted substeps per cell and
+        stage, beside the fixed scheme's."""
+        torch, mri, args, w, c, G = self.torch, self.mri, self.args, self.w, self.c, self.G
+        y = y_start.clone()
+        st = torch.zeros((self.ncell, 4), dtype=torch.int32, device=self.dev)
+        evs = []
+        with torch.cuda.stream(self.stream):
+            for s in range(args.steps):
+                self.flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                for i in range(1, 4):
+                    mri.mri_slow_rhs(y, self.fS[i - 1], self.grid, stream=self.stream)
+                    mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=self.stream)
+                    o = self.opts(prec)
+                    o.adaptive, o.ctrl_rtol, o.ctrl_atol_Y, o.ctrl_atol_T = 1, tol, tol * 1e-6, tol
+                    mri.mri_stage_fast(y, self.p, self.phi, 0.0, (c[i] - c[i - 1]) * w.H, w.h, self.mech, o,
+                                       cell_stats=st, stream=self.stream)
+                e1.record(self.stream)
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b_) for a, b_ in evs) / args.steps
+        acc = st[:, 0].sum().item() / (3 * args.steps * self.ncell)
+        return {"ctrl_rtol": tol, "ms_per_step": ms, "accepted_substeps_per_cell_stage": acc,
+                "fixed_substeps_per_cell_stage": 12 / 3,
+                "note": "controller tolerance 1e-6 (global stage error about 1e-6 on relaxed states, "
+                        "against about 3e-4 for the fixed h = H/10 in the oracle's comparison with "
+                        "256x finer steps)"}
+
     def train_learned(self, prec):
         """The learned form's network, trained by the library's kernels on the
         substep-end states the plain solver produces over the first MRI steps of the
@@ -441,6 +472,7 @@ class Bench:
                 e1.synchronize()
                 e2e_ms.append(e0.elapsed_time(e1))
         e2e_sub = int(e2e_stats[:, 0].sum().item())
+        adaptive = self.adaptive_steps(y_start, prec) if (args.adaptive and model is None) else None
         fm = flop_model(w.mech)
         f64, f32 = algorithmic_flops(fm, newton, njac, prec)
         # kernels per step: 3 x (stencil, forcing, stage) [+ 3 x (features, input conversion,
@@ -450,7 +482,7 @@ class Bench:
                     njac=njac, failed=failed, clocks=clocks, stage_total_ms=float(np.sum(stage_ms)),
                     stage_launches=3 * args.steps, flops64=f64, flops32=f32, e2e_ms=float(sum(e2e_ms)),
                     e2e_substeps=e2e_sub, launches=per_step * args.steps, launch=launch, graph_ms=graph_ms,
-                    graph_substeps=graph_sub, model=model, learn=learn, fallbacks=fallbacks)
+                    graph_substeps=graph_sub, model=model, learn=learn, fallbacks=fallbacks, adaptive=adaptive)
 
 
 def cpu_baseline_sample(ncells_sample, seed=0, nthreads=None, repeats=1):
@@ -544,6 +576,8 @@ def main():
     ap.add_argument("--prec", type=int, default=None,
                     help="time one form only: 0 plain FP64, 1 mixed precision, 2 learned start (mixed)")
     ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip the learned form")
+    ap.add_argument("--no-adaptive", dest="adaptive", action="store_false",
+                    help="skip the adaptive-substep timing of each form")
     ap.add_argument("--no-matrix-cache", dest="matrix_cache", action="store_false",
                     help="refactorise the Newton matrix at the start of every stage instead of keeping it")
     ap.add_argument("--learn-steps", type=int, default=3, help="MRI steps of training data for the learned form")
@@ -633,6 +667,7 @@ def main():
                              "jac_per_substep": results[p]["njac"] / max(results[p]["substeps"], 1),
                              "launch": results[p]["launch"] and {k: v for k, v in results[p]["launch"].items()
                                                                  if k != "autotuned"},
+                             "adaptive_substeps": results[p]["adaptive"],
                              "learned": results[p]["learn"] and dict(
                                  results[p]["learn"], newton_fallbacks=results[p]["fallbacks"],
                                  accept_rate=1.0 - results[p]["fallbacks"] / max(3 * results[p]["substeps"], 1)),

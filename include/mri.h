@@ -132,11 +132,27 @@ typedef struct {
    * not overlap on the GPU.  mri_stage_fast_batch rejects a cache. */
   void* matrix_cache;
   size_t matrix_cache_bytes;
+  /* Adaptive substeps (the paper's fast steps are fixed; adaptivity is its stated
+   * future work).  1: starting from the uniform substep Hstage/n_sub, each SDIRK step
+   * is accepted when the WRMS norm (weights ctrl_rtol |y| + ctrl_atol) of the
+   * embedded estimate h sum_i (b_i - bhat_i) F_i is at most 1, with bhat the weights
+   * of one order lower on the same stages (SDIRK3: bhat_3 = 0, sum bhat = 1,
+   * bhat . c = 1/2; SDIRK2: bhat = (1, 0)); the next size is the step's times the
+   * largest of 4, 2, 1, 1/2 not above 0.9 err^(-1/q) (q = 3 for SDIRK3, 2 for SDIRK2;
+   * 1/2 or 1/4 after a rejection, 1/4 after a Newton failure), never above Hstage,
+   * and the last step ends exactly at Hstage.  A cell fails when a step falls below
+   * Hstage 2^-40 or after 10000 attempts.  ramp is ignored; cell_stats[0] counts
+   * accepted steps, [1] and [2] include rejected attempts.  h sets the first step. */
+  int adaptive;
+  double ctrl_rtol;
+  double ctrl_atol_Y;
+  double ctrl_atol_T;
 } mri_fast_opts;
 
 /* Fill opts with the defaults (SDIRK3, rtol 1e-10, atol_Y 1e-20, atol_T 1e-10 K,
  * 10 Newton iterations, per-substep Jacobian, FP64, no ramp, automatic launch
- * shape, no time budget, no matrix cache). */
+ * shape, no time budget, no matrix cache, fixed substeps; controller tolerances
+ * 1e-6, 1e-12, 1e-6 K for the adaptive option). */
 void mri_fast_opts_default(mri_fast_opts* opts);
 
 /* One MRI stage of the fast partition for every cell (Eq. 3):

@@ -38,7 +38,8 @@ class mri_fast_opts(ct.Structure):
                 ("newton_atol_T", ct.c_double), ("max_newton", ct.c_int), ("jac_policy", ct.c_int),
                 ("precision", ct.c_int), ("ramp", ct.c_int), ("warps_per_block", ct.c_int),
                 ("blocks_per_sm", ct.c_int), ("time_budget_s", ct.c_double), ("matrix_cache", ct.c_void_p),
-                ("matrix_cache_bytes", ct.c_size_t)]
+                ("matrix_cache_bytes", ct.c_size_t), ("adaptive", ct.c_int), ("ctrl_rtol", ct.c_double),
+                ("ctrl_atol_Y", ct.c_double), ("ctrl_atol_T", ct.c_double)]
 
 
 class mri_stage_group(ct.Structure):

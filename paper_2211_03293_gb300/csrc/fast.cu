@@ -629,6 +629,9 @@ struct StageArgs {
   int32_t* n_fallback;   // counts Newton restarts from the previous stage value (nullable)
   unsigned char* mcache; // Newton-matrix cache entries (nullable), mc_stride bytes per cell
   size_t mc_stride;
+  int adaptive, q;       // adaptive substeps; order of the error estimate
+  double ctrl_rtol, ctrl_atol_Y, ctrl_atol_T;
+  double bhat[3];        // embedded weights of the error estimate
   unsigned long long budget_ns;   // 0: no time budget
   double Hs, hh, rtol, atol_Y, atol_T;
   double A[3][3], c[3], gamma;
@@ -718,6 +721,21 @@ __device__ __forceinline__ int next_cell(const StageArgs& a, unsigned long long 
   return __shfl_sync(0xffffffffu, c, 0);
 }
 
+// Step-size factor of the adaptive controller: the largest of 4, 2, 1, 1/2 not above
+// 0.9 err^(-1/q), else 1/4.  Powers of two keep every substep size and offset a dyadic
+// multiple of the first substep.
+__device__ __forceinline__ double ctrl_factor(double err, int q) {
+  const double F[4] = {4.0, 2.0, 1.0, 0.5};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double th = 0.9 / F[k];
+    double thq = th;
+    for (int j = 1; j < q; ++j) thq *= th;
+    if (err <= thq) return F[k];
+  }
+  return 0.25;
+}
+
 // The cells of one stage launch, for one warp: after the CTA has staged the
 // mechanism tables at smem and the SDIRK tableau at sA / sc, the warp takes cells from
 // the launch's queue and integrates each over the stage (Eq. 3 with the forcing
@@ -779,12 +797,27 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
     }
     bool have_Fl = false;  // w.Fl holds the last stage derivative of the previous substep
     double hk_prev = 0.0;  // size of the previous substep
-    for (int sidx = 0; sidx < total_sub && status == MRI_CELL_OK; ++sidx) {
+    bool step_failed = false;   // adaptive: Newton failed in the current step
+    // adaptive substeps: time reached within the stage, next size, attempts so far
+    double t_ad = 0.0, hc = a.hh;
+    int attempts = 0;
+    for (int sidx = 0; status == MRI_CELL_OK; ++sidx) {
       double tau, hk;
-      substep_geometry(sidx, a.ramp, a.hh, tau, hk);
+      bool last_ad = false;
+      if (a.adaptive) {
+        if (!(t_ad < a.Hs)) break;
+        if (hc < ldexp(a.Hs, -40) || attempts >= 10000) { status = MRI_CELL_ENEWTON; break; }
+        ++attempts;
+        last_ad = (t_ad + hc >= a.Hs * (1.0 - 1e-12));
+        hk = last_ad ? a.Hs - t_ad : hc;
+        tau = t_ad;
+      } else {
+        if (sidx >= total_sub) break;
+        substep_geometry(sidx, a.ramp, a.hh, tau, hk);
+      }
       const double hg = hk * a.gamma;
       const double inv_hg = 1.0 / hg;
-      const bool startup_sub = (a.ramp > 0 && sidx <= a.ramp);
+      const bool startup_sub = (!a.adaptive && a.ramp > 0 && sidx <= a.ramp);
       // MRI_JAC_PER_SUBSTEP: Jacobian + LU at every substep start.  MRI_JAC_LAZY: the
       // factorised matrix carries over while h gamma is unchanged and it is younger
       // than kMaxJacAge substeps; poor contraction refreshes it inside Newton.
@@ -943,12 +976,42 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
           prev = nrm;
         }
         }
-        if (!conv) { status = MRI_CELL_ENEWTON; break; }
+        if (!conv) {
+          if (a.adaptive) step_failed = true;   // repeated at a quarter of the size
+          else status = MRI_CELL_ENEWTON;
+          break;
+        }
         double* Fi = (i < S - 1) ? w.F(i) : w.Fl;
         for (int k = lane; k < n; k += 32) Fi[k] = (w.Z[k] - w.base[k]) * inv_hg;
         __syncwarp();
       }
       if (status != MRI_CELL_OK) break;
+      if (a.adaptive) {
+        // embedded estimate h sum_i (b_i - bhat_i) F_i (b_i = a_{s,i}) in the WRMS norm of
+        // the controller's tolerances at the new state; FP64, as it decides the steps
+        double err = 0.0;
+        if (!step_failed) {
+          double acc = 0.0;
+          for (int k = lane; k < n; k += 32) {
+            double e = 0.0;
+            for (int j = 0; j < S; ++j) e = fma(sA[S - 1][j] - a.bhat[j], (j < S - 1) ? w.F(j)[k] : w.Fl[k], e);
+            e *= hk;
+            const double wgt = fma(a.ctrl_rtol, fabs(w.Z[k]), (k == n - 1) ? a.ctrl_atol_T : a.ctrl_atol_Y);
+            const double v = e / wgt;
+            acc = fma(v, v, acc);
+          }
+          err = sqrt(warp_sum(acc) / n);
+        }
+        const double fac = step_failed ? 0.25 : ctrl_factor(err, a.q);
+        if (step_failed || !(err <= 1.0)) {   // rejected: the state stays at the step's start
+          hc = hk * fac;
+          have_Fl = false;
+          step_failed = false;
+          continue;
+        }
+        t_ad = last_ad ? a.Hs : t_ad + hk;
+        hc = fmin(hk * fac, a.Hs);
+      }
       for (int k = lane; k < n; k += 32) w.y0[k] = w.Z[k];
       __syncwarp();
       have_Fl = true;
@@ -1018,7 +1081,7 @@ struct BatchArgs {
   int warps[MRI_MAX_GROUPS];
   int ngroups;
 };
-static_assert(sizeof(BatchArgs) <= 4096, "batch arguments must fit the classic kernel parameter space");
+static_assert(sizeof(BatchArgs) <= 32764, "batch arguments must fit the kernel parameter space");
 static_assert(sizeof(StageArgs) + 12 * sizeof(double) <= 1024, "static shared memory of the stage kernels");
 
 template <bool PREC32>
@@ -1199,6 +1262,9 @@ static void sdirk_table(int method, StageArgs& a) {
     a.A[1][0] = 1.0 - g; a.A[1][1] = g;
     a.c[0] = g; a.c[1] = 1.0;
     a.nstage = 2;
+    // first-order embedded weights (1, 0): the estimate is h gamma (F_2 - F_1)
+    a.bhat[0] = 1.0; a.bhat[1] = 0.0; a.bhat[2] = 0.0;
+    a.q = 2;
   } else {
     // L-stable root of g^3 - 3 g^2 + 3/2 g - 1/6 = 0
     const double g = 0.43586652150845899941601945119356;
@@ -1210,6 +1276,11 @@ static void sdirk_table(int method, StageArgs& a) {
     a.A[2][2] = g;
     a.c[0] = g; a.c[1] = 0.5 * (1.0 + g); a.c[2] = 1.0;
     a.nstage = 3;
+    // second-order embedded weights on the first two stages: sum 1, bhat . c = 1/2
+    a.bhat[1] = (0.5 - a.c[0]) / (a.c[1] - a.c[0]);
+    a.bhat[0] = 1.0 - a.bhat[1];
+    a.bhat[2] = 0.0;
+    a.q = 3;
   }
 }
 
@@ -1237,6 +1308,9 @@ static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, 
   sdirk_table(o.method, a);
   a.ws_stride = ws_offsets(m.L, o.precision == MRI_PREC_FP32_LU, K).total;
   a.budget_ns = o.time_budget_s > 0 ? (unsigned long long)std::ceil(o.time_budget_s * 1e9) : 0ull;
+  a.adaptive = o.adaptive;
+  a.ctrl_rtol = o.ctrl_rtol; a.ctrl_atol_Y = o.ctrl_atol_Y; a.ctrl_atol_T = o.ctrl_atol_T;
+  if (o.adaptive) a.ramp = 0;   // the controller finds its own start-up steps
   if (o.matrix_cache) {
     a.mc_stride = mc_stride(m.L, o.precision == MRI_PREC_FP32_LU);
     if (o.matrix_cache_bytes < a.mc_stride * (size_t)ncell) return MRI_EINVAL;
@@ -1375,7 +1449,10 @@ bool fast_opts_ok(const mri_fast_opts* o) {
          (o->precision == MRI_PREC_FP64 || o->precision == MRI_PREC_FP32_LU) &&
          o->ramp >= 0 && o->ramp <= 40 && o->warps_per_block >= 0 && o->warps_per_block <= kMaxWarps &&
          o->blocks_per_sm >= 0 && o->blocks_per_sm <= 8 && o->time_budget_s >= 0 &&
-         o->time_budget_s <= 1e6;
+         o->time_budget_s <= 1e6 && (o->adaptive == 0 || o->adaptive == 1) &&
+         (o->adaptive == 0 || (o->ctrl_rtol > 0 && std::isfinite(o->ctrl_rtol) && o->ctrl_atol_Y >= 0 &&
+                               o->ctrl_atol_T >= 0 && std::isfinite(o->ctrl_atol_Y) &&
+                               std::isfinite(o->ctrl_atol_T)));
 }
 
 int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* phi, int K, double Hstage,
@@ -1407,6 +1484,10 @@ extern "C" void mri_fast_opts_default(mri_fast_opts* o) {
   o->time_budget_s = 0.0;
   o->matrix_cache = nullptr;
   o->matrix_cache_bytes = 0;
+  o->adaptive = 0;
+  o->ctrl_rtol = 1e-6;
+  o->ctrl_atol_Y = 1e-12;
+  o->ctrl_atol_T = 1e-6;
 }
 
 extern "C" size_t mri_matrix_cache_size(const mri_mech* mech, int ncell, int precision) {

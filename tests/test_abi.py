@@ -50,6 +50,7 @@ def test_defaults_and_status_strings(lib):
         3, 1e-10, 1e-20, 1e-10, 10, 0)
     assert (o.jac_policy, o.precision, o.warps_per_block, o.blocks_per_sm, o.time_budget_s) == (0, 0, 0, 0, 0.0)
     assert (o.matrix_cache, o.matrix_cache_bytes) == (None, 0)
+    assert (o.adaptive, o.ctrl_rtol, o.ctrl_atol_Y, o.ctrl_atol_T) == (0, 1e-6, 1e-12, 1e-6)
     assert lib.mri_status_str(0) == "ok"
     assert "Newton" in lib.mri_status_str(-2)
 
@@ -83,7 +84,8 @@ def test_stage_argument_validation_on_host(lib):
                             None) == lib.MRI_EINVAL
     for kw in (dict(max_newton=0), dict(max_newton=101), dict(newton_rtol=0.0), dict(ramp=41), dict(precision=7),
                dict(warps_per_block=17), dict(warps_per_block=-1), dict(blocks_per_sm=9),
-               dict(time_budget_s=-1.0), dict(time_budget_s=float("nan"))):
+               dict(time_budget_s=-1.0), dict(time_budget_s=float("nan")), dict(adaptive=2),
+               dict(adaptive=1, ctrl_rtol=0.0), dict(adaptive=1, ctrl_atol_T=-1.0)):
         bad = lib.mri_fast_opts_default(**kw)
         assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, fake, ct.byref(bad), None, None, None,
                                 None) == lib.MRI_EINVAL

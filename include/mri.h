@@ -40,6 +40,7 @@ extern "C" {
 #define MRI_ECUDA (-3)     /* a CUDA call failed (launch, copy, allocation) */
 #define MRI_ETIMEOUT (-4)  /* a device work budget ran out */
 #define MRI_ENOMEM (-5)    /* workspace too small */
+#define MRI_ECONV (-6)     /* an iterative linear solve missed its tolerance in max_iter iterations */
 
 /* ---- per-cell status written by the kernels -------------------------- */
 #define MRI_CELL_OK 0
@@ -293,6 +294,44 @@ int mri_step(double* y, const double* p, const mri_grid* grid, double t, double 
              int mri_method, const mri_mech* mech, const mri_fast_opts* opts, void* workspace,
              size_t workspace_bytes, int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed,
              void* stream);
+
+/* ---- IMEX: implicit slow diffusion ---------------------------------------
+ * The paper's IMEX-MRI runs (Sec. 3.2, problem 2 of Sec. 3.1) split the slow
+ * partition into explicit advection f^E and implicit diffusion f^I and solve the
+ * implicit stages' linear systems with Krylov solvers.  The third- and fourth-order
+ * IMEX-MRI-GARK coupling tables the paper uses are not printed in it, so this
+ * library provides the implicit solve and a first-order solve-decoupled IMEX-MRI
+ * step built from it (its own, first order):
+ *
+ * mri_diffusion_solve: (I - a L) x = b for every component of [ncell][n], L = D lap_h
+ * the periodic 7-point (2nd-order) Laplacian of the grid (axes with one cell
+ * skipped; grid->u and grid->order are not used), by Jacobi-preconditioned
+ * conjugate gradients for all components at once (each with its own scalars),
+ * until |r|_2 <= tol |b|_2 per component (a component with b = 0: tol times its
+ * initial residual); n <= 1024.  x holds the initial guess on entry and
+ * the solution on return.  workspace: mri_diffusion_workspace_size bytes (device).
+ * *iterations (host, nullable) receives the iterations taken.  The host reads a
+ * device convergence flag every 8 iterations, so the call synchronises `stream`.
+ * Returns MRI_OK, MRI_ECONV after max_iter iterations without convergence,
+ * MRI_EINVAL, MRI_ENOMEM or MRI_ECUDA. */
+size_t mri_diffusion_workspace_size(const mri_grid* grid, int n);
+int mri_diffusion_solve(double* x, const double* b, int n, const mri_grid* grid, double a, double tol,
+                        int max_iter, void* workspace, size_t workspace_bytes, int* iterations, void* stream);
+
+/* One first-order IMEX-MRI step over [t, t + H]: with f^E the grid's advection
+ * (its order) and f^I = D lap_h y (7-point), the fast stage integrates
+ *   v' = f^F(v) + f^E(y_n) + f^I(y_n)   on [t, t + H] from y_n
+ * (mri_stage_fast with K = 1 and step h), then the solve-decoupled implicit stage
+ *   (I - H L) y_{n+1} = v - H L y_n
+ * (mri_diffusion_solve from x = v).  With f^F = 0 and u = 0 it is backward Euler for
+ * the diffusion.  workspace: mri_step_imex1_workspace_size bytes.  Status, stats and
+ * n_failed as mri_step; cg_iterations (host, nullable) as mri_diffusion_solve; the
+ * call synchronises `stream`. */
+size_t mri_step_imex1_workspace_size(const mri_grid* grid, int n);
+int mri_step_imex1(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
+                   const mri_mech* mech, const mri_fast_opts* opts, double cg_tol, int cg_max_iter,
+                   void* workspace, size_t workspace_bytes, int32_t* cell_status, int32_t* cell_stats,
+                   int32_t* n_failed, int* cg_iterations, void* stream);
 
 /* Allocation-free variant of mri_step.  The paper has no counterpart: this is a
  * service for callers that must not allocate device memory while they run --

@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ct.CDLL(LIB_PATH)
 
-MRI_OK, MRI_EINVAL, MRI_ENEWTON, MRI_ECUDA, MRI_ETIMEOUT, MRI_ENOMEM = 0, -1, -2, -3, -4, -5
+MRI_OK, MRI_EINVAL, MRI_ENEWTON, MRI_ECUDA, MRI_ETIMEOUT, MRI_ENOMEM, MRI_ECONV = 0, -1, -2, -3, -4, -5, -6
 MRI_CELL_OK, MRI_CELL_ENEWTON, MRI_CELL_EINPUT, MRI_CELL_TIMEOUT = 0, 1, 2, 3
 MRI_SDIRK2, MRI_SDIRK3 = 2, 3
 MRI_KW3 = 1
@@ -93,6 +93,15 @@ _lib.mri_probe_log.argtypes = [_vp, _vp, ct.c_longlong, _vp]
 _lib.mri_probe_exp_pair.argtypes = [_vp, _vp, _vp, ct.c_longlong, _vp]
 _lib.mri_matrix_cache_size.argtypes = [_vp, ct.c_int, ct.c_int]
 _lib.mri_matrix_cache_size.restype = ct.c_size_t
+_lib.mri_diffusion_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
+_lib.mri_diffusion_workspace_size.restype = ct.c_size_t
+_lib.mri_diffusion_solve.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_int,
+                                     _vp, ct.c_size_t, ct.POINTER(ct.c_int), _vp]
+_lib.mri_step_imex1_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
+_lib.mri_step_imex1_workspace_size.restype = ct.c_size_t
+_lib.mri_step_imex1.argtypes = [_vp, _vp, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_double, _vp,
+                                ct.POINTER(mri_fast_opts), ct.c_double, ct.c_int, _vp, ct.c_size_t, _vp, _vp, _vp,
+                                ct.POINTER(ct.c_int), _vp]
 _lib.mri_slow_rhs.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, _vp]
 _lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_workspace_size.restype = ct.c_size_t
@@ -119,7 +128,8 @@ EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_de
             "mri_mlp_forward", "mri_mlp_grad", "mri_mlp_grad_copy", "mri_mlp_adam", "mri_mlp_status",
             "mri_gemm_bf16", "mri_stage_fast_guided", "mri_learned_features", "mri_learned_targets",
             "mri_learned_guess", "mri_probe_log", "mri_probe_exp_pair",
-            "mri_matrix_cache_size")
+            "mri_matrix_cache_size", "mri_diffusion_workspace_size", "mri_diffusion_solve",
+            "mri_step_imex1_workspace_size", "mri_step_imex1")
 
 
 class MriError(RuntimeError):
@@ -287,6 +297,36 @@ def mri_step_noalloc(y, p, g: mri_grid, t, H, h, mech: Mech, opts: mri_fast_opts
     rc = _lib.mri_step_noalloc(_f64(y), _f64(p), ct.byref(g), t, H, h, mri_method, mech.handle, ct.byref(opts),
                                _i32(cell_status), _i32(cell_stats), _i32(n_failed), _stream(stream))
     return _check(rc, "mri_step_noalloc")
+
+
+def mri_diffusion_workspace_size(g: mri_grid, n: int) -> int:
+    return int(_lib.mri_diffusion_workspace_size(ct.byref(g), n))
+
+
+def mri_diffusion_solve(x, b, g: mri_grid, a, workspace, tol=1e-12, max_iter=1000, stream=None) -> int:
+    """(I - a D lap_h) x = b for every component (x: initial guess in, solution out);
+    returns the CG iterations taken."""
+    it = ct.c_int()
+    rc = _lib.mri_diffusion_solve(_f64(x), _f64(b), x.shape[1], ct.byref(g), float(a), float(tol), int(max_iter),
+                                  _ptr(workspace), workspace.numel() * workspace.element_size(), ct.byref(it),
+                                  _stream(stream))
+    _check(rc, "mri_diffusion_solve")
+    return it.value
+
+
+def mri_step_imex1_workspace_size(g: mri_grid, n: int) -> int:
+    return int(_lib.mri_step_imex1_workspace_size(ct.byref(g), n))
+
+
+def mri_step_imex1(y, p, g: mri_grid, t, H, h, mech: Mech, opts: mri_fast_opts, workspace, cg_tol=1e-12,
+                   cg_max_iter=1000, cell_status=None, cell_stats=None, n_failed=None, stream=None) -> int:
+    """One first-order IMEX-MRI step; returns the CG iterations of its implicit stage."""
+    it = ct.c_int()
+    rc = _lib.mri_step_imex1(_f64(y), _f64(p), ct.byref(g), t, H, h, mech.handle, ct.byref(opts), float(cg_tol),
+                             int(cg_max_iter), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                             _i32(cell_status), _i32(cell_stats), _i32(n_failed), ct.byref(it), _stream(stream))
+    _check(rc, "mri_step_imex1")
+    return it.value
 
 
 def mri_stage_forcing(fS, nslow, coeffs, phi, stream=None) -> int:

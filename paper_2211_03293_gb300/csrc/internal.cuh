@@ -199,5 +199,7 @@ int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* 
                            int32_t* cell_stats, int32_t* n_failed, cudaStream_t st, bool sticky);
 int device_smem_limit();
 int device_sm_count();
+int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double a, double tol, int max_iter,
+                    void* ws, int* iters, cudaStream_t st);
 
 }  // namespace mri

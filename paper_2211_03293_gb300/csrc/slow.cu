@@ -209,6 +209,7 @@ extern "C" const char* mri_status_str(int code) {
     case MRI_ECUDA: return "CUDA error";
     case MRI_ETIMEOUT: return "device work budget exhausted";
     case MRI_ENOMEM: return "workspace too small";
+    case MRI_ECONV: return "iterative solve did not converge";
     default: return "unknown status";
   }
 }

@@ -1,0 +1,63 @@
+"""The implicit diffusion solve (Jacobi-PCG on the 7-point Laplacian) and the
+first-order IMEX-MRI step on the GPU against the oracle's exact Fourier solve and
+its IMEX step."""
+import numpy as np
+import pytest
+
+import mechgen
+from _parity import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("shape,a", [((32, 32, 32), 3e-3), ((64, 1, 1), 1e-2), ((9, 7, 5), 3e-4)])
+def test_diffusion_solve_matches_fourier_solution(mri, orc, shape, a):
+    import torch
+    nx, ny, nz = shape
+    n = 41
+    g = dict(nx=nx, ny=ny, nz=nz, dx=1e-4, u=(0.0, 0.0, 0.0), D=1e-5, order=2)
+    grid = mri.grid(nx, ny, nz, 1e-4, (0.0, 0.0, 0.0), 1e-5, 2)
+    rng = np.random.default_rng(nx + 10 * ny + 100 * nz)
+    b = rng.standard_normal((nx * ny * nz, n)) * 10.0 ** rng.uniform(-3, 3, n)
+    ref = orc.diffusion_solve(b, g, a)
+    bd = torch.tensor(b, device="cuda")
+    xd = bd.clone()                              # initial guess: b
+    ws = torch.empty(mri.mri_diffusion_workspace_size(grid, n), dtype=torch.uint8, device="cuda")
+    its = mri.mri_diffusion_solve(xd, bd, grid, a, ws, tol=1e-13, max_iter=2000)
+    x = xd.cpu().numpy()
+    err = np.abs(x - ref) / np.abs(ref).max(axis=0)
+    assert err.max() < 1e-11, err.max()
+    assert 0 < its < 2000
+
+
+def test_diffusion_solve_reports_no_convergence(mri):
+    import torch
+    grid = mri.grid(32, 32, 1, 1e-4, (0.0, 0.0, 0.0), 1e-5, 2)
+    b = torch.rand((32 * 32, 3), dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    ws = torch.empty(mri.mri_diffusion_workspace_size(grid, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(mri.MriError) as e:
+        mri.mri_diffusion_solve(x, b, grid, 1.0, ws, tol=1e-14, max_iter=2)
+    assert e.value.code == mri.MRI_ECONV
+
+
+@pytest.mark.parametrize("name,cells", [("line64", None), ("box32", 8)])
+def test_imex1_step_matches_oracle(mri, orc, name, cells):
+    import torch
+    w = mechgen.workload(name, cells_per_side=cells)
+    g = dict(w.grid, D=w.grid["D"] * 200)       # H D / dx^2 about 0.1: several CG iterations
+    grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
+    m = orc.Mech(w.mech)
+    y0, _, _ = m.stage_fast(w.y0, w.p, None, w.H / 3, w.h, orc.opts(method=w.method, ramp=w.ramp))
+    H = w.H / 2
+    ref, rst, _ = orc.imex1_step(m, y0, w.p, g, H, w.h, orc.opts(method=w.method))
+    assert np.all(rst == 0)
+    gm = mri.mri_mech_load(w.mech.to_blob())
+    y = torch.tensor(y0, device="cuda")
+    p = torch.tensor(w.p, device="cuda")
+    st = torch.zeros(y0.shape[0], dtype=torch.int32, device="cuda")
+    ws = torch.empty(mri.mri_step_imex1_workspace_size(grid, w.mech.n), dtype=torch.uint8, device="cuda")
+    its = mri.mri_step_imex1(y, p, grid, 0.0, H, w.h, gm, mri.mri_fast_opts_default(method=w.method, jac_policy=1),
+                             ws, cg_tol=1e-14, cell_status=st)
+    assert int((st != 0).sum()) == 0 and its > 0
+    assert_parity(y.cpu().numpy(), ref, what=f"IMEX1 step {name}")

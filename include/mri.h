@@ -308,30 +308,38 @@ int mri_step(double* y, const double* p, const mri_grid* grid, double t, double 
  * skipped; grid->u and grid->order are not used), by Jacobi-preconditioned
  * conjugate gradients for all components at once (each with its own scalars),
  * until |r|_2 <= tol |b|_2 per component (a component with b = 0: tol times its
- * initial residual); n <= 1024.  x holds the initial guess on entry and
- * the solution on return.  workspace: mri_diffusion_workspace_size bytes (device).
- * *iterations (host, nullable) receives the iterations taken.  The host reads a
- * device convergence flag every 8 iterations, so the call synchronises `stream`.
- * Returns MRI_OK, MRI_ECONV after max_iter iterations without convergence,
- * MRI_EINVAL, MRI_ENOMEM or MRI_ECUDA. */
+ * initial residual); n <= 1024.  x holds the initial guess on entry and the
+ * solution on return.  workspace: mri_diffusion_workspace_size bytes (device).
+ *   check_every > 0: the host reads the solve's device state every check_every
+ *     iterations (synchronising `stream`) and stops once every component has
+ *     converged; *iterations (host, nullable) receives the iterations taken.
+ *     Returns MRI_ECONV when max_iter iterations did not converge.
+ *   check_every = 0: all max_iter iterations are enqueued without synchronisation
+ *     (their launches do nothing once the solve has converged), so the call can be
+ *     captured in a CUDA graph; convergence is reported only through cg_info.
+ * cg_info (device, nullable, 2 ints): [0] 1 if every component converged, else 0;
+ * [1] iterations taken.  Returns MRI_OK, MRI_ECONV, MRI_EINVAL, MRI_ENOMEM or
+ * MRI_ECUDA. */
 size_t mri_diffusion_workspace_size(const mri_grid* grid, int n);
 int mri_diffusion_solve(double* x, const double* b, int n, const mri_grid* grid, double a, double tol,
-                        int max_iter, void* workspace, size_t workspace_bytes, int* iterations, void* stream);
+                        int max_iter, int check_every, void* workspace, size_t workspace_bytes, int* iterations,
+                        int32_t* cg_info, void* stream);
 
 /* One first-order IMEX-MRI step over [t, t + H]: with f^E the grid's advection
  * (its order) and f^I = D lap_h y (7-point), the fast stage integrates
  *   v' = f^F(v) + f^E(y_n) + f^I(y_n)   on [t, t + H] from y_n
  * (mri_stage_fast with K = 1 and step h), then the solve-decoupled implicit stage
  *   (I - H L) y_{n+1} = v - H L y_n
- * (mri_diffusion_solve from x = v).  With f^F = 0 and u = 0 it is backward Euler for
- * the diffusion.  workspace: mri_step_imex1_workspace_size bytes.  Status, stats and
- * n_failed as mri_step; cg_iterations (host, nullable) as mri_diffusion_solve; the
- * call synchronises `stream`. */
+ * (mri_diffusion_solve from x = v, with cg_tol, cg_max_iter, cg_check_every).  With
+ * f^F = 0 and u = 0 it is backward Euler for the diffusion.  workspace:
+ * mri_step_imex1_workspace_size bytes.  Status, stats and n_failed as mri_step;
+ * cg_iterations and cg_info as mri_diffusion_solve.  With cg_check_every = 0 the
+ * step does not synchronise and can be captured in a CUDA graph. */
 size_t mri_step_imex1_workspace_size(const mri_grid* grid, int n);
 int mri_step_imex1(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
                    const mri_mech* mech, const mri_fast_opts* opts, double cg_tol, int cg_max_iter,
-                   void* workspace, size_t workspace_bytes, int32_t* cell_status, int32_t* cell_stats,
-                   int32_t* n_failed, int* cg_iterations, void* stream);
+                   int cg_check_every, void* workspace, size_t workspace_bytes, int32_t* cell_status,
+                   int32_t* cell_stats, int32_t* n_failed, int* cg_iterations, int32_t* cg_info, void* stream);
 
 /* Allocation-free variant of mri_step.  The paper has no counterpart: this is a
  * service for callers that must not allocate device memory while they run --

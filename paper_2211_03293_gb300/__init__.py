@@ -96,12 +96,12 @@ _lib.mri_matrix_cache_size.restype = ct.c_size_t
 _lib.mri_diffusion_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_diffusion_workspace_size.restype = ct.c_size_t
 _lib.mri_diffusion_solve.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_int,
-                                     _vp, ct.c_size_t, ct.POINTER(ct.c_int), _vp]
+                                     ct.c_int, _vp, ct.c_size_t, ct.POINTER(ct.c_int), _vp, _vp]
 _lib.mri_step_imex1_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_imex1_workspace_size.restype = ct.c_size_t
 _lib.mri_step_imex1.argtypes = [_vp, _vp, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_double, _vp,
-                                ct.POINTER(mri_fast_opts), ct.c_double, ct.c_int, _vp, ct.c_size_t, _vp, _vp, _vp,
-                                ct.POINTER(ct.c_int), _vp]
+                                ct.POINTER(mri_fast_opts), ct.c_double, ct.c_int, ct.c_int, _vp, ct.c_size_t, _vp,
+                                _vp, _vp, ct.POINTER(ct.c_int), _vp, _vp]
 _lib.mri_slow_rhs.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, _vp]
 _lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_workspace_size.restype = ct.c_size_t
@@ -303,15 +303,18 @@ def mri_diffusion_workspace_size(g: mri_grid, n: int) -> int:
     return int(_lib.mri_diffusion_workspace_size(ct.byref(g), n))
 
 
-def mri_diffusion_solve(x, b, g: mri_grid, a, workspace, tol=1e-12, max_iter=1000, stream=None) -> int:
-    """(I - a D lap_h) x = b for every component (x: initial guess in, solution out);
-    returns the CG iterations taken."""
-    it = ct.c_int()
+def mri_diffusion_solve(x, b, g: mri_grid, a, workspace, tol=1e-12, max_iter=1000, check_every=8, cg_info=None,
+                        stream=None) -> int:
+    """(I - a D lap_h) x = b for every component (x: initial guess in, solution out).
+    With check_every > 0 returns the CG iterations taken; with check_every = 0 the
+    call does not synchronise (graph-capturable) and returns -1, convergence being
+    reported in cg_info (device int32[2])."""
+    it = ct.c_int(-1)
     rc = _lib.mri_diffusion_solve(_f64(x), _f64(b), x.shape[1], ct.byref(g), float(a), float(tol), int(max_iter),
-                                  _ptr(workspace), workspace.numel() * workspace.element_size(), ct.byref(it),
-                                  _stream(stream))
+                                  int(check_every), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                  ct.byref(it), _i32(cg_info), _stream(stream))
     _check(rc, "mri_diffusion_solve")
-    return it.value
+    return it.value if check_every > 0 else -1
 
 
 def mri_step_imex1_workspace_size(g: mri_grid, n: int) -> int:
@@ -319,14 +322,17 @@ def mri_step_imex1_workspace_size(g: mri_grid, n: int) -> int:
 
 
 def mri_step_imex1(y, p, g: mri_grid, t, H, h, mech: Mech, opts: mri_fast_opts, workspace, cg_tol=1e-12,
-                   cg_max_iter=1000, cell_status=None, cell_stats=None, n_failed=None, stream=None) -> int:
-    """One first-order IMEX-MRI step; returns the CG iterations of its implicit stage."""
-    it = ct.c_int()
+                   cg_max_iter=1000, cg_check_every=8, cell_status=None, cell_stats=None, n_failed=None,
+                   cg_info=None, stream=None) -> int:
+    """One first-order IMEX-MRI step; returns the CG iterations of its implicit stage
+    (-1 with cg_check_every = 0, which makes the step graph-capturable)."""
+    it = ct.c_int(-1)
     rc = _lib.mri_step_imex1(_f64(y), _f64(p), ct.byref(g), t, H, h, mech.handle, ct.byref(opts), float(cg_tol),
-                             int(cg_max_iter), _ptr(workspace), workspace.numel() * workspace.element_size(),
-                             _i32(cell_status), _i32(cell_stats), _i32(n_failed), ct.byref(it), _stream(stream))
+                             int(cg_max_iter), int(cg_check_every), _ptr(workspace),
+                             workspace.numel() * workspace.element_size(), _i32(cell_status), _i32(cell_stats),
+                             _i32(n_failed), ct.byref(it), _i32(cg_info), _stream(stream))
     _check(rc, "mri_step_imex1")
-    return it.value
+    return it.value if cg_check_every > 0 else -1
 
 
 def mri_stage_forcing(fS, nslow, coeffs, phi, stream=None) -> int:

@@ -611,6 +611,117 @@ __device__ __forceinline__ void lu_solve_warp(const MT* A, int n, int ld, const 
   }
 }
 
+// The row interchanges piv of lu_factor_warp as one permutation, in place:
+// (P b)[i] = b[perm[i]].  Each lane traces its own rows back through the
+// interchanges (the last one first), so no lane waits on another.
+__device__ __forceinline__ void piv_to_perm(int* piv, int n, int lane) {
+  int src[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int idx = lane + 32 * r;
+    if (idx < n)
+      for (int k = n - 1; k >= 0; --k) {
+        const int pk = piv[k];
+        idx = (idx == k) ? pk : ((idx == pk) ? k : idx);
+      }
+    src[r] = idx;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (lane + 32 * r < n) piv[lane + 32 * r] = src[r];
+  __syncwarp();
+}
+
+// Solve with SCALED factors and the permutation of piv_to_perm, with the solution
+// held in registers (row lane + 32 r in x[r], R = ceil(n / 32)): each step of the
+// substitutions broadcasts one solved entry by a shuffle, so the chain from one step
+// to the next is one FMA and one shuffle, with no shared-memory round trip.  The
+// arithmetic (its order included) is that of lu_solve_warp<true>.
+template <int R, typename MT>
+__device__ __forceinline__ void lu_solve_regs(const MT* A, int n, int ld, const int* perm, const MT* dinv, MT* b,
+                                              int lane) {
+  MT x[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    x[r] = (i < n) ? b[perm[i]] : MT(0);
+  }
+  // L y = P b (unit lower triangle)
+#pragma unroll
+  for (int jb = 0; jb < R; ++jb) {
+    const int j1 = min(n - 1, 32 * (jb + 1));
+#pragma unroll 1
+    for (int j = 32 * jb; j < j1; ++j) {
+      const MT xj = __shfl_sync(0xffffffffu, x[jb], j - 32 * jb);
+#pragma unroll
+      for (int r = jb; r < R; ++r) {
+        const int i = lane + 32 * r;
+        if (i > j && i < n) x[r] = fma_t(-A[i * ld + j], xj, x[r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i < n) x[r] *= dinv[i];
+  }
+  // (D^-1 U) x = D^-1 y (unit upper triangle)
+#pragma unroll
+  for (int jb = R - 1; jb >= 0; --jb) {
+    const int j0 = max(1, 32 * jb);
+#pragma unroll 1
+    for (int j = min(n - 1, 32 * jb + 31); j >= j0; --j) {
+      const MT xj = __shfl_sync(0xffffffffu, x[jb], j - 32 * jb);
+#pragma unroll
+      for (int r = 0; r <= jb; ++r) {
+        const int i = lane + 32 * r;
+        if (i < j) x[r] = fma_t(-A[i * ld + j], xj, x[r]);
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i < n) b[i] = x[r];
+  }
+  __syncwarp();
+}
+
+// n <= 64: the register solve; larger systems gather P b in place and run the
+// shared-memory substitutions of lu_solve_warp<true> (the same arithmetic).
+template <typename MT>
+__device__ __forceinline__ void lu_solve_perm(const MT* A, int n, int ld, const int* perm, const MT* dinv, MT* b,
+                                              int lane) {
+  if (n <= 32) {
+    lu_solve_regs<1, MT>(A, n, ld, perm, dinv, b, lane);
+  } else if (n <= 64) {
+    lu_solve_regs<2, MT>(A, n, ld, perm, dinv, b, lane);
+  } else {
+    MT g[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) g[r] = (lane + 32 * r < n) ? b[perm[lane + 32 * r]] : MT(0);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (lane + 32 * r < n) b[lane + 32 * r] = g[r];
+    __syncwarp();
+    for (int j = 0; j < n - 1; ++j) {
+      const MT xj = b[j];
+      for (int i = j + 1 + lane; i < n; i += 32) b[i] = fma_t(-A[i * ld + j], xj, b[i]);
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) b[i] *= dinv[i];
+    __syncwarp();
+    for (int j = n - 1; j > 0; --j) {
+      const MT xj = b[j];
+      for (int i = lane; i < j; i += 32) b[i] = fma_t(-A[i * ld + j], xj, b[i]);
+      __syncwarp();
+    }
+  }
+}
+
 // ------------------------------------------------------------------ stage kernel
 
 struct StageArgs {
@@ -673,21 +784,26 @@ __device__ __forceinline__ double wrms_update(const double* d, const double* Z, 
   return isnan(nrm) ? (double)INFINITY : nrm;
 }
 
-// Jacobian at Z, M = I - hg J, LU.  Returns the LU info (0 = ok).  PREC32: the
-// assembly (from FP64 rates), the matrix and its factors are FP32.
+// Jacobian at Z, M = I - hg J, LU; the row interchanges are kept as a permutation
+// (piv_to_perm).  Returns the LU info (0 = ok).  PREC32: the assembly (from FP64
+// rates), the matrix and its factors are FP32.
 template <bool PREC32>
 __device__ __forceinline__ int refresh_matrix(const Tab& t, const WS& w, const double* Z, double p, double hg, int lane) {
   Scal s;
   chem_eval<true>(t, w, Z, p, s, lane);
+  int rc;
   if (PREC32) {
     const JacIn<float> in = jac_in32(t, w, lane);
     chem_jac<float>(t, w, Z, s, w.M32, in, lane);
     form_newton_matrix<float>(w.M32, t.n, w.ld, hg, lane);
-    return lu_factor_warp<true, float>(w.M32, t.n, w.ld, w.piv, w.dinv32, lane);
+    rc = lu_factor_warp<true, float>(w.M32, t.n, w.ld, w.piv, w.dinv32, lane);
+  } else {
+    chem_jac<double>(t, w, Z, s, w.M, jac_in64(t, w), lane);
+    form_newton_matrix<double>(w.M, t.n, w.ld, hg, lane);
+    rc = lu_factor_warp<true, double>(w.M, t.n, w.ld, w.piv, w.dinv, lane);
   }
-  chem_jac<double>(t, w, Z, s, w.M, jac_in64(t, w), lane);
-  form_newton_matrix<double>(w.M, t.n, w.ld, hg, lane);
-  return lu_factor_warp<true, double>(w.M, t.n, w.ld, w.piv, w.dinv, lane);
+  if (rc == 0) piv_to_perm(w.piv, t.n, lane);
+  return rc;
 }
 
 // Newton correction: d <- M^-1 d.  PREC32: the FP64 residual is rounded to FP32,
@@ -699,11 +815,11 @@ __device__ __forceinline__ void newton_solve(const WS& w, int n, int lane) {
   if (PREC32) {
     for (int k = lane; k < n; k += 32) w.d32[k] = (float)w.d[k];
     __syncwarp();
-    lu_solve_warp<true, float>(w.M32, n, w.ld, w.piv, w.dinv32, w.d32, lane);
+    lu_solve_perm<float>(w.M32, n, w.ld, w.piv, w.dinv32, w.d32, lane);
     for (int k = lane; k < n; k += 32) w.d[k] = (double)w.d32[k];
     __syncwarp();
   } else {
-    lu_solve_warp<true, double>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane);
+    lu_solve_perm<double>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane);
   }
 }
 
@@ -1061,8 +1177,11 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
   }
 }
 
+// The launch is planned at one CTA per SM or more, each of at most kMaxWarps warps;
+// the minimum of one block lets ptxas spend the whole per-thread register budget
+// (without it ptxas settles on far fewer registers and spills).
 template <bool PREC32>
-__global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_kernel(StageArgs a) {
+__global__ void __launch_bounds__(kMaxWarps * 32, 1) stage_fast_kernel(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sA[3][3], sc[3];    // SDIRK tableau, indexed by the runtime stage
   stage_table(smem, a.table, a.L.bytes);

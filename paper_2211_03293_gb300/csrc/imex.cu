@@ -24,8 +24,23 @@ struct Lap7 {
   double centre, w[3];   // operator A = I - a L: centre weight and the neighbour weight per axis
 };
 
+// Device-side progress of one solve: finished (every component converged), the
+// iterations taken and the per-component scalars.  The scalar kernels run as one
+// block of one thread per component, so the "any component still iterating" test is
+// a block vote and needs no atomics.
+struct CgState {
+  int finished;
+  int iterations;
+};
+
+struct CgScal {          // per component
+  double rz, alpha, beta, bb;
+  int done;
+};
+
 // y = A x on [ncell][n]
-__global__ void apply_kernel(const double* __restrict__ x, double* __restrict__ y, Lap7 s) {
+__global__ void apply_kernel(const double* __restrict__ x, double* __restrict__ y, Lap7 s, const CgState* cs) {
+  if (cs && cs->finished) return;
   const long long total = (long long)s.nx * s.ny * s.nz * s.n;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -55,7 +70,8 @@ __global__ void apply_kernel(const double* __restrict__ x, double* __restrict__ 
 // part[block][q] = sum over this block's cells of u[cell][q] * v[cell][q]; thread q of
 // the block owns component q (blockDim >= n), so the sums are in a fixed order.
 __global__ void dot_partial_kernel(const double* __restrict__ u, const double* __restrict__ v, long long ncell, int n,
-                                   double* __restrict__ part) {
+                                   double* __restrict__ part, const CgState* cs) {
+  if (cs && cs->finished) return;
   const int q = threadIdx.x;
   if (q >= n) return;
   double acc = 0.0;
@@ -69,31 +85,35 @@ __device__ __forceinline__ double sum_parts(const double* part, int nblk, int n,
   return s;
 }
 
-struct CgScal {          // per component
-  double rz, alpha, beta, bb;
-  int done;
-};
-
-// after r = b - A x and z = r / diag: rz = <r, z>, bb = <b, b> (both from partials)
+// after r = b - A x and z = r / diag: rz = <r, z>, bb = <b, b> (both from partials).
+// One block, thread q = component q.
 __global__ void cg_init_kernel(const double* part_rz, const double* part_bb, int nblk, int n, double diag, double tol,
-                               CgScal* sc, int* all_done) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  CgScal s;
-  s.rz = sum_parts(part_rz, nblk, n, q);
-  s.bb = sum_parts(part_bb, nblk, n, q);
-  s.alpha = s.beta = 0.0;
-  // Jacobi: z = r / diag, so |r|^2 = diag <r, z>.  The residual is measured against
-  // |b|; a component with b = 0 is measured against its initial residual instead.
-  if (!(s.bb > 0.0)) s.bb = s.rz * diag;
-  s.done = (s.rz * diag <= tol * tol * s.bb) ? 1 : 0;
-  sc[q] = s;
-  if (!s.done) atomicExch(all_done, 0);
+                               CgScal* sc, CgState* cs) {
+  const int q = threadIdx.x;
+  bool active = false;
+  if (q < n) {
+    CgScal s;
+    s.rz = sum_parts(part_rz, nblk, n, q);
+    s.bb = sum_parts(part_bb, nblk, n, q);
+    s.alpha = s.beta = 0.0;
+    // Jacobi: z = r / diag, so |r|^2 = diag <r, z>.  The residual is measured against
+    // |b|; a component with b = 0 is measured against its initial residual instead.
+    if (!(s.bb > 0.0)) s.bb = s.rz * diag;
+    s.done = (s.rz * diag <= tol * tol * s.bb) ? 1 : 0;
+    sc[q] = s;
+    active = !s.done;
+  }
+  const int any = __syncthreads_or(active);
+  if (q == 0) {
+    cs->finished = any ? 0 : 1;
+    cs->iterations = 0;
+  }
 }
 
 // alpha = <r, z> / <p, A p>
-__global__ void cg_alpha_kernel(const double* part_pq, int nblk, int n, CgScal* sc) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void cg_alpha_kernel(const double* part_pq, int nblk, int n, CgScal* sc, const CgState* cs) {
+  if (cs->finished) return;
+  const int q = threadIdx.x;
   if (q >= n) return;
   const double pq = sum_parts(part_pq, nblk, n, q);
   sc[q].alpha = (sc[q].done || !(pq > 0.0)) ? 0.0 : sc[q].rz / pq;
@@ -101,7 +121,8 @@ __global__ void cg_alpha_kernel(const double* part_pq, int nblk, int n, CgScal* 
 
 // x += alpha p; r -= alpha A p; z = r / diag
 __global__ void cg_update_kernel(double* x, double* r, double* z, const double* p, const double* Ap, long long len,
-                                 int n, double inv_diag, const CgScal* sc) {
+                                 int n, double inv_diag, const CgScal* sc, const CgState* cs) {
+  if (cs->finished) return;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len;
        e += (long long)gridDim.x * blockDim.x) {
     const int q = (int)(e % n);
@@ -113,26 +134,35 @@ __global__ void cg_update_kernel(double* x, double* r, double* z, const double* 
   }
 }
 
-// beta = <r, z>_new / <r, z>_old; convergence on |r|^2 = diag <r, z>
+// beta = <r, z>_new / <r, z>_old; convergence on |r|^2 = diag <r, z>.  One block.
 __global__ void cg_beta_kernel(const double* part_rz, int nblk, int n, double diag, double tol, CgScal* sc,
-                               int* all_done) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  CgScal s = sc[q];
-  if (!s.done) {
-    const double rz = sum_parts(part_rz, nblk, n, q);
-    s.beta = (s.rz > 0.0) ? rz / s.rz : 0.0;
-    s.rz = rz;
-    if (rz * diag <= tol * tol * s.bb) s.done = 1;
-  } else {
-    s.beta = 0.0;
+                               CgState* cs) {
+  if (cs->finished) return;     // uniform over the block: read before anyone writes
+  const int q = threadIdx.x;
+  bool active = false;
+  if (q < n) {
+    CgScal s = sc[q];
+    if (!s.done) {
+      const double rz = sum_parts(part_rz, nblk, n, q);
+      s.beta = (s.rz > 0.0) ? rz / s.rz : 0.0;
+      s.rz = rz;
+      if (rz * diag <= tol * tol * s.bb) s.done = 1;
+    } else {
+      s.beta = 0.0;
+    }
+    sc[q] = s;
+    active = !s.done;
   }
-  sc[q] = s;
-  if (!s.done) atomicExch(all_done, 0);
+  const int any = __syncthreads_or(active);
+  if (q == 0) {
+    cs->iterations += 1;
+    if (!any) cs->finished = 1;
+  }
 }
 
 // p = z + beta p (components still iterating)
-__global__ void cg_dir_kernel(double* p, const double* z, long long len, int n, const CgScal* sc) {
+__global__ void cg_dir_kernel(double* p, const double* z, long long len, int n, const CgScal* sc, const CgState* cs) {
+  if (cs->finished) return;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len;
        e += (long long)gridDim.x * blockDim.x) {
     const int q = (int)(e % n);
@@ -150,6 +180,12 @@ __global__ void cg_start_kernel(const double* b, double* r, double* z, double* p
     z[e] = zz;
     p[e] = zz;
   }
+}
+
+// info[0] = converged, info[1] = iterations
+__global__ void cg_info_kernel(const CgState* cs, int32_t* info) {
+  info[0] = cs->finished;
+  info[1] = cs->iterations;
 }
 
 // out = u + s v
@@ -187,9 +223,13 @@ bool grid_ok2(const mri_grid* g) {
 
 }  // namespace
 
-// The CG solve; ws: 4 len + kRedBlocks (2 n) doubles, then n CgScal and an int.
+// The CG solve; ws: 4 len + kRedBlocks (2 n) doubles, then n CgScal and the CgState.
+// check_every > 0: the host reads the device state every check_every iterations
+// (synchronising the stream) and returns once it is finished; check_every = 0: all
+// max_iter iterations are enqueued without synchronisation (their launches do nothing
+// once the solve is finished), so the sequence can be captured in a CUDA graph.
 int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double a, double tol, int max_iter,
-                    void* ws, int* iters, cudaStream_t st) {
+                    int check_every, void* ws, int* iters, int32_t* info, cudaStream_t st) {
   const long long ncell = (long long)g->nx * g->ny * g->nz, len = ncell * n;
   double* r = static_cast<double*>(ws);
   double* z = r + len;
@@ -198,50 +238,52 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
   double* part1 = Ap + len;
   double* part2 = part1 + (size_t)kRedBlocks * n;
   CgScal* sc = reinterpret_cast<CgScal*>(part2 + (size_t)kRedBlocks * n);
-  int* all_done = reinterpret_cast<int*>(sc + n);
+  CgState* cs = reinterpret_cast<CgState*>(sc + n);
   const Lap7 op = make_op(g, n, a);
   const double diag = op.centre, inv_diag = 1.0 / op.centre;
   const int eb = elementwise_blocks(len);
   const int nblk = (int)(ncell < kRedBlocks ? ncell : kRedBlocks);
   const int rt = ((n + 31) / 32) * 32;
-  const int sb = (n + 127) / 128;
   if (iters) *iters = 0;
-  if (cudaMemsetAsync(all_done, 0xff, sizeof(int), st) != cudaSuccess) return MRI_ECUDA;   // nonzero: done
-  apply_kernel<<<eb, 256, 0, st>>>(x, r, op);
+  apply_kernel<<<eb, 256, 0, st>>>(x, r, op, nullptr);
   cg_start_kernel<<<eb, 256, 0, st>>>(b, r, z, p, len, inv_diag);
-  dot_partial_kernel<<<nblk, rt, 0, st>>>(r, z, ncell, n, part1);
-  dot_partial_kernel<<<nblk, rt, 0, st>>>(b, b, ncell, n, part2);
-  cg_init_kernel<<<sb, 128, 0, st>>>(part1, part2, nblk, n, diag, tol, sc, all_done);
+  // the initial reductions run unconditionally: cs is first written by cg_init
+  dot_partial_kernel<<<nblk, rt, 0, st>>>(r, z, ncell, n, part1, nullptr);
+  dot_partial_kernel<<<nblk, rt, 0, st>>>(b, b, ncell, n, part2, nullptr);
+  cg_init_kernel<<<1, rt, 0, st>>>(part1, part2, nblk, n, diag, tol, sc, cs);
   if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
+  CgState h{};
   for (int it = 0; it < max_iter; ++it) {
-    if (it % kCheckEvery == 0) {
-      int h = 0;
-      if (cudaMemcpyAsync(&h, all_done, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (check_every > 0 && it % check_every == 0) {
+      if (cudaMemcpyAsync(&h, cs, sizeof(CgState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess)
         return MRI_ECUDA;
-      if (h != 0) return MRI_OK;
-      if (cudaMemsetAsync(all_done, 0xff, sizeof(int), st) != cudaSuccess) return MRI_ECUDA;
+      if (h.finished) break;
     }
-    apply_kernel<<<eb, 256, 0, st>>>(p, Ap, op);
-    dot_partial_kernel<<<nblk, rt, 0, st>>>(p, Ap, ncell, n, part1);
-    cg_alpha_kernel<<<sb, 128, 0, st>>>(part1, nblk, n, sc);
-    cg_update_kernel<<<eb, 256, 0, st>>>(x, r, z, p, Ap, len, n, inv_diag, sc);
-    dot_partial_kernel<<<nblk, rt, 0, st>>>(r, z, ncell, n, part1);
-    cg_beta_kernel<<<sb, 128, 0, st>>>(part1, nblk, n, diag, tol, sc, all_done);
-    cg_dir_kernel<<<eb, 256, 0, st>>>(p, z, len, n, sc);
+    apply_kernel<<<eb, 256, 0, st>>>(p, Ap, op, cs);
+    dot_partial_kernel<<<nblk, rt, 0, st>>>(p, Ap, ncell, n, part1, cs);
+    cg_alpha_kernel<<<1, rt, 0, st>>>(part1, nblk, n, sc, cs);
+    cg_update_kernel<<<eb, 256, 0, st>>>(x, r, z, p, Ap, len, n, inv_diag, sc, cs);
+    dot_partial_kernel<<<nblk, rt, 0, st>>>(r, z, ncell, n, part1, cs);
+    cg_beta_kernel<<<1, rt, 0, st>>>(part1, nblk, n, diag, tol, sc, cs);
+    cg_dir_kernel<<<eb, 256, 0, st>>>(p, z, len, n, sc, cs);
     if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
-    if (iters) *iters = it + 1;
   }
-  int h = 0;
-  if (cudaMemcpyAsync(&h, all_done, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  if (info) {
+    cg_info_kernel<<<1, 1, 0, st>>>(cs, info);
+    if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
+  }
+  if (check_every == 0) return MRI_OK;
+  if (cudaMemcpyAsync(&h, cs, sizeof(CgState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return MRI_ECUDA;
-  return h != 0 ? MRI_OK : MRI_ECONV;
+  if (iters) *iters = h.iterations;
+  return h.finished ? MRI_OK : MRI_ECONV;
 }
 
 size_t diffusion_ws_doubles(const mri_grid* g, int n) {
   const size_t len = (size_t)g->nx * g->ny * g->nz * n;
-  return 4 * len + 2 * (size_t)kRedBlocks * n + (sizeof(CgScal) * (size_t)n + sizeof(int) + 7) / 8;
+  return 4 * len + 2 * (size_t)kRedBlocks * n + (sizeof(CgScal) * (size_t)n + sizeof(CgState) + 7) / 8;
 }
 
 }  // namespace mri
@@ -252,12 +294,13 @@ extern "C" size_t mri_diffusion_workspace_size(const mri_grid* grid, int n) {
 }
 
 extern "C" int mri_diffusion_solve(double* x, const double* b, int n, const mri_grid* grid, double a, double tol,
-                                   int max_iter, void* workspace, size_t workspace_bytes, int* iterations,
-                                   void* stream) {
-  if (!mri::grid_ok2(grid) || n < 1 || n > 1024 || !x || !b || !(a >= 0) || !std::isfinite(a) || !(tol > 0) || max_iter < 0)
+                                   int max_iter, int check_every, void* workspace, size_t workspace_bytes,
+                                   int* iterations, int32_t* cg_info, void* stream) {
+  if (!mri::grid_ok2(grid) || n < 1 || n > 1024 || !x || !b || !(a >= 0) || !std::isfinite(a) || !(tol > 0) ||
+      max_iter < 0 || check_every < 0)
     return MRI_EINVAL;
   if (!workspace || workspace_bytes < mri_diffusion_workspace_size(grid, n)) return MRI_ENOMEM;
-  return mri::diffusion_solve(x, b, n, grid, a, tol, max_iter, workspace, iterations,
+  return mri::diffusion_solve(x, b, n, grid, a, tol, max_iter, check_every, workspace, iterations, cg_info,
                               static_cast<cudaStream_t>(stream));
 }
 
@@ -269,10 +312,12 @@ extern "C" size_t mri_step_imex1_workspace_size(const mri_grid* grid, int n) {
 
 extern "C" int mri_step_imex1(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
                               const mri_mech* mech, const mri_fast_opts* opts, double cg_tol, int cg_max_iter,
-                              void* workspace, size_t workspace_bytes, int32_t* cell_status, int32_t* cell_stats,
-                              int32_t* n_failed, int* cg_iterations, void* stream) {
+                              int cg_check_every, void* workspace, size_t workspace_bytes, int32_t* cell_status,
+                              int32_t* cell_stats, int32_t* n_failed, int* cg_iterations, int32_t* cg_info,
+                              void* stream) {
   if (!mri::grid_ok2(grid) || !mech || !opts || !y || !p) return MRI_EINVAL;
-  if (!(H > 0) || !(h > 0) || !std::isfinite(H) || !std::isfinite(h) || !(cg_tol > 0) || cg_max_iter < 0)
+  if (!(H > 0) || !(h > 0) || !std::isfinite(H) || !std::isfinite(h) || !(cg_tol > 0) || cg_max_iter < 0 ||
+      cg_check_every < 0)
     return MRI_EINVAL;
   if (!mri::fast_opts_ok(opts) || opts->time_budget_s != 0.0) return MRI_EINVAL;
   const mri::Mech* m = reinterpret_cast<const mri::Mech*>(mech);
@@ -304,5 +349,6 @@ extern "C" int mri_step_imex1(double* y, const double* p, const mri_grid* grid, 
   // solve-decoupled implicit correction: (I - H L) y_{n+1} = v - H L y_n, from x = v
   mri::axpy_kernel<<<eb, 256, 0, st>>>(phi, y, fI, -H, len);
   if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
-  return mri::diffusion_solve(y, phi, n, &gI, H, cg_tol, cg_max_iter, cgws, cg_iterations, st);
+  return mri::diffusion_solve(y, phi, n, &gI, H, cg_tol, cg_max_iter, cg_check_every, cgws, cg_iterations, cg_info,
+                              st);
 }

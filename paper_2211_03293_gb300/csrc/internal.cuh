@@ -71,7 +71,7 @@ struct McHeader {
   int age, tag, n, prec;
   int pad[2];
 };
-constexpr int kMcTag = 0x4D434143;   // marks a filled entry (a zeroed entry is empty)
+constexpr int kMcTag = 0x4D434144;   // marks a filled entry (a zeroed entry is empty)
 
 __host__ __device__ inline size_t mc_stride(const Layout& L, bool prec32) {
   const size_t vb = prec32 ? 4 : 8;
@@ -200,6 +200,6 @@ int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* 
 int device_smem_limit();
 int device_sm_count();
 int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double a, double tol, int max_iter,
-                    void* ws, int* iters, cudaStream_t st);
+                    int check_every, void* ws, int* iters, int32_t* info, cudaStream_t st);
 
 }  // namespace mri

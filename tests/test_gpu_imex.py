@@ -45,7 +45,7 @@ def test_diffusion_solve_reports_no_convergence(mri):
 def test_imex1_step_matches_oracle(mri, orc, name, cells):
     import torch
     w = mechgen.workload(name, cells_per_side=cells)
-    g = dict(w.grid, D=w.grid["D"] * 200)       # H D / dx^2 about 0.1: several CG iterations
+    g = dict(w.grid, D=w.grid["D"] * 200)       # H D / dx^2 about 1e-2: several CG iterations
     grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
     m = orc.Mech(w.mech)
     y0, _, _ = m.stage_fast(w.y0, w.p, None, w.H / 3, w.h, orc.opts(method=w.method, ramp=w.ramp))
@@ -61,3 +61,67 @@ def test_imex1_step_matches_oracle(mri, orc, name, cells):
                              ws, cg_tol=1e-14, cell_status=st)
     assert int((st != 0).sum()) == 0 and its > 0
     assert_parity(y.cpu().numpy(), ref, what=f"IMEX1 step {name}")
+
+
+def test_diffusion_solve_without_host_checks_matches_checked_solve(mri):
+    """check_every = 0 enqueues every iteration without synchronising: the launches
+    after convergence do nothing, so the result and iteration count are the checked
+    solve's; a solve cut short reports no convergence in cg_info."""
+    import torch
+    grid = mri.grid(24, 16, 8, 1e-4, (0.0, 0.0, 0.0), 1e-5, 2)
+    n = 9
+    b = torch.rand((24 * 16 * 8, n), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    ws = torch.empty(mri.mri_diffusion_workspace_size(grid, n), dtype=torch.uint8, device="cuda")
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    x1 = b.clone()
+    its = mri.mri_diffusion_solve(x1, b, grid, 1e-2, ws, tol=1e-13, max_iter=500, check_every=1, cg_info=info)
+    assert info.tolist() == [1, its]
+    x0 = b.clone()
+    assert mri.mri_diffusion_solve(x0, b, grid, 1e-2, ws, tol=1e-13, max_iter=500, check_every=0, cg_info=info) == -1
+    torch.cuda.synchronize()
+    assert info.tolist() == [1, its]
+    assert torch.equal(x0, x1)
+    x2 = b.clone()
+    mri.mri_diffusion_solve(x2, b, grid, 1e-2, ws, tol=1e-13, max_iter=3, check_every=0, cg_info=info)
+    torch.cuda.synchronize()
+    assert info.tolist() == [0, 3]
+
+
+def test_imex1_step_captured_in_a_cuda_graph(mri, orc):
+    """The IMEX step with cg_check_every = 0 recorded once in a CUDA graph and
+    replayed for two steps, against two oracle steps."""
+    import torch
+    w = mechgen.workload("box32", cells_per_side=8)
+    g = dict(w.grid, D=w.grid["D"] * 200)
+    grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
+    m = orc.Mech(w.mech)
+    y0, _, _ = m.stage_fast(w.y0, w.p, None, w.H / 3, w.h, orc.opts(method=w.method, ramp=w.ramp))
+    H = w.H / 2
+    ref = y0
+    for _ in range(2):
+        ref, rst, _ = orc.imex1_step(m, ref, w.p, g, H, w.h, orc.opts(method=w.method))
+        assert np.all(rst == 0)
+    gm = mri.mri_mech_load(w.mech.to_blob())
+    y = torch.tensor(y0, device="cuda")
+    p = torch.tensor(w.p, device="cuda")
+    st = torch.zeros(y0.shape[0], dtype=torch.int32, device="cuda")
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    ws = torch.empty(mri.mri_step_imex1_workspace_size(grid, w.mech.n), dtype=torch.uint8, device="cuda")
+    opts = mri.mri_fast_opts_default(method=w.method, jac_policy=1)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    y_cap = y.clone()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(graph, stream=s):
+        mri.mri_step_imex1(y_cap, p, grid, 0.0, H, w.h, gm, opts, ws, cg_tol=1e-14, cg_max_iter=200,
+                           cg_check_every=0, cell_status=st, cg_info=info, stream=s)
+    y_cap.copy_(y)
+    torch.cuda.synchronize()
+    iters = []
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        assert int((st != 0).sum()) == 0
+        iters.append(info.tolist())
+    assert all(c == 1 and 0 < k < 200 for c, k in iters), iters
+    assert_parity(y_cap.cpu().numpy(), ref, what="IMEX1 two graph replays, box 8^3")

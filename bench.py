@@ -214,12 +214,17 @@ class Bench:
         except Exception:
             self.gpu_id = str(dev.index)
 
+    def newton_safety(self, prec):
+        """The plain FP64 form keeps the library's default acceptance of modified-Newton
+        iterates; the tuned forms (mixed and learned) use the bench's setting."""
+        return 3e-4 if prec == 0 else self.args.tuned_newton_safety
+
     def opts(self, prec, ramp=0):
         w = self.w
         wpb, bps = self.shape.get(prec, (0, 0))
         o = self.mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, ramp=ramp,
                                            jac_policy=self.args.jac, precision=prec, warps_per_block=wpb,
-                                           blocks_per_sm=bps)
+                                           blocks_per_sm=bps, newton_safety=self.newton_safety(prec))
         cache = self.cache.get(prec)
         return o if cache is None else self.mri.with_matrix_cache(o, cache)
 
@@ -562,6 +567,126 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def extras(b, args):
+    """Rows of the batched form beside the headline, each measured once on the GPU:
+    the first-order IMEX-MRI step of the 32^3 box captured in a CUDA graph (fast
+    stage plus the implicit diffusion solve), the Jacobi-PCG diffusion solve alone
+    against the HBM roofline, and the mixed 9/40/80-species reactor batch in one
+    launch."""
+    import torch
+
+    import mechgen
+    mri, w, dev, st = b.mri, b.w, b.dev, b.stream
+    out = {}
+    hbm = measured_hbm_gbs()
+
+    def timed(fn, reps):
+        evs = []
+        with torch.cuda.stream(st):
+            for _ in range(reps):
+                b.flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn()
+                e1.record(st)
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, c in evs]
+
+    # IMEX-MRI step (graph-captured; the CG runs a fixed iteration cap without host checks)
+    n, ncell = b.n, b.ncell
+    y0 = torch.tensor(w.y0, device=dev)
+    o = b.opts(1)
+    with torch.cuda.stream(st):
+        for s in range(2):                       # past the start-up transient, as the MRI steps are
+            b.step(y0, 1, s == 0, None)
+    torch.cuda.synchronize()
+    ws = torch.empty(mri.mri_step_imex1_workspace_size(b.grid, n), dtype=torch.uint8, device=dev)
+    info = torch.zeros(2, dtype=torch.int32, device=dev)
+    ss = torch.zeros((ncell, 4), dtype=torch.int32, device=dev)
+    y = y0.clone()
+    graph = torch.cuda.CUDAGraph()
+    st.synchronize()
+    with torch.cuda.graph(graph, stream=st):
+        mri.mri_step_imex1(y, b.p, b.grid, 0.0, w.H, w.h, b.mech, o, ws, cg_tol=1e-12, cg_max_iter=20,
+                           cg_check_every=0, cell_stats=ss, cg_info=info, stream=st)
+    y.copy_(y0)
+    timed(graph.replay, 2)
+    ss.zero_()
+    ms = timed(graph.replay, 3)
+    sub = int(ss[:, 0].sum().item())
+    out["imex1_step"] = {
+        "what": "first-order IMEX-MRI step of the 32^3 box (fast stage over H with the explicit advection "
+                "plus diffusion forcing, then the implicit diffusion correction by Jacobi-PCG), mixed form, "
+                "captured once in a CUDA graph and replayed",
+        "ms_per_step": sum(ms) / len(ms), "cell_steps_per_s": sub / (sum(ms) * 1e-3),
+        "cg_converged": bool(info[0].item()), "cg_iterations": int(info[1].item())}
+    del graph
+
+    # Jacobi-PCG diffusion solve alone: (I - a D lap_h) x = b on the box's state with
+    # a D / dx^2 = 1, iterations fixed at the converged count, against the HBM roofline
+    g = w.grid
+    a = g["dx"] ** 2 / g["D"]
+    rhs = y0.clone()
+    x = rhs.clone()
+    cws = torch.empty(mri.mri_diffusion_workspace_size(b.grid, n), dtype=torch.uint8, device=dev)
+    its = mri.mri_diffusion_solve(x, rhs, b.grid, a, cws, tol=1e-12, max_iter=500, check_every=1, stream=st)
+    nbytes = ncell * n * 8
+
+    def solve():
+        x.copy_(rhs)
+        mri.mri_diffusion_solve(x, rhs, b.grid, a, cws, tol=1e-12, max_iter=its, check_every=0, stream=st)
+    timed(solve, 2)
+    ms = timed(solve, 5)
+    avg = sum(ms) / len(ms)
+    traffic = nbytes * (2 + 11 + its * 16)     # copy of x, the start (apply, r/z/p, two dots), 16 doubles per iteration
+    out["diffusion_cg"] = {
+        "what": "mri_diffusion_solve on the 32^3 x 41 state, a D / dx^2 = 1, tol 1e-12, no host checks",
+        "iterations": its, "ms": avg,
+        "roofline": {"bound": "hbm", "achieved": traffic / (avg * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": traffic / (avg * 1e-3) / 1e9 / hbm if hbm else None,
+                     "traffic": None,
+                     "basis": "bytes the kernels move as written: 16 doubles per element and iteration (stencil "
+                              "2, two dots 4, update 7, direction 3) plus the start and the copy of x; peak from "
+                              "MEASURED_PEAKS.json hbm_gbs"}}
+
+    # mixed 9/40/80-species batch of 0-D reactors, one launch
+    batch = mechgen.reactor_batch()
+    groups, inits = [], []
+    for mech, yy, pp in batch.groups:
+        groups.append(dict(mech=mri.mri_mech_load(mech.to_blob()), y=torch.tensor(yy, device=dev),
+                           p=torch.tensor(pp, device=dev),
+                           cell_stats=torch.zeros((yy.shape[0], 4), dtype=torch.int32, device=dev)))
+        inits.append(torch.tensor(yy, device=dev))
+    res = {}
+    for prec in (0, 1):
+        bo = mri.mri_fast_opts_default(method=batch.method, newton_rtol=batch.newton_rtol, ramp=batch.ramp,
+                                       jac_policy=mri.MRI_JAC_LAZY, precision=prec)
+
+        def launch():
+            for gg, yi in zip(groups, inits):
+                gg["y"].copy_(yi)
+            mri.mri_stage_fast_batch(groups, 0.0, batch.Hstage, batch.h, bo, stream=st)
+        timed(launch, 1)
+        for gg in groups:
+            gg["cell_stats"].zero_()
+        ms = timed(launch, 3)
+        sub = sum(int(gg["cell_stats"][:, 0].sum().item()) for gg in groups)
+        res[FORMS[prec].split(":")[0]] = {"ms_per_launch": sum(ms) / len(ms), "cell_steps_per_s": sub / (sum(ms) * 1e-3)}
+    out["reactor_batch"] = {"what": "4096 constant-pressure 0-D reactors on 9/40/80-species mechanisms "
+                                    "(21/170/350 reactions) in one mri_stage_fast_batch launch, one stage of "
+                                    "1e-7 s with h = 1e-8 s and the start-up ramp", **res}
+    return out
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -573,6 +698,8 @@ def main():
                     help="shrink the box (profiling captures only; the bench line is for 32^3)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline and the gate (profiling captures)")
     ap.add_argument("--jac", type=int, default=1, help="Newton matrix policy: 0 per substep, 1 lazy")
+    ap.add_argument("--tuned-newton-safety", type=float, default=3e-2,
+                    help="mri_fast_opts.newton_safety of the tuned forms (the plain form keeps 3e-4)")
     ap.add_argument("--prec", type=int, default=None,
                     help="time one form only: 0 plain FP64, 1 mixed precision, 2 learned start (mixed)")
     ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip the learned form")
@@ -586,6 +713,8 @@ def main():
                     help="use the automatic launch shape instead of timing the candidates")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="skip the CUDA-graph replay of the step")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the IMEX step, diffusion-solve and reactor-batch measurements")
     args = ap.parse_args()
     rank, world = dist_init(args)
 
@@ -605,6 +734,7 @@ def main():
         r["gate"] = None if (args.no_cpu or rank != 0) else b.gate(r["prec"], r["model"])
         r["model"] = None
         results[prec] = r
+    ext = extras(b, args) if args.extras else None
     if rank != 0:
         return
     ok = [p for p in forms if results[p]["gate"] is None or results[p]["gate"]["passed"]]
@@ -664,6 +794,7 @@ def main():
         "forms": {FORMS[p]: {"value": results[p]["value"], "e2e": results[p]["e2e_value"],
                              "roofline_frac": roofline(results[p])["frac"], "gate": results[p]["gate"],
                              "newton_per_substep": results[p]["newton"] / max(results[p]["substeps"], 1),
+                             "newton_safety": b.newton_safety(results[p]["prec"]),
                              "jac_per_substep": results[p]["njac"] / max(results[p]["substeps"], 1),
                              "launch": results[p]["launch"] and {k: v for k, v in results[p]["launch"].items()
                                                                  if k != "autotuned"},
@@ -678,6 +809,8 @@ def main():
                                          "replayed; device-timed like value"},
                              "clocks": results[p]["clocks"]} for p in forms},
     }
+    if ext is not None:
+        line["extras"] = ext
     print(json.dumps(line))
 
 

@@ -148,12 +148,22 @@ typedef struct {
   double ctrl_rtol;
   double ctrl_atol_Y;
   double ctrl_atol_T;
+  /* Acceptance of a Newton iterate computed with an older matrix (modified Newton,
+   * linear convergence at the rate rho = WRMS(delta_k) / WRMS(delta_k-1)): besides
+   * WRMS(delta_k) <= 1, the estimated remaining error rho WRMS(delta_k) must be at
+   * most newton_safety, 0 < newton_safety <= 1 (default 3e-4).  The default keeps
+   * each accepted stage value within about 1e-12 relative of the exact solution of
+   * the stage equation, so whole MRI steps match a full-Newton solution to 1e-10;
+   * a larger value accepts an iteration earlier more often, with the remaining error
+   * still inside the Newton tolerance.  Iterates of a fresh matrix are accepted at
+   * WRMS(delta) <= 1 either way. */
+  double newton_safety;
 } mri_fast_opts;
 
 /* Fill opts with the defaults (SDIRK3, rtol 1e-10, atol_Y 1e-20, atol_T 1e-10 K,
  * 10 Newton iterations, per-substep Jacobian, FP64, no ramp, automatic launch
  * shape, no time budget, no matrix cache, fixed substeps; controller tolerances
- * 1e-6, 1e-12, 1e-6 K for the adaptive option). */
+ * 1e-6, 1e-12, 1e-6 K for the adaptive option; Newton safety 3e-4). */
 void mri_fast_opts_default(mri_fast_opts* opts);
 
 /* One MRI stage of the fast partition for every cell (Eq. 3):

@@ -39,7 +39,7 @@ class mri_fast_opts(ct.Structure):
                 ("precision", ct.c_int), ("ramp", ct.c_int), ("warps_per_block", ct.c_int),
                 ("blocks_per_sm", ct.c_int), ("time_budget_s", ct.c_double), ("matrix_cache", ct.c_void_p),
                 ("matrix_cache_bytes", ct.c_size_t), ("adaptive", ct.c_int), ("ctrl_rtol", ct.c_double),
-                ("ctrl_atol_Y", ct.c_double), ("ctrl_atol_T", ct.c_double)]
+                ("ctrl_atol_Y", ct.c_double), ("ctrl_atol_T", ct.c_double), ("newton_safety", ct.c_double)]
 
 
 class mri_stage_group(ct.Structure):

@@ -745,11 +745,11 @@ struct StageArgs {
   double bhat[3];        // embedded weights of the error estimate
   unsigned long long budget_ns;   // 0: no time budget
   double Hs, hh, rtol, atol_Y, atol_T;
+  float newton_safety_f;
   double A[3][3], c[3], gamma;
 };
 
 constexpr int kMaxJacAge = 20;
-constexpr double kNewtonSafety = 3e-4;
 
 __device__ __forceinline__ void substep_geometry(int s, int ramp, double hh, double& tau, double& hk) {
   if (ramp > 0) {
@@ -768,7 +768,7 @@ __device__ __forceinline__ void substep_geometry(int s, int ramp, double hh, dou
 // estimates), so it is formed in FP32 from the FP64 vectors: 1e-7 relative on a
 // number compared with 1.  Corrections beyond the FP32 range give Inf, which the
 // iteration treats like an FP64 overflow.
-__device__ __forceinline__ double wrms_update(const double* d, const double* Z, int n, double rtol, double atolY, double atolT,
+__device__ __forceinline__ float wrms_update(const double* d, const double* Z, int n, double rtol, double atolY, double atolT,
                               int lane) {
   float acc = 0.0f;
   const float rt = (float)rtol, aY = (float)atolY, aT = (float)atolT;
@@ -780,8 +780,8 @@ __device__ __forceinline__ double wrms_update(const double* d, const double* Z, 
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  const double nrm = (double)sqrtf(acc / (float)n);
-  return isnan(nrm) ? (double)INFINITY : nrm;
+  const float nrm = sqrtf(acc / (float)n);
+  return isnan(nrm) ? INFINITY : nrm;
 }
 
 // Jacobian at Z, M = I - hg J, LU; the row interchanges are kept as a permutation
@@ -1021,7 +1021,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
         bool startup = startup_sub;
         bool fresh = (i == 0) && need && !predicted;   // matrix evaluated at the starting iterate (y_n)
         bool conv = false;
-        double prev = 0.0;
+        float prev = 0.0f;       // the iteration's control quantities are FP32, like the norm
         for (int attempt = 0; attempt < 2 && !conv; ++attempt) {
         if (attempt == 1) {
           if (!predicted) break;      // the start was already the previous stage value
@@ -1034,7 +1034,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
           __syncwarp();
           startup = true;
           fresh = false;
-          prev = 0.0;
+          prev = 0.0f;
         }
         for (int it = 0; it < a.max_newton; ++it) {
           Scal s;
@@ -1052,17 +1052,17 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
             fresh = true;
           }
           newton_solve<PREC32>(w, n, lane);
-          double nrm = wrms_update(w.d, w.Z, n, a.rtol, a.atol_Y, a.atol_T, lane);
+          float nrm = wrms_update(w.d, w.Z, n, a.rtol, a.atol_Y, a.atol_T, lane);
           // redo with a fresh matrix when the stale one contracts by less than 10x, or
           // when its contraction rate would not reach the tolerance three iterations
           // before max_newton
-          bool redo = !fresh && (!isfinite(nrm) || (it > 0 && nrm > 0.1 * prev));
-          if (!fresh && !redo && it > 0 && nrm > 1.0) {
-            const double rho = nrm / prev;
-            double proj = nrm;
+          bool redo = !fresh && (!isfinite(nrm) || (it > 0 && nrm > 0.1f * prev));
+          if (!fresh && !redo && it > 0 && nrm > 1.0f) {
+            const float rho = nrm / prev;
+            float proj = nrm;
             const int left = a.max_newton - 3 - (it + 1);
-            for (int j = 0; j < left && proj > 1.0; ++j) proj *= rho;
-            redo = proj > 1.0;
+            for (int j = 0; j < left && proj > 1.0f; ++j) proj *= rho;
+            redo = proj > 1.0f;
           }
           if (redo) {
             if (refresh_matrix<PREC32>(t, w, w.Z, p, hg, lane) != 0) break;
@@ -1084,8 +1084,9 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
           // remaining error is about rho * nrm, which must also be small, so that the
           // accepted iterate matches the exact stage solution far inside the tolerance.
           // (a correction that is exactly zero has nothing left to converge)
-          if (nrm == 0.0 ||
-              (full_step ? (nrm <= 1.0) : (it > 0 && nrm <= 1.0 && nrm * (nrm / prev) <= kNewtonSafety))) {
+          // (prev > 0 here: a zero correction is accepted when it occurs)
+          if (nrm == 0.0f ||
+              (full_step ? (nrm <= 1.0f) : (it > 0 && nrm <= 1.0f && nrm * nrm <= a.newton_safety_f * prev))) {
             conv = true;
             break;
           }
@@ -1424,6 +1425,7 @@ static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, 
   a.max_newton = o.max_newton;
   a.jac_policy = o.jac_policy;
   a.rtol = o.newton_rtol; a.atol_Y = o.newton_atol_Y; a.atol_T = o.newton_atol_T;
+  a.newton_safety_f = (float)o.newton_safety;
   sdirk_table(o.method, a);
   a.ws_stride = ws_offsets(m.L, o.precision == MRI_PREC_FP32_LU, K).total;
   a.budget_ns = o.time_budget_s > 0 ? (unsigned long long)std::ceil(o.time_budget_s * 1e9) : 0ull;
@@ -1571,7 +1573,8 @@ bool fast_opts_ok(const mri_fast_opts* o) {
          o->time_budget_s <= 1e6 && (o->adaptive == 0 || o->adaptive == 1) &&
          (o->adaptive == 0 || (o->ctrl_rtol > 0 && std::isfinite(o->ctrl_rtol) && o->ctrl_atol_Y >= 0 &&
                                o->ctrl_atol_T >= 0 && std::isfinite(o->ctrl_atol_Y) &&
-                               std::isfinite(o->ctrl_atol_T)));
+                               std::isfinite(o->ctrl_atol_T))) &&
+         o->newton_safety > 0 && o->newton_safety <= 1.0;
 }
 
 int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* phi, int K, double Hstage,
@@ -1607,6 +1610,7 @@ extern "C" void mri_fast_opts_default(mri_fast_opts* o) {
   o->ctrl_rtol = 1e-6;
   o->ctrl_atol_Y = 1e-12;
   o->ctrl_atol_T = 1e-6;
+  o->newton_safety = 3e-4;
 }
 
 extern "C" size_t mri_matrix_cache_size(const mri_mech* mech, int ncell, int precision) {

@@ -85,7 +85,8 @@ def test_stage_argument_validation_on_host(lib):
     for kw in (dict(max_newton=0), dict(max_newton=101), dict(newton_rtol=0.0), dict(ramp=41), dict(precision=7),
                dict(warps_per_block=17), dict(warps_per_block=-1), dict(blocks_per_sm=9),
                dict(time_budget_s=-1.0), dict(time_budget_s=float("nan")), dict(adaptive=2),
-               dict(adaptive=1, ctrl_rtol=0.0), dict(adaptive=1, ctrl_atol_T=-1.0)):
+               dict(adaptive=1, ctrl_rtol=0.0), dict(adaptive=1, ctrl_atol_T=-1.0), dict(newton_safety=0.0),
+               dict(newton_safety=1.5), dict(newton_safety=float("nan"))):
         bad = lib.mri_fast_opts_default(**kw)
         assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, fake, ct.byref(bad), None, None, None,
                                 None) == lib.MRI_EINVAL

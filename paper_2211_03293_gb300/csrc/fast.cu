@@ -223,12 +223,11 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
   const double lnT = log_tab(T, t.logt);
   const double rho = (p * (1.0 / kRu)) * (invT * invS);
   const double invrho = (kRu * T) * (S * invp);
-  double ctot = 0.0, cpp = 0.0;
+  double cpp = 0.0;
   for (int k = lane; k < Ns; k += 32) {
     const double zw = Z[k] * t.invW[k];
     const double c = rho * zw;
     w.C[k] = c;
-    ctot += c;
     double cpv = fma(fma(fma(fma(t.cp[4 * nsv + k], T, t.cp[3 * nsv + k]), T, t.cp[2 * nsv + k]), T,
                          t.cp[nsv + k]), T, t.cp[k]);
     double hv = fma(fma(fma(fma(t.hh[4 * nsv + k], T, t.hh[3 * nsv + k]), T, t.hh[2 * nsv + k]), T,
@@ -252,7 +251,8 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     const double v = (lane == 0) ? C0 * C0 : (lane == 1) ? C0 : (lane == 2) ? 1.0 : (lane == 3) ? iC0 : iC0 * iC0;
     w.c0p[lane] = v;
   }
-  const double Ctot = warp_sum(ctot);
+  // sum_k C_k = rho sum_k Y_k / W_k = p / (R T): no reduction needed
+  const double Ctot = (p * (1.0 / kRu)) * invT;
   const double cpm = warp_sum(cpp);
   __syncwarp();
   // falloff, phase 1: exp(ln k0 - ln k_inf), e^{-T/T***}, e^{-T/T*}, e^{-T**/T}
@@ -516,10 +516,8 @@ __device__ __forceinline__ void form_newton_matrix(MT* M, int n, int ld, double 
 
 // ------------------------------------------------------------------ dense LU
 
-// In-place LU with partial pivoting (largest |a|; ties to the lowest row).  The
-// pivot search compares the magnitudes' IEEE bit patterns as integers, which
-// orders non-negative doubles exactly.  dinv[k] = 1 / U_kk.  Returns 0 or k+1 for
-// a zero or non-finite pivot in column k (the factorisation stops there).
+// Magnitudes as IEEE bit patterns: compared as integers they order non-negative
+// values exactly.
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
@@ -529,22 +527,30 @@ __device__ __forceinline__ unsigned long long abs_bits(float v) {
 __device__ __forceinline__ unsigned long long inf_bits(double) { return 0x7ff0000000000000ull; }
 __device__ __forceinline__ unsigned long long inf_bits(float) { return 0x7f800000ull; }
 
+// In-place LU with partial pivoting (largest |a|; ties to the lowest row) of the
+// n x n matrix A (row stride ld, n <= 128), one warp.  piv[k] is the row interchanged
+// with row k at step k, dinv[k] = 1/U_kk.  Returns 0, or k + 1 when the pivot column
+// k is zero or not finite (the factorisation stops there).
+// The trailing update runs over the flattened (row, column) pairs of the trailing
+// block, each lane stepping through its pairs without integer division.
 template <bool SCALED, typename MT>
 __device__ __forceinline__ int lu_factor_warp(MT* A, int n, int ld, int* piv, MT* dinv, int lane) {
   for (int k = 0; k < n; ++k) {
-    unsigned long long best = 0ull;
-    int bi = 0x7fffffff;
+    // largest |a| (the IEEE bit patterns compared as integers), ties to the lowest
+    // row: each lane's best, then three warp maxima (high word, low word among the
+    // lanes holding the high maximum, and 127 - row among the lanes holding both)
+    unsigned long long v = 0ull;
+    int bi = 127;
     for (int i = k + lane; i < n; i += 32) {
-      const unsigned long long v = abs_bits(A[i * ld + k]);
-      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+      const unsigned long long a = abs_bits(A[i * ld + k]);
+      if (a > v) { v = a; bi = i; }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned hmax = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned lmax = __reduce_max_sync(0xffffffffu, hi == hmax ? lo : 0u);
+    const unsigned long long best = ((unsigned long long)hmax << 32) | lmax;
     if (best == 0ull || best >= inf_bits(MT(0))) return k + 1;
+    bi = 127 - (int)__reduce_max_sync(0xffffffffu, (v == best) ? (unsigned)(127 - bi) : 0u);
     if (lane == 0) piv[k] = bi;
     if (bi != k)
       for (int j = lane; j < n; j += 32) {
@@ -558,18 +564,25 @@ __device__ __forceinline__ int lu_factor_warp(MT* A, int n, int ld, int* piv, MT
     for (int i = k + 1 + lane; i < n; i += 32) A[i * ld + k] *= inv;
     __syncwarp();
     const int m = n - k - 1;
-    for (int e = lane; e < m * m; e += 32) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      A[i * ld + j] = fma_t(-A[i * ld + k], A[k * ld + j], A[i * ld + j]);
+    if (m > 0) {
+      int q = lane / m, r = lane - q * m;      // pair e = q m + r of the trailing block
+      for (; q < m;) {
+        const int i = k + 1 + q, j = k + 1 + r;
+        A[i * ld + j] = fma_t(-A[i * ld + k], A[k * ld + j], A[i * ld + j]);
+        r += 32;
+        while (r >= m) { r -= m; ++q; }
+      }
     }
     __syncwarp();
   }
   // SCALED: the strict upper triangle is scaled row by row with 1/U_kk, so the back
   // substitution of every later solve needs no multiplication by the diagonal inverse.
   if (SCALED) {
-    for (int e = lane; e < n * n; e += 32) {
-      const int i = e / n, j = e - i * n;
+    int i = lane / n, j = lane - i * n;
+    for (; i < n;) {
       if (j > i) A[i * ld + j] *= dinv[i];
+      j += 32;
+      while (j >= n) { j -= n; ++i; }
     }
     __syncwarp();
   }

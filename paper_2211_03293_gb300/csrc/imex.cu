@@ -5,10 +5,15 @@
 // the fast stage, diffusion implicit in a solve-decoupled correction).
 //
 // All components share the operator, so the CG recurrences of the n components run
-// in lockstep, each with its own scalars: every iteration is a stencil apply, two
-// per-component reductions (block partials in fixed order, then a sum over blocks)
-// and elementwise updates; a component stops updating once its residual meets the
-// tolerance.  The host checks a device "all converged" flag every few iterations.
+// in lockstep, each with its own scalars.  The Jacobi preconditioner of (I - a L) is
+// a constant diagonal, so z = r / diag needs no array.  Every iteration is three
+// passes over the state: the stencil apply fused with the per-component partial sums
+// of p.Ap, the x / r update fused with the partial sums of r.z, and the direction
+// update; between them one block turns the partial sums into alpha and beta.  All
+// sums run in a fixed order (per thread, then over the block's cell slots, then
+// over the blocks), so a solve is deterministic.  A component stops updating once its
+// residual meets the tolerance; a device "finished" flag turns the launches after
+// convergence into no-ops, and the host may read it every few iterations.
 #include <cmath>
 
 #include "internal.cuh"
@@ -16,18 +21,18 @@
 namespace mri {
 namespace {
 
-constexpr int kRedBlocks = 512;     // blocks of the per-component reductions
-constexpr int kCheckEvery = 8;      // iterations between convergence checks on the host
+constexpr int kRedBlocks = 512;     // blocks of the fused passes (partial sums per block)
+constexpr int kPassThreads = 256;   // threads of a fused pass (at least one warp per component)
+constexpr int kPassMax = 1024;      // n <= 1024: one slot of up to 1024 threads
+constexpr int kScalThreads = 1024;  // the scalar kernels: one warp per component at a time
 
 struct Lap7 {
   int nx, ny, nz, n;
   double centre, w[3];   // operator A = I - a L: centre weight and the neighbour weight per axis
 };
 
-// Device-side progress of one solve: finished (every component converged), the
-// iterations taken and the per-component scalars.  The scalar kernels run as one
-// block of one thread per component, so the "any component still iterating" test is
-// a block vote and needs no atomics.
+// Device-side progress of one solve: finished (every component converged) and the
+// iterations taken.
 struct CgState {
   int finished;
   int iterations;
@@ -38,147 +43,193 @@ struct CgScal {          // per component
   int done;
 };
 
-// y = A x on [ncell][n]
-__global__ void apply_kernel(const double* __restrict__ x, double* __restrict__ y, Lap7 s, const CgState* cs) {
-  if (cs && cs->finished) return;
-  const long long total = (long long)s.nx * s.ny * s.nz * s.n;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long cell = e / s.n;
-    const int q = (int)(e - cell * s.n);
-    const int i = (int)(cell % s.nx), j = (int)((cell / s.nx) % s.ny), k = (int)(cell / ((long long)s.nx * s.ny));
-    double acc = s.centre * x[e];
-    if (s.nx > 1) {
-      const int ip = (i + 1 == s.nx) ? 0 : i + 1, im = (i == 0) ? s.nx - 1 : i - 1;
-      acc = fma(s.w[0], x[(((long long)k * s.ny + j) * s.nx + ip) * s.n + q] +
-                            x[(((long long)k * s.ny + j) * s.nx + im) * s.n + q], acc);
-    }
-    if (s.ny > 1) {
-      const int jp = (j + 1 == s.ny) ? 0 : j + 1, jm = (j == 0) ? s.ny - 1 : j - 1;
-      acc = fma(s.w[1], x[(((long long)k * s.ny + jp) * s.nx + i) * s.n + q] +
-                            x[(((long long)k * s.ny + jm) * s.nx + i) * s.n + q], acc);
-    }
-    if (s.nz > 1) {
-      const int kp = (k + 1 == s.nz) ? 0 : k + 1, km = (k == 0) ? s.nz - 1 : k - 1;
-      acc = fma(s.w[2], x[(((long long)kp * s.ny + j) * s.nx + i) * s.n + q] +
-                            x[(((long long)km * s.ny + j) * s.nx + i) * s.n + q], acc);
-    }
-    y[e] = acc;
+// (A x)[cell][q] for the 7-point operator
+__device__ __forceinline__ double apply_at(const double* __restrict__ x, const Lap7& s, long long cell, int q) {
+  const int i = (int)(cell % s.nx), j = (int)((cell / s.nx) % s.ny), k = (int)(cell / ((long long)s.nx * s.ny));
+  double acc = s.centre * x[cell * s.n + q];
+  if (s.nx > 1) {
+    const int ip = (i + 1 == s.nx) ? 0 : i + 1, im = (i == 0) ? s.nx - 1 : i - 1;
+    acc = fma(s.w[0], x[(((long long)k * s.ny + j) * s.nx + ip) * s.n + q] +
+                          x[(((long long)k * s.ny + j) * s.nx + im) * s.n + q], acc);
+  }
+  if (s.ny > 1) {
+    const int jp = (j + 1 == s.ny) ? 0 : j + 1, jm = (j == 0) ? s.ny - 1 : j - 1;
+    acc = fma(s.w[1], x[(((long long)k * s.ny + jp) * s.nx + i) * s.n + q] +
+                          x[(((long long)k * s.ny + jm) * s.nx + i) * s.n + q], acc);
+  }
+  if (s.nz > 1) {
+    const int kp = (k + 1 == s.nz) ? 0 : k + 1, km = (k == 0) ? s.nz - 1 : k - 1;
+    acc = fma(s.w[2], x[(((long long)kp * s.ny + j) * s.nx + i) * s.n + q] +
+                          x[(((long long)km * s.ny + j) * s.nx + i) * s.n + q], acc);
+  }
+  return acc;
+}
+
+// Layout of a fused pass: thread (slot, q), q < rt = n rounded up to a warp,
+// slot < S = kPassThreads / rt; block b takes the cells b S + slot + m (gridDim S).
+// The block's partial sums over its slots are written component-major,
+// part[q][block], in slot order.
+__device__ __forceinline__ void block_partial(double v, int n, int rt, double* __restrict__ part) {
+  __shared__ double red[kPassMax];
+  const int q = threadIdx.x % rt, slot = threadIdx.x / rt, S = blockDim.x / rt;
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (slot == 0 && q < n) {
+    double s = 0.0;
+    for (int k = 0; k < S; ++k) s += red[k * rt + q];
+    part[(size_t)q * gridDim.x + blockIdx.x] = s;
   }
 }
 
-// part[block][q] = sum over this block's cells of u[cell][q] * v[cell][q]; thread q of
-// the block owns component q (blockDim >= n), so the sums are in a fixed order.
-__global__ void dot_partial_kernel(const double* __restrict__ u, const double* __restrict__ v, long long ncell, int n,
-                                   double* __restrict__ part, const CgState* cs) {
-  if (cs && cs->finished) return;
-  const int q = threadIdx.x;
-  if (q >= n) return;
-  double acc = 0.0;
-  for (long long c = blockIdx.x; c < ncell; c += gridDim.x) acc = fma(u[c * n + q], v[c * n + q], acc);
-  part[(size_t)blockIdx.x * n + q] = acc;
+// mode 0: r = b - A x, partial sums of <r, r> and <b, b> (start)
+// mode 1: Ap = A p, partial sums of <p, Ap>
+template <int MODE>
+__global__ void __launch_bounds__(kPassMax) apply_pass_kernel(const double* __restrict__ x,
+                                                                 const double* __restrict__ bvec,
+                                                                 double* __restrict__ out, Lap7 s, int rt,
+                                                                 double* __restrict__ part1,
+                                                                 double* __restrict__ part2, const CgState* cs) {
+  if (MODE == 1 && cs->finished) return;   // uniform over the grid
+  const int q = threadIdx.x % rt, slot = threadIdx.x / rt, S = blockDim.x / rt;
+  const long long ncell = (long long)s.nx * s.ny * s.nz;
+  double a1 = 0.0, a2 = 0.0;
+  if (q < s.n)
+    for (long long c = (long long)blockIdx.x * S + slot; c < ncell; c += (long long)gridDim.x * S) {
+      const double ax = apply_at(x, s, c, q);
+      const long long e = c * s.n + q;
+      if (MODE == 0) {
+        const double bv = bvec[e];
+        const double rr = bv - ax;
+        out[e] = rr;
+        a1 = fma(rr, rr, a1);
+        a2 = fma(bv, bv, a2);
+      } else {
+        out[e] = ax;
+        a1 = fma(x[e], ax, a1);
+      }
+    }
+  block_partial(a1, s.n, rt, part1);
+  if (MODE == 0) {
+    __syncthreads();
+    block_partial(a2, s.n, rt, part2);
+  }
 }
 
-__device__ __forceinline__ double sum_parts(const double* part, int nblk, int n, int q) {
+// x += alpha p, r -= alpha Ap, partial sums of <r, r> (components still iterating)
+__global__ void __launch_bounds__(kPassMax) update_pass_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                                  const double* __restrict__ p,
+                                                                  const double* __restrict__ Ap, long long ncell,
+                                                                  int n, int rt, const CgScal* sc,
+                                                                  double* __restrict__ part, const CgState* cs) {
+  if (cs->finished) return;
+  const int q = threadIdx.x % rt, slot = threadIdx.x / rt, S = blockDim.x / rt;
+  double acc = 0.0;
+  if (q < n && !sc[q].done) {
+    const double al = sc[q].alpha;
+    for (long long c = (long long)blockIdx.x * S + slot; c < ncell; c += (long long)gridDim.x * S) {
+      const long long e = c * n + q;
+      x[e] = fma(al, p[e], x[e]);
+      const double rr = fma(-al, Ap[e], r[e]);
+      r[e] = rr;
+      acc = fma(rr, rr, acc);
+    }
+  }
+  block_partial(acc, n, rt, part);
+}
+
+// START: p = r / diag for every component; else p = r / diag + beta p for the
+// components still iterating
+template <bool START>
+__global__ void dir_kernel(double* __restrict__ p, const double* __restrict__ r, long long len, int n, double inv_diag,
+                           const CgScal* sc, const CgState* cs) {
+  if (!START && cs->finished) return;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (START) {
+      p[e] = r[e] * inv_diag;
+    } else {
+      const int q = (int)(e % n);
+      if (!sc[q].done) p[e] = fma(sc[q].beta, p[e], r[e] * inv_diag);
+    }
+  }
+}
+
+// sum over the blocks' partials of component q by one warp, in a fixed order
+__device__ __forceinline__ double sum_parts(const double* part, int nblk, int q, int lane) {
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * n + q];
+  for (int b = lane; b < nblk; b += 32) s += part[(size_t)q * nblk + b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   return s;
 }
 
-// after r = b - A x and z = r / diag: rz = <r, z>, bb = <b, b> (both from partials).
-// One block, thread q = component q.
-__global__ void cg_init_kernel(const double* part_rz, const double* part_bb, int nblk, int n, double diag, double tol,
-                               CgScal* sc, CgState* cs) {
-  const int q = threadIdx.x;
-  bool active = false;
-  if (q < n) {
-    CgScal s;
-    s.rz = sum_parts(part_rz, nblk, n, q);
-    s.bb = sum_parts(part_bb, nblk, n, q);
-    s.alpha = s.beta = 0.0;
-    // Jacobi: z = r / diag, so |r|^2 = diag <r, z>.  The residual is measured against
-    // |b|; a component with b = 0 is measured against its initial residual instead.
-    if (!(s.bb > 0.0)) s.bb = s.rz * diag;
-    s.done = (s.rz * diag <= tol * tol * s.bb) ? 1 : 0;
-    sc[q] = s;
-    active = !s.done;
+// Start: <r, z> = <r, r> / diag and <b, b>; a component with b = 0 is measured
+// against its initial residual.  Convergence: |r|_2 <= tol |b|_2.
+__global__ void __launch_bounds__(kScalThreads) cg_init_kernel(const double* part_rr, const double* part_bb, int nblk,
+                                                               int n, double inv_diag, double tol, CgScal* sc,
+                                                               CgState* cs) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int active = 0;
+  for (int q = warp; q < n; q += nw) {
+    const double rr = sum_parts(part_rr, nblk, q, lane);
+    double bb = sum_parts(part_bb, nblk, q, lane);
+    if (!(bb > 0.0)) bb = rr;
+    const int done = (rr <= tol * tol * bb) ? 1 : 0;
+    if (lane == 0) {
+      CgScal s;
+      s.rz = rr * inv_diag;
+      s.bb = bb;
+      s.alpha = 0.0;
+      s.beta = 0.0;
+      s.done = done;
+      sc[q] = s;
+    }
+    active |= !done;
   }
   const int any = __syncthreads_or(active);
-  if (q == 0) {
+  if (threadIdx.x == 0) {
     cs->finished = any ? 0 : 1;
     cs->iterations = 0;
   }
 }
 
 // alpha = <r, z> / <p, A p>
-__global__ void cg_alpha_kernel(const double* part_pq, int nblk, int n, CgScal* sc, const CgState* cs) {
+__global__ void __launch_bounds__(kScalThreads) cg_alpha_kernel(const double* part_pq, int nblk, int n, CgScal* sc,
+                                                                const CgState* cs) {
   if (cs->finished) return;
-  const int q = threadIdx.x;
-  if (q >= n) return;
-  const double pq = sum_parts(part_pq, nblk, n, q);
-  sc[q].alpha = (sc[q].done || !(pq > 0.0)) ? 0.0 : sc[q].rz / pq;
-}
-
-// x += alpha p; r -= alpha A p; z = r / diag
-__global__ void cg_update_kernel(double* x, double* r, double* z, const double* p, const double* Ap, long long len,
-                                 int n, double inv_diag, const CgScal* sc, const CgState* cs) {
-  if (cs->finished) return;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(e % n);
-    const double al = sc[q].alpha;
-    x[e] = fma(al, p[e], x[e]);
-    const double rr = fma(-al, Ap[e], r[e]);
-    r[e] = rr;
-    z[e] = rr * inv_diag;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = warp; q < n; q += nw) {
+    const double pq = sum_parts(part_pq, nblk, q, lane);
+    if (lane == 0) sc[q].alpha = (sc[q].done || !(pq > 0.0)) ? 0.0 : sc[q].rz / pq;
   }
 }
 
-// beta = <r, z>_new / <r, z>_old; convergence on |r|^2 = diag <r, z>.  One block.
-__global__ void cg_beta_kernel(const double* part_rz, int nblk, int n, double diag, double tol, CgScal* sc,
-                               CgState* cs) {
+// beta = <r, z>_new / <r, z>_old and the convergence test
+__global__ void __launch_bounds__(kScalThreads) cg_beta_kernel(const double* part_rr, int nblk, int n,
+                                                               double inv_diag, double tol, CgScal* sc,
+                                                               CgState* cs) {
   if (cs->finished) return;     // uniform over the block: read before anyone writes
-  const int q = threadIdx.x;
-  bool active = false;
-  if (q < n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int active = 0;
+  for (int q = warp; q < n; q += nw) {
+    const double rr = sum_parts(part_rr, nblk, q, lane);
     CgScal s = sc[q];
     if (!s.done) {
-      const double rz = sum_parts(part_rz, nblk, n, q);
+      const double rz = rr * inv_diag;
       s.beta = (s.rz > 0.0) ? rz / s.rz : 0.0;
       s.rz = rz;
-      if (rz * diag <= tol * tol * s.bb) s.done = 1;
+      if (rr <= tol * tol * s.bb) s.done = 1;
     } else {
       s.beta = 0.0;
     }
-    sc[q] = s;
-    active = !s.done;
+    __syncwarp();
+    if (lane == 0) sc[q] = s;
+    active |= !s.done;
   }
   const int any = __syncthreads_or(active);
-  if (q == 0) {
+  if (threadIdx.x == 0) {
     cs->iterations += 1;
     if (!any) cs->finished = 1;
-  }
-}
-
-// p = z + beta p (components still iterating)
-__global__ void cg_dir_kernel(double* p, const double* z, long long len, int n, const CgScal* sc, const CgState* cs) {
-  if (cs->finished) return;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(e % n);
-    if (!sc[q].done) p[e] = fma(sc[q].beta, p[e], z[e]);
-  }
-}
-
-// r = b - r (r holds A x on entry), z = r / diag, p = z
-__global__ void cg_start_kernel(const double* b, double* r, double* z, double* p, long long len, double inv_diag) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-       e += (long long)gridDim.x * blockDim.x) {
-    const double rr = b[e] - r[e];
-    r[e] = rr;
-    const double zz = rr * inv_diag;
-    z[e] = zz;
-    p[e] = zz;
   }
 }
 
@@ -223,7 +274,7 @@ bool grid_ok2(const mri_grid* g) {
 
 }  // namespace
 
-// The CG solve; ws: 4 len + kRedBlocks (2 n) doubles, then n CgScal and the CgState.
+// The CG solve; ws: 3 len + 2 kRedBlocks n doubles, then n CgScal and the CgState.
 // check_every > 0: the host reads the device state every check_every iterations
 // (synchronising the stream) and returns once it is finished; check_every = 0: all
 // max_iter iterations are enqueued without synchronisation (their launches do nothing
@@ -232,25 +283,24 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
                     int check_every, void* ws, int* iters, int32_t* info, cudaStream_t st) {
   const long long ncell = (long long)g->nx * g->ny * g->nz, len = ncell * n;
   double* r = static_cast<double*>(ws);
-  double* z = r + len;
-  double* p = z + len;
+  double* p = r + len;
   double* Ap = p + len;
   double* part1 = Ap + len;
   double* part2 = part1 + (size_t)kRedBlocks * n;
   CgScal* sc = reinterpret_cast<CgScal*>(part2 + (size_t)kRedBlocks * n);
   CgState* cs = reinterpret_cast<CgState*>(sc + n);
   const Lap7 op = make_op(g, n, a);
-  const double diag = op.centre, inv_diag = 1.0 / op.centre;
+  const double inv_diag = 1.0 / op.centre;
   const int eb = elementwise_blocks(len);
-  const int nblk = (int)(ncell < kRedBlocks ? ncell : kRedBlocks);
   const int rt = ((n + 31) / 32) * 32;
+  const int S = rt < kPassThreads ? kPassThreads / rt : 1;
+  const int pt = S * rt;                                   // threads of a fused pass
+  const long long want = (ncell + S - 1) / S;
+  const int nblk = (int)(want < kRedBlocks ? want : kRedBlocks);
   if (iters) *iters = 0;
-  apply_kernel<<<eb, 256, 0, st>>>(x, r, op, nullptr);
-  cg_start_kernel<<<eb, 256, 0, st>>>(b, r, z, p, len, inv_diag);
-  // the initial reductions run unconditionally: cs is first written by cg_init
-  dot_partial_kernel<<<nblk, rt, 0, st>>>(r, z, ncell, n, part1, nullptr);
-  dot_partial_kernel<<<nblk, rt, 0, st>>>(b, b, ncell, n, part2, nullptr);
-  cg_init_kernel<<<1, rt, 0, st>>>(part1, part2, nblk, n, diag, tol, sc, cs);
+  apply_pass_kernel<0><<<nblk, pt, 0, st>>>(x, b, r, op, rt, part1, part2, nullptr);
+  cg_init_kernel<<<1, kScalThreads, 0, st>>>(part1, part2, nblk, n, inv_diag, tol, sc, cs);
+  dir_kernel<true><<<eb, 256, 0, st>>>(p, r, len, n, inv_diag, sc, cs);
   if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
   CgState h{};
   for (int it = 0; it < max_iter; ++it) {
@@ -260,13 +310,11 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
         return MRI_ECUDA;
       if (h.finished) break;
     }
-    apply_kernel<<<eb, 256, 0, st>>>(p, Ap, op, cs);
-    dot_partial_kernel<<<nblk, rt, 0, st>>>(p, Ap, ncell, n, part1, cs);
-    cg_alpha_kernel<<<1, rt, 0, st>>>(part1, nblk, n, sc, cs);
-    cg_update_kernel<<<eb, 256, 0, st>>>(x, r, z, p, Ap, len, n, inv_diag, sc, cs);
-    dot_partial_kernel<<<nblk, rt, 0, st>>>(r, z, ncell, n, part1, cs);
-    cg_beta_kernel<<<1, rt, 0, st>>>(part1, nblk, n, diag, tol, sc, cs);
-    cg_dir_kernel<<<eb, 256, 0, st>>>(p, z, len, n, sc, cs);
+    apply_pass_kernel<1><<<nblk, pt, 0, st>>>(p, nullptr, Ap, op, rt, part1, nullptr, cs);
+    cg_alpha_kernel<<<1, kScalThreads, 0, st>>>(part1, nblk, n, sc, cs);
+    update_pass_kernel<<<nblk, pt, 0, st>>>(x, r, p, Ap, ncell, n, rt, sc, part1, cs);
+    cg_beta_kernel<<<1, kScalThreads, 0, st>>>(part1, nblk, n, inv_diag, tol, sc, cs);
+    dir_kernel<false><<<eb, 256, 0, st>>>(p, r, len, n, inv_diag, sc, cs);
     if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
   }
   if (info) {
@@ -283,7 +331,7 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
 
 size_t diffusion_ws_doubles(const mri_grid* g, int n) {
   const size_t len = (size_t)g->nx * g->ny * g->nz * n;
-  return 4 * len + 2 * (size_t)kRedBlocks * n + (sizeof(CgScal) * (size_t)n + sizeof(CgState) + 7) / 8;
+  return 3 * len + 2 * (size_t)kRedBlocks * n + (sizeof(CgScal) * (size_t)n + sizeof(CgState) + 7) / 8;
 }
 
 }  // namespace mri

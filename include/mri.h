@@ -128,9 +128,13 @@ typedef struct {
    * steps of a run instead of refactorising at the start of every call.  The
    * caller zeroes it once (a zeroed entry is empty), keeps the cell order fixed
    * between calls that share it, and uses one cache per mechanism and precision;
-   * entries of another n or precision are ignored.  Like the lazy policy itself it
-   * changes the cost, not the converged results.  Calls that share a cache must
-   * not overlap on the GPU.  mri_stage_fast_batch rejects a cache. */
+   * entries of another n or precision are ignored.  Each entry also keeps f^F at
+   * the cell's output state; with MRI_START_PREDICTOR the next call adds its own
+   * forcing at the stage start to it and so predicts the Newton start of its first
+   * stage too (a state changed by the caller in between only makes that start
+   * worse).  Like the lazy policy itself the cache changes the cost, not the
+   * converged results.  Calls that share a cache must not overlap on the GPU.
+   * mri_stage_fast_batch rejects a cache. */
   void* matrix_cache;
   size_t matrix_cache_bytes;
   /* Adaptive substeps (the paper's fast steps are fixed; adaptivity is its stated

@@ -752,7 +752,7 @@ struct StageArgs {
   int start;             // MRI_START_*
   int32_t* n_fallback;   // counts Newton restarts from the previous stage value (nullable)
   unsigned char* mcache; // Newton-matrix cache entries (nullable), mc_stride bytes per cell
-  size_t mc_stride;
+  size_t mc_stride, mc_f_off;
   int adaptive, q;       // adaptive substeps; order of the error estimate
   double ctrl_rtol, ctrl_atol_Y, ctrl_atol_T;
   double bhat[3];        // embedded weights of the error estimate
@@ -899,6 +899,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
     int nsub = 0, nnewton = 0, njac = 0;
     double M_hg = 0.0;     // h gamma of the factorised Newton matrix (0: none yet)
     int M_age = 0;         // substeps since its Jacobian was evaluated
+    bool f_cached = false; // the cache entry holds f^F at the cell's state
     // the cell's factorised matrix from an earlier call, when the cache holds one
     unsigned char* mce = (a.mcache && a.jac_policy == MRI_JAC_LAZY && status == MRI_CELL_OK)
                              ? a.mcache + (size_t)cell * a.mc_stride : nullptr;
@@ -921,11 +922,22 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
         }
         M_hg = hd->hg;
         M_age = hd->age;
+        f_cached = (hd->has_f == 1);
       }
       __syncwarp();
     }
     bool have_Fl = false;  // w.Fl holds the last stage derivative of the previous substep
     double hk_prev = 0.0;  // size of the previous substep
+    // With the predictor start, f^F at the cell's state from the end of the previous
+    // call (the state this call starts from, unless the caller changed it since) plus
+    // this stage's forcing at its start is the derivative at the first substep's
+    // start: the first stage gets a predicted Newton start too.
+    if (f_cached && a.start == MRI_START_PREDICTOR) {
+      const double* fc = reinterpret_cast<const double*>(mce + a.mc_f_off);
+      for (int k = lane; k < n; k += 32) w.Fl[k] = fc[k] + (a.K > 0 ? w.phi[k] : 0.0);
+      __syncwarp();
+      have_Fl = true;
+    }
     bool step_failed = false;   // adaptive: Newton failed in the current step
     // adaptive substeps: time reached within the stage, next size, attempts so far
     double t_ad = 0.0, hc = a.hh;
@@ -1166,11 +1178,15 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
           for (int e = lane; e < n; e += 32) pd[e] = w.piv[e];
         }
       }
+      // f^F at the output state: the last stage derivative less the forcing it included
+      double* fc = reinterpret_cast<double*>(mce + a.mc_f_off);
+      for (int k = lane; k < n; k += 32) fc[k] = w.Fl[k] - w.r[k];
       if (lane == 0) {
         hd->hg = M_hg;
         hd->age = M_age;
         hd->n = n;
         hd->prec = PREC32 ? 1 : 0;
+        hd->has_f = (nsub > 0) ? 1 : 0;
         hd->tag = kMcTag;
       }
     } else if (mce && lane == 0) {
@@ -1447,6 +1463,7 @@ static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, 
   if (o.adaptive) a.ramp = 0;   // the controller finds its own start-up steps
   if (o.matrix_cache) {
     a.mc_stride = mc_stride(m.L, o.precision == MRI_PREC_FP32_LU);
+    a.mc_f_off = mc_f_offset(m.L, o.precision == MRI_PREC_FP32_LU);
     if (o.matrix_cache_bytes < a.mc_stride * (size_t)ncell) return MRI_EINVAL;
     a.mcache = static_cast<unsigned char*>(o.matrix_cache);
   }

@@ -65,17 +65,24 @@ struct Layout {
 };
 
 // Newton-matrix cache entry: header, then the factorised matrix (n * ld values), the
-// diagonal inverses (n values) and the pivots (n int32), in the form's precision.
+// diagonal inverses (n values) and the pivot permutation (n int32), in the form's
+// precision, then (8-byte aligned) f^F at the cell's state when the last call ended
+// (n doubles; has_f = 1 when present).
 struct McHeader {
   double hg;
   int age, tag, n, prec;
-  int pad[2];
+  int has_f, pad;
 };
-constexpr int kMcTag = 0x4D434144;   // marks a filled entry (a zeroed entry is empty)
+constexpr int kMcTag = 0x4D434145;   // marks a filled entry (a zeroed entry is empty)
 
-__host__ __device__ inline size_t mc_stride(const Layout& L, bool prec32) {
+__host__ __device__ inline size_t mc_f_offset(const Layout& L, bool prec32) {
   const size_t vb = prec32 ? 4 : 8;
   const size_t b = sizeof(McHeader) + (size_t)L.n * L.ld * vb + (size_t)L.n * vb + (size_t)L.n * 4;
+  return (b + 7) / 8 * 8;
+}
+
+__host__ __device__ inline size_t mc_stride(const Layout& L, bool prec32) {
+  const size_t b = mc_f_offset(L, prec32) + (size_t)L.n * 8;
   return (b + 127) / 128 * 128;
 }
 

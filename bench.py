@@ -796,6 +796,8 @@ def main():
                              "roofline_frac": roofline(results[p])["frac"], "gate": results[p]["gate"],
                              "newton_per_substep": results[p]["newton"] / max(results[p]["substeps"], 1),
                              "newton_safety": b.newton_safety(results[p]["prec"]),
+                             "fast_stage_cell_steps_per_s": results[p]["substeps"] / (results[p]["stage_total_ms"]
+                                                                                      * 1e-3),
                              "jac_per_substep": results[p]["njac"] / max(results[p]["substeps"], 1),
                              "launch": results[p]["launch"] and {k: v for k, v in results[p]["launch"].items()
                                                                  if k != "autotuned"},

@@ -132,3 +132,46 @@ def test_matrix_cache_keeps_results_and_saves_jacobians(mri, prec):
     small = mri.with_matrix_cache(mri.mri_fast_opts_default(**kw), cache[: cache.numel() // 2])
     with pytest.raises(mri.MriError):
         mri.mri_stage_fast(y, p, None, 0.0, w.H / 3, w.h, gm, small)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cached_derivative_predicts_the_first_stage(mri, orc, prec):
+    """With the matrix cache a call's first SDIRK stage starts from the predictor
+    built on f^F kept from the previous call: fewer Newton iterations than the same
+    call started from the input state there (the guided start with the input state
+    as guess), and both agree with the oracle."""
+    import math
+    import torch
+    w = mechgen.workload("box32", cells_per_side=8)
+    gm = mri.mri_mech_load(w.mech.to_blob())
+    nc, n = w.y0.shape
+    kw = dict(method=3, jac_policy=mri.MRI_JAC_LAZY, precision=prec)
+    cache = torch.zeros(mri.mri_matrix_cache_size(gm, nc, prec), dtype=torch.uint8, device="cuda")
+    y = torch.tensor(w.y0, device="cuda")
+    p = torch.tensor(w.p, device="cuda")
+    mri.mri_stage_fast(y, p, None, 0.0, w.H / 3, w.h, gm,
+                       mri.with_matrix_cache(mri.mri_fast_opts_default(ramp=w.ramp, **kw), cache))
+    torch.cuda.synchronize()
+    y1 = y.cpu().numpy()
+    phi = mechgen.random_forcing(21, nc, n, 1)
+    Hs = w.H * 5 / 12
+    G = math.ceil(Hs / w.h * (1 - 1e-12))
+    ref, rst, _ = orc.Mech(w.mech).stage_fast(y1, w.p, phi, Hs, w.h, orc.opts(method=3))
+    assert np.all(rst == 0)
+    counts = {}
+    for start in (mri.MRI_START_PREDICTOR, mri.MRI_START_GUESS_FIRST):
+        yy = torch.tensor(y1, device="cuda")
+        c = cache.clone()
+        ss = torch.zeros((nc, 4), dtype=torch.int32, device="cuda")
+        st = torch.zeros(nc, dtype=torch.int32, device="cuda")
+        guess = yy[:, None, :].expand(nc, G, n).contiguous()
+        mri.mri_stage_fast_guided(yy, p, torch.tensor(phi, device="cuda"), 0.0, Hs, w.h, gm,
+                                  mri.with_matrix_cache(mri.mri_fast_opts_default(**kw), c), start=start,
+                                  guess=guess, cell_status=st, cell_stats=ss)
+        torch.cuda.synchronize()
+        assert int((st != 0).sum()) == 0
+        assert_parity(yy.cpu().numpy(), ref, what=f"start {start}, form {prec}")
+        counts[start] = int(ss[:, 1].sum())
+    print(f"form {prec}: Newton iterations with the cached derivative {counts[mri.MRI_START_PREDICTOR]}, "
+          f"from the input state {counts[mri.MRI_START_GUESS_FIRST]}")
+    assert counts[mri.MRI_START_PREDICTOR] < counts[mri.MRI_START_GUESS_FIRST]

@@ -265,6 +265,20 @@ def imex1_step(mech: "Mech", y, p, g: dict, H, h, o: Opts):
     return diffusion_solve(v - H * fI, gI, H), st, ss
 
 
+def imex2_step(mech: "Mech", y, p, g: dict, H, h, o: Opts):
+    """One second-order Strang-split IMEX multirate step: a Crank-Nicolson half step
+    of the diffusion, (I - (H/4) L) y* = (I + (H/4) L) y_n (L = D lap_h, 7-point), the
+    MRI3 step over H with the chemistry fast and the advection (the grid with D = 0)
+    as the explicit slow partition, and a second Crank-Nicolson half step.  Returns
+    (y_{n+1}, status, stats)."""
+    gE = dict(g, D=0.0)
+    gI = dict(g, u=(0.0, 0.0, 0.0), order=2)
+    a = H / 4.0
+    y1 = diffusion_solve(_f64(y) + a * slow_rhs(y, gI), gI, a)
+    y2, st, ss = mech.mri_step(y1, p, gE, H, h, o)
+    return diffusion_solve(y2 + a * slow_rhs(y2, gI), gI, a), st, ss
+
+
 def sdirk_scalar(method, problem, lam, t0, t1, nsteps, y0):
     out = np.zeros(1)
     rc = lib().orc_sdirk_scalar(method, problem, lam, t0, t1, nsteps, y0, _d(out))

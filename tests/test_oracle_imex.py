@@ -82,3 +82,46 @@ def test_imex1_without_diffusion_is_one_mis_stage(orc):
     ref, rst, _ = m.stage_fast(w.y0, w.p, fE[:, None, :], H, w.h, orc.opts(method=w.method))
     assert np.all(rst == 0)
     np.testing.assert_allclose(out, ref, rtol=1e-13, atol=1e-18)
+
+
+def test_imex2_without_chemistry_and_advection_is_two_crank_nicolson_half_steps(orc):
+    """No chemistry, no advection: the MRI step is the identity and the step is
+    (I - (H/4) L)^-1 (I + (H/4) L) applied twice, checked with the dense periodic
+    Laplacian and a dense solve."""
+    mech = no_chemistry()
+    m = orc.Mech(mech)
+    nx = 10
+    g = dict(nx=nx, ny=1, nz=1, dx=1e-4, u=(0.0, 0.0, 0.0), D=1e-5, order=2)
+    rng = np.random.default_rng(6)
+    y = np.concatenate([rng.dirichlet(np.ones(3), nx), rng.uniform(500, 2000, (nx, 1))], 1)
+    H = 2e-3
+    out, st, _ = orc.imex2_step(m, y, np.full(nx, 101325.0), g, H, H / 10, orc.opts(method=3))
+    assert np.all(st == 0)
+    Ld = (np.roll(np.eye(nx), 1, 1) + np.roll(np.eye(nx), -1, 1) - 2 * np.eye(nx)) * g["D"] / g["dx"] ** 2
+    a = H / 4
+    S = np.linalg.solve(np.eye(nx) - a * Ld, np.eye(nx) + a * Ld)
+    np.testing.assert_allclose(out, S @ (S @ y), rtol=1e-12, atol=1e-15)
+
+
+def test_imex2_converges_at_second_order(orc):
+    """The coupled line problem of the first-order test: the Strang-split step's
+    error falls by about four when H halves."""
+    w = mechgen.workload("line64", cells_per_side=16)
+    m = orc.Mech(w.mech)
+    g = dict(w.grid, order=2, D=4e-4)
+    t_end = 2e-8
+    o = orc.opts(method=3, ramp=10)
+    y0, _, _ = m.stage_fast(w.y0, w.p, None, 1e-8, 1e-10, o)      # start past the initial transient
+    g2 = dict(g, order=2)
+    ref = m.single_rate(y0, w.p, g2, t_end, 800, orc.opts(method=3))
+    errs = []
+    for nsteps in (4, 8, 16):
+        H = t_end / nsteps
+        y = y0.copy()
+        for s in range(nsteps):
+            y, st, _ = orc.imex2_step(m, y, w.p, g, H, H / 10, orc.opts(method=3))
+            assert np.all(st == 0)
+        errs.append(np.max(np.abs(y[:, -1] - ref[:, -1])))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    print("errors", errs, "rates", rates)
+    assert np.all(rates > 1.7) and np.all(rates < 2.5), (errs, rates)

@@ -217,12 +217,16 @@ int mri_stage_fast(double* y, const double* p, int ncell, const double* phi, int
  * chosen start the stage is solved again with full Newton from the previous stage
  * value; n_fallback (device int32, nullable, added to) counts those restarts.  The
  * paper's explicit fast methods need no Newton start; this is part of the learned
- * form.  Other arguments, results and codes as mri_stage_fast. */
+ * form.  step_exp (device int8 [ncell], nullable; adaptive substeps only): each
+ * cell's first step is the uniform substep Hstage/n_sub times 2^step_exp[c], with
+ * step_exp clamped to [-20, 10] (the learned form's substep-size prediction; the
+ * controller takes over from the second step).  Other arguments, results and codes
+ * as mri_stage_fast. */
 int mri_stage_fast_guided(double* y, const double* p, int ncell, const double* phi, int K, double t0,
                           double Hstage, double h, const double* guess, int guess_steps, int start,
                           const mri_mech* mech,
                           const mri_fast_opts* opts, int32_t* cell_status, int32_t* cell_stats,
-                          int32_t* n_failed, int32_t* n_fallback, void* stream);
+                          int32_t* n_failed, int32_t* n_fallback, const int8_t* step_exp, void* stream);
 
 /* ---- several mechanisms in one launch ------------------------------------ */
 #define MRI_MAX_GROUPS 8
@@ -354,6 +358,24 @@ int mri_step_imex1(double* y, const double* p, const mri_grid* grid, double t, d
                    const mri_mech* mech, const mri_fast_opts* opts, double cg_tol, int cg_max_iter,
                    int cg_check_every, void* workspace, size_t workspace_bytes, int32_t* cell_status,
                    int32_t* cell_stats, int32_t* n_failed, int* cg_iterations, int32_t* cg_info, void* stream);
+
+/* One second-order IMEX multirate step over [t, t + H], Strang-split (its own
+ * scheme; the paper's IMEX-MRI-GARK tables are not printed): a Crank-Nicolson half
+ * step of the diffusion, (I - (H/4) L) y* = (I + (H/4) L) y_n with L = D lap_h
+ * (7-point), then mri_step over H with the chemistry fast and the advection (the
+ * grid with D = 0) as the explicit slow partition, then a second Crank-Nicolson
+ * half step; each half step by mri_diffusion_solve from x = y (cg_tol,
+ * cg_max_iter, cg_check_every).  mri_method: MRI_KW3.  workspace:
+ * mri_step_imex2_workspace_size bytes.  Status, stats and n_failed as mri_step;
+ * cg_iterations (host, nullable) the CG iterations of both half steps (-1 with
+ * cg_check_every = 0); cg_info (device, nullable) that of the second half step as
+ * in mri_diffusion_solve.  With cg_check_every = 0 the step does not synchronise. */
+size_t mri_step_imex2_workspace_size(const mri_grid* grid, int n);
+int mri_step_imex2(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
+                   int mri_method, const mri_mech* mech, const mri_fast_opts* opts, double cg_tol,
+                   int cg_max_iter, int cg_check_every, void* workspace, size_t workspace_bytes,
+                   int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed, int* cg_iterations,
+                   int32_t* cg_info, void* stream);
 
 /* Allocation-free variant of mri_step.  The paper has no counterpart: this is a
  * service for callers that must not allocate device memory while they run --

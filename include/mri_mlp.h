@@ -92,6 +92,13 @@ int mri_learned_targets(const double* y_in, const double* y_seq, int G, int ncel
 int mri_learned_guess(const double* y_in, const float* yhat, int ld_yhat, int G, int ncell, int n,
                       const float* tmean, const float* tstd, double* guess, void* stream);
 
+/* The network's substep-size prediction: output column col of yhat [ncell][ld_yhat]
+ * holds the standardised log2 of a cell's step relative to the uniform substep;
+ * step_exp[c] = round(tmean + tstd * yhat[c][col]) clamped to [kmin, kmax], the
+ * first-step exponent of mri_stage_fast_guided (int8, device). */
+int mri_learned_step_exp(const float* yhat, int ld_yhat, int col, int ncell, float tmean, float tstd, int kmin,
+                         int kmax, int8_t* step_exp, void* stream);
+
 /* The GEMM the network is built on, exposed for testing:
  * C [M][ldc] (FP32) = A [M][lda] * B [N][ldb]^T over K, A and B bfloat16 bit
  * patterns (uint16) with K contiguous; N a multiple of 16 in 16..256, K, lda and

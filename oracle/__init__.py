@@ -57,6 +57,8 @@ def lib():
         L.orc_mri_coupling.argtypes = [_dp, _ip]
         L.orc_stage_fast.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, _dp, ct.c_int, ct.c_double, ct.c_double,
                                      ct.POINTER(Opts), _ip, _ip, ct.c_int]
+        L.orc_stage_fast_exp.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, _dp, ct.c_int, ct.c_double,
+                                         ct.c_double, ct.POINTER(Opts), ct.c_void_p, _ip, _ip, ct.c_int]
         L.orc_slow_rhs.argtypes = [_dp, _dp, ct.c_int, ct.POINTER(Grid)]
         L.orc_mri_step.argtypes = [ct.c_void_p, _dp, _dp, ct.POINTER(Grid), ct.c_double, ct.c_double,
                                    ct.POINTER(Opts), _ip, _ip, ct.c_int]
@@ -150,8 +152,9 @@ class Mech:
         assert lib().orc_jac_cs(self.ptr, _d(y), float(p), _d(J)) == 0
         return J
 
-    def stage_fast(self, y, p, phi, Hs, h, o: Opts, nthreads=None):
-        """One MRI stage's fast IVP for every cell; returns (y_new, status, stats)."""
+    def stage_fast(self, y, p, phi, Hs, h, o: Opts, nthreads=None, step_exp=None):
+        """One MRI stage's fast IVP for every cell; returns (y_new, status, stats).
+        step_exp (int8 per cell, adaptive mode): first step = uniform substep * 2^k."""
         y = _f64(y).copy()
         ncell = y.shape[0]
         p = _f64(p)
@@ -159,8 +162,15 @@ class Mech:
         K = phi.shape[1] if phi is not None else 0
         status = np.zeros(ncell, np.int32)
         stats = np.zeros((ncell, 4), np.int32)
-        rc = lib().orc_stage_fast(self.ptr, _d(y), _d(p), ncell, _d(phi), K, float(Hs), float(h),
-                                  ct.byref(o), _i(status), _i(stats), nthreads or default_threads())
+        if step_exp is None:
+            rc = lib().orc_stage_fast(self.ptr, _d(y), _d(p), ncell, _d(phi), K, float(Hs), float(h),
+                                      ct.byref(o), _i(status), _i(stats), nthreads or default_threads())
+        else:
+            ke = np.ascontiguousarray(step_exp, dtype=np.int8)
+            assert ke.shape == (ncell,)
+            rc = lib().orc_stage_fast_exp(self.ptr, _d(y), _d(p), ncell, _d(phi), K, float(Hs), float(h),
+                                          ct.byref(o), ke.ctypes.data_as(ct.c_void_p), _i(status), _i(stats),
+                                          nthreads or default_threads())
         if rc < 0:
             raise ValueError("orc_stage_fast rejected its arguments")
         return y, status, stats

@@ -526,11 +526,11 @@ int n_substeps(double Hs, double h) {
 // sequence hh 2^-R, hh 2^-R, hh 2^(1-R), ..., hh 2^-1 (sizes sum to hh exactly), which
 // lets Newton follow a state far from the fast manifold onto it.
 int fast_stage_adaptive(const Problem& P, const Tableau& tab, double t0, double Hs, double h, double* y,
-                        const Forcing& fo, const orc_opts& o, int32_t* stats);
+                        const Forcing& fo, const orc_opts& o, int32_t* stats, int step_exp);
 
 int fast_stage_unit(const Problem& P, const Tableau& tab, double t0, double Hs, double h, double* y,
-                    const Forcing& fo, const orc_opts& o, int32_t* stats) {
-  if (o.adaptive) return fast_stage_adaptive(P, tab, t0, Hs, h, y, fo, o, stats);
+                    const Forcing& fo, const orc_opts& o, int32_t* stats, int step_exp = 0) {
+  if (o.adaptive) return fast_stage_adaptive(P, tab, t0, Hs, h, y, fo, o, stats, step_exp);
   int n_sub = n_substeps(Hs, h);
   double hh = Hs / n_sub;
   std::vector<double> tau, hs;   // substep offsets within the stage and sizes
@@ -568,15 +568,16 @@ int fast_stage_unit(const Problem& P, const Tableau& tab, double t0, double Hs, 
 }
 
 // Fast IVP over one MRI stage with adaptive substeps: start from the uniform substep
-// Hs/n_sub; after each SDIRK step accept it when the embedded error estimate is at
+// Hs/n_sub times 2^step_exp (step_exp clamped to [-20, 10]; a predicted first step);
+// after each SDIRK step accept it when the embedded error estimate is at
 // most 1 (next size factor from ctrl_factor), else repeat it with the factor (1/2 or
 // 1/4); a step whose Newton iteration fails is repeated at 1/4 of the size.  The last
 // step ends exactly at Hs; sizes never exceed Hs.  The cell fails (keeping its last
 // accepted state) when a step falls below Hs 2^-40 or after 10000 attempts.
 int fast_stage_adaptive(const Problem& P, const Tableau& tab, double t0, double Hs, double h, double* y,
-                        const Forcing& fo, const orc_opts& o, int32_t* stats) {
+                        const Forcing& fo, const orc_opts& o, int32_t* stats, int step_exp) {
   const int n_sub = n_substeps(Hs, h);
-  double hc = Hs / n_sub;
+  double hc = std::ldexp(Hs / n_sub, std::min(10, std::max(-20, step_exp)));
   const double h_floor = std::ldexp(Hs, -40);
   double t = 0.0;
   StepStats st;
@@ -640,7 +641,8 @@ void parallel_for(int count, int nthreads, Fn fn) {
 }
 
 int stage_fast(const Mech& m, double* y, const double* p, int ncell, const double* phi, int K, double Hs,
-               double h, const orc_opts& o, int32_t* status, int32_t* stats, int nthreads) {
+               double h, const orc_opts& o, int32_t* status, int32_t* stats, int nthreads,
+               const int8_t* step_exp = nullptr) {
   const int n = m.Ns + 1;
   Tableau tab = sdirk(o.method);
   std::vector<int> fails(ncell, 0);
@@ -648,7 +650,7 @@ int stage_fast(const Mech& m, double* y, const double* p, int ncell, const doubl
     ChemCell P(&m, p[c], o);
     Forcing fo{phi ? phi + (size_t)c * K * n : nullptr, phi ? K : 0};
     int32_t* sc = stats ? stats + 4 * (size_t)c : nullptr;
-    int s = fast_stage_unit(P, tab, 0.0, Hs, h, y + (size_t)c * n, fo, o, sc);
+    int s = fast_stage_unit(P, tab, 0.0, Hs, h, y + (size_t)c * n, fo, o, sc, step_exp ? step_exp[c] : 0);
     if (status) status[c] = s;
     fails[c] = s;
   });
@@ -955,6 +957,15 @@ int orc_stage_fast(const void* mech, double* y, const double* p, int ncell, cons
   if (!mech || !o || ncell < 0 || K < 0 || !(Hs > 0) || !(h > 0)) return -1;
   if (o->method != 2 && o->method != 3) return -1;
   return stage_fast(*static_cast<const Mech*>(mech), y, p, ncell, phi, K, Hs, h, *o, status, stats, nthreads);
+}
+
+int orc_stage_fast_exp(const void* mech, double* y, const double* p, int ncell, const double* phi, int K,
+                       double Hs, double h, const orc_opts* o, const int8_t* step_exp, int32_t* status,
+                       int32_t* stats, int nthreads) {
+  if (!mech || !o || ncell < 0 || K < 0 || !(Hs > 0) || !(h > 0)) return -1;
+  if (o->method != 2 && o->method != 3) return -1;
+  return stage_fast(*static_cast<const Mech*>(mech), y, p, ncell, phi, K, Hs, h, *o, status, stats, nthreads,
+                    step_exp);
 }
 
 int orc_slow_rhs(const double* y, double* f, int n, const orc_grid* g) {

@@ -88,6 +88,11 @@ int orc_mri_coupling(double* G, int* s);
 
 int orc_stage_fast(const void* mech, double* y, const double* p, int ncell, const double* phi, int K,
                    double Hs, double h, const orc_opts* o, int32_t* status, int32_t* stats, int nthreads);
+/* orc_stage_fast with, in adaptive mode, each cell's first step set to the uniform
+ * substep times 2^step_exp[c] (step_exp clamped to [-20, 10]; NULL: all 0). */
+int orc_stage_fast_exp(const void* mech, double* y, const double* p, int ncell, const double* phi, int K,
+                       double Hs, double h, const orc_opts* o, const int8_t* step_exp, int32_t* status,
+                       int32_t* stats, int nthreads);
 int orc_slow_rhs(const double* y, double* f, int n, const orc_grid* g);
 /* one MRI3 slow step; o->ramp applies to the first fast stage only */
 int orc_mri_step(const void* mech, double* y, const double* p, const orc_grid* g, double H, double h,

@@ -84,11 +84,13 @@ _lib.mri_mlp_status.argtypes = [_vp]
 _lib.mri_gemm_bf16.argtypes = [_vp, ct.c_int, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _vp, ct.c_int, _vp, _vp]
 _lib.mri_stage_fast_guided.argtypes = [_vp, _vp, ct.c_int, _vp, ct.c_int, ct.c_double, ct.c_double, ct.c_double,
                                        _vp, ct.c_int, ct.c_int, _vp, ct.POINTER(mri_fast_opts), _vp, _vp, _vp, _vp,
-                                       _vp]
+                                       _vp, _vp]
 _lib.mri_learned_features.argtypes = [_vp, _vp, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_double, _vp, _vp, _vp,
                                       ct.c_int, _vp]
 _lib.mri_learned_targets.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, ct.c_int, _vp]
 _lib.mri_learned_guess.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, _vp]
+_lib.mri_learned_step_exp.argtypes = [_vp, ct.c_int, ct.c_int, ct.c_int, ct.c_float, ct.c_float, ct.c_int, ct.c_int,
+                                      _vp, _vp]
 _lib.mri_probe_log.argtypes = [_vp, _vp, ct.c_longlong, _vp]
 _lib.mri_probe_exp_pair.argtypes = [_vp, _vp, _vp, ct.c_longlong, _vp]
 _lib.mri_matrix_cache_size.argtypes = [_vp, ct.c_int, ct.c_int]
@@ -102,6 +104,11 @@ _lib.mri_step_imex1_workspace_size.restype = ct.c_size_t
 _lib.mri_step_imex1.argtypes = [_vp, _vp, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_double, _vp,
                                 ct.POINTER(mri_fast_opts), ct.c_double, ct.c_int, ct.c_int, _vp, ct.c_size_t, _vp,
                                 _vp, _vp, ct.POINTER(ct.c_int), _vp, _vp]
+_lib.mri_step_imex2_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
+_lib.mri_step_imex2_workspace_size.restype = ct.c_size_t
+_lib.mri_step_imex2.argtypes = [_vp, _vp, ct.POINTER(mri_grid), ct.c_double, ct.c_double, ct.c_double, ct.c_int,
+                                _vp, ct.POINTER(mri_fast_opts), ct.c_double, ct.c_int, ct.c_int, _vp, ct.c_size_t,
+                                _vp, _vp, _vp, ct.POINTER(ct.c_int), _vp, _vp]
 _lib.mri_slow_rhs.argtypes = [_vp, _vp, ct.c_int, ct.POINTER(mri_grid), ct.c_double, _vp]
 _lib.mri_step_workspace_size.argtypes = [ct.POINTER(mri_grid), ct.c_int]
 _lib.mri_step_workspace_size.restype = ct.c_size_t
@@ -127,9 +134,10 @@ EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_de
             "mri_stage_fast_batch", "mri_mlp_create", "mri_mlp_free", "mri_mlp_num_params", "mri_mlp_params",
             "mri_mlp_forward", "mri_mlp_grad", "mri_mlp_grad_copy", "mri_mlp_adam", "mri_mlp_status",
             "mri_gemm_bf16", "mri_stage_fast_guided", "mri_learned_features", "mri_learned_targets",
-            "mri_learned_guess", "mri_probe_log", "mri_probe_exp_pair",
+            "mri_learned_guess", "mri_learned_step_exp", "mri_probe_log", "mri_probe_exp_pair",
             "mri_matrix_cache_size", "mri_diffusion_workspace_size", "mri_diffusion_solve",
-            "mri_step_imex1_workspace_size", "mri_step_imex1")
+            "mri_step_imex1_workspace_size", "mri_step_imex1", "mri_step_imex2_workspace_size",
+            "mri_step_imex2")
 
 
 class MriError(RuntimeError):
@@ -159,6 +167,13 @@ def _i32(t):
     import torch
     if t is not None and t.dtype != torch.int32:
         raise TypeError("int32 tensor expected")
+    return _ptr(t)
+
+
+def _i8(t):
+    import torch
+    if t is not None and t.dtype != torch.int8:
+        raise TypeError("int8 tensor expected")
     return _ptr(t)
 
 
@@ -240,14 +255,15 @@ def mri_stage_fast(y, p, phi, t0, Hstage, h, mech: Mech, opts: mri_fast_opts, ce
 
 def mri_stage_fast_guided(y, p, phi, t0, Hstage, h, mech: Mech, opts: mri_fast_opts, start=MRI_START_PREDICTOR,
                           guess=None, cell_status=None, cell_stats=None, n_failed=None, n_fallback=None,
-                          stream=None) -> int:
-    """mri_stage_fast with a chosen Newton start; guess: [ncell][n_sub][n] float64 (MRI_START_GUESS*)."""
+                          step_exp=None, stream=None) -> int:
+    """mri_stage_fast with a chosen Newton start; guess: [ncell][n_sub][n] float64 (MRI_START_GUESS*);
+    step_exp: int8 [ncell], the adaptive first step's power-of-two factor."""
     ncell = y.shape[0]
     K = 0 if phi is None else phi.shape[1]
     G = 0 if guess is None else guess.shape[1]
     rc = _lib.mri_stage_fast_guided(_f64(y), _f64(p), ncell, _f64(phi), K, t0, Hstage, h, _f64(guess), G, start,
                                     mech.handle, ct.byref(opts), _i32(cell_status), _i32(cell_stats), _i32(n_failed),
-                                    _i32(n_fallback), _stream(stream))
+                                    _i32(n_fallback), _i8(step_exp), _stream(stream))
     return _check(rc, "mri_stage_fast_guided")
 
 
@@ -332,6 +348,24 @@ def mri_step_imex1(y, p, g: mri_grid, t, H, h, mech: Mech, opts: mri_fast_opts, 
                              workspace.numel() * workspace.element_size(), _i32(cell_status), _i32(cell_stats),
                              _i32(n_failed), ct.byref(it), _i32(cg_info), _stream(stream))
     _check(rc, "mri_step_imex1")
+    return it.value if cg_check_every > 0 else -1
+
+
+def mri_step_imex2_workspace_size(g: mri_grid, n: int) -> int:
+    return int(_lib.mri_step_imex2_workspace_size(ct.byref(g), n))
+
+
+def mri_step_imex2(y, p, g: mri_grid, t, H, h, mech: Mech, opts: mri_fast_opts, workspace, cg_tol=1e-12,
+                   cg_max_iter=1000, cg_check_every=8, cell_status=None, cell_stats=None, n_failed=None,
+                   cg_info=None, stream=None, method=None) -> int:
+    """One second-order Strang-split IMEX multirate step; returns the CG iterations of
+    its two diffusion half steps (-1 with cg_check_every = 0)."""
+    it = ct.c_int(-1)
+    rc = _lib.mri_step_imex2(_f64(y), _f64(p), ct.byref(g), t, H, h, MRI_KW3 if method is None else method,
+                             mech.handle, ct.byref(opts), float(cg_tol), int(cg_max_iter), int(cg_check_every),
+                             _ptr(workspace), workspace.numel() * workspace.element_size(), _i32(cell_status),
+                             _i32(cell_stats), _i32(n_failed), ct.byref(it), _i32(cg_info), _stream(stream))
+    _check(rc, "mri_step_imex2")
     return it.value if cg_check_every > 0 else -1
 
 
@@ -500,6 +534,12 @@ def mri_learned_targets(y_in, y_seq, tmean, tinv_std, t, stream=None) -> int:
     return _check(_lib.mri_learned_targets(_f64(y_in), _f64(y_seq), y_seq.shape[1], y_in.shape[0], y_in.shape[1],
                                            _f32(tmean), _f32(tinv_std), _f32(t), t.shape[1], _stream(stream)),
                   "mri_learned_targets")
+
+
+def mri_learned_step_exp(yhat, col, tmean, tstd, step_exp, kmin=-20, kmax=10, stream=None) -> int:
+    return _check(_lib.mri_learned_step_exp(_f32(yhat), yhat.shape[1], int(col), yhat.shape[0], float(tmean),
+                                            float(tstd), int(kmin), int(kmax), _i8(step_exp), _stream(stream)),
+                  "mri_learned_step_exp")
 
 
 def mri_learned_guess(y_in, yhat, G, tmean, tstd, guess, stream=None) -> int:

@@ -751,6 +751,7 @@ struct StageArgs {
   const double* guess;   // [ncell][n_sub][n] predicted substep ends (MRI_START_GUESS*), else null
   int start;             // MRI_START_*
   int32_t* n_fallback;   // counts Newton restarts from the previous stage value (nullable)
+  const int8_t* step_exp;  // adaptive: per-cell first step exponent (nullable)
   unsigned char* mcache; // Newton-matrix cache entries (nullable), mc_stride bytes per cell
   size_t mc_stride, mc_f_off;
   int adaptive, q;       // adaptive substeps; order of the error estimate
@@ -941,6 +942,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
     bool step_failed = false;   // adaptive: Newton failed in the current step
     // adaptive substeps: time reached within the stage, next size, attempts so far
     double t_ad = 0.0, hc = a.hh;
+    if (a.adaptive && a.step_exp) hc = ldexp(a.hh, min(10, max(-20, (int)a.step_exp[cell])));
     int attempts = 0;
     for (int sidx = 0; status == MRI_CELL_OK; ++sidx) {
       double tau, hk;
@@ -1482,7 +1484,7 @@ static int take_queue(const Mech& m, StageArgs& a, cudaStream_t st) {
 int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double Hs, double h,
                       const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status, int32_t* stats,
                       int32_t* n_failed, cudaStream_t st, bool sticky, const double* guess, int start,
-                      int32_t* n_fallback) {
+                      int32_t* n_fallback, const int8_t* step_exp) {
   if (ncell == 0) return MRI_OK;
   StageArgs a;
   int rc = fill_stage_args(a, y, p, ncell, phi, K, Hs, h, m, o, ramp, status, stats, n_failed, sticky);
@@ -1490,6 +1492,7 @@ int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, 
   a.guess = guess;
   a.start = start;
   a.n_fallback = n_fallback;
+  a.step_exp = step_exp;
   const bool prec32 = (o.precision == MRI_PREC_FP32_LU);
   int warps, blocks;
   size_t smem;
@@ -1661,7 +1664,8 @@ extern "C" int mri_stage_fast(double* y, const double* p, int ncell, const doubl
 extern "C" int mri_stage_fast_guided(double* y, const double* p, int ncell, const double* phi, int K, double t0,
                                      double Hstage, double h, const double* guess, int guess_steps, int start,
                                      const mri_mech* mech, const mri_fast_opts* opts, int32_t* cell_status,
-                                     int32_t* cell_stats, int32_t* n_failed, int32_t* n_fallback, void* stream) {
+                                     int32_t* cell_stats, int32_t* n_failed, int32_t* n_fallback,
+                                     const int8_t* step_exp, void* stream) {
   (void)t0;
   if (!mech || !mri::fast_opts_ok(opts) || ncell < 0 || K < 0 || K > mri::kMaxK) return MRI_EINVAL;
   if (start < MRI_START_PREDICTOR || start > MRI_START_GUESS_FIRST) return MRI_EINVAL;
@@ -1674,7 +1678,7 @@ extern "C" int mri_stage_fast_guided(double* y, const double* p, int ncell, cons
   if (ncell > 0 && (!y || !p || (K > 0 && !phi))) return MRI_EINVAL;
   return mri::launch_stage_fast(y, p, ncell, phi, K, Hstage, h, *reinterpret_cast<const Mech*>(mech), *opts,
                                 opts->ramp, cell_status, cell_stats, n_failed, static_cast<cudaStream_t>(stream),
-                                false, guess, start, n_fallback);
+                                false, guess, start, n_fallback, step_exp);
 }
 
 extern "C" int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, double t0, double Hstage, double h,

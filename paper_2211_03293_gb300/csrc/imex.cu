@@ -400,3 +400,65 @@ extern "C" int mri_step_imex1(double* y, const double* p, const mri_grid* grid, 
   return mri::diffusion_solve(y, phi, n, &gI, H, cg_tol, cg_max_iter, cg_check_every, cgws, cg_iterations, cg_info,
                               st);
 }
+
+extern "C" size_t mri_step_imex2_workspace_size(const mri_grid* grid, int n) {
+  if (!mri::grid_ok2(grid) || n < 1) return 0;
+  const size_t len = (size_t)grid->nx * grid->ny * grid->nz * n;
+  return 2 * len * sizeof(double) + mri_diffusion_workspace_size(grid, n) + mri_step_workspace_size(grid, n);
+}
+
+namespace mri {
+namespace {
+
+// Crank-Nicolson step of the diffusion over 2a: (I - a L) y <- (I + a L) y, from
+// x = y; fI and rhs are len-sized scratch
+int cn_diffusion(double* y, int n, const mri_grid* gI, double a, double tol, int max_iter, int check_every,
+                 double* fI, double* rhs, void* cgws, int* iters, int32_t* info, cudaStream_t st) {
+  const long long len = (long long)gI->nx * gI->ny * gI->nz * n;
+  int rc = mri_slow_rhs(y, fI, n, gI, 0.0, st);
+  if (rc != MRI_OK) return rc;
+  axpy_kernel<<<elementwise_blocks(len), 256, 0, st>>>(rhs, y, fI, a, len);
+  if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
+  return diffusion_solve(y, rhs, n, gI, a, tol, max_iter, check_every, cgws, iters, info, st);
+}
+
+}  // namespace
+}  // namespace mri
+
+extern "C" int mri_step_imex2(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
+                              int mri_method, const mri_mech* mech, const mri_fast_opts* opts, double cg_tol,
+                              int cg_max_iter, int cg_check_every, void* workspace, size_t workspace_bytes,
+                              int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed, int* cg_iterations,
+                              int32_t* cg_info, void* stream) {
+  if (!mri::grid_ok2(grid) || !mech || !opts || !y || !p || mri_method != MRI_KW3) return MRI_EINVAL;
+  if (!(H > 0) || !(h > 0) || !std::isfinite(H) || !std::isfinite(h) || !(cg_tol > 0) || cg_max_iter < 0 ||
+      cg_check_every < 0)
+    return MRI_EINVAL;
+  if (!mri::fast_opts_ok(opts) || opts->time_budget_s != 0.0) return MRI_EINVAL;
+  const mri::Mech* m = reinterpret_cast<const mri::Mech*>(mech);
+  const int n = m->L.n;
+  if (n > 1024) return MRI_EINVAL;
+  if (!workspace || workspace_bytes < mri_step_imex2_workspace_size(grid, n)) return MRI_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long len = (long long)grid->nx * grid->ny * grid->nz * n;
+  double* fI = static_cast<double*>(workspace);
+  double* rhs = fI + len;
+  void* cgws = rhs + len;
+  void* stepws = static_cast<unsigned char*>(cgws) + mri_diffusion_workspace_size(grid, n);
+  // explicit slow partition of the MRI step: advection (the grid's order); the
+  // diffusion is the 7-point Laplacian of the Crank-Nicolson half steps
+  mri_grid gE = *grid, gI = *grid;
+  gE.D = 0.0;
+  gI.u[0] = gI.u[1] = gI.u[2] = 0.0;
+  gI.order = 2;
+  const double a = 0.25 * H;
+  int it1 = 0, it2 = 0;
+  int rc = mri::cn_diffusion(y, n, &gI, a, cg_tol, cg_max_iter, cg_check_every, fI, rhs, cgws, &it1, nullptr, st);
+  if (rc != MRI_OK) return rc;
+  rc = mri_step(y, p, &gE, t, H, h, mri_method, mech, opts, stepws, mri_step_workspace_size(grid, n), cell_status,
+                cell_stats, n_failed, stream);
+  if (rc != MRI_OK) return rc;
+  rc = mri::cn_diffusion(y, n, &gI, a, cg_tol, cg_max_iter, cg_check_every, fI, rhs, cgws, &it2, cg_info, st);
+  if (cg_iterations) *cg_iterations = (cg_check_every > 0) ? it1 + it2 : -1;
+  return rc;
+}

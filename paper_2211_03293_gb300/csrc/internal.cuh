@@ -198,7 +198,8 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = f
 int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, int K, double Hs, double h,
                       const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status, int32_t* stats,
                       int32_t* n_failed, cudaStream_t st, bool sticky, const double* guess = nullptr,
-                      int start = MRI_START_PREDICTOR, int32_t* n_fallback = nullptr);
+                      int start = MRI_START_PREDICTOR, int32_t* n_fallback = nullptr,
+                      const int8_t* step_exp = nullptr);
 bool fast_opts_ok(const mri_fast_opts* o);
 // mri_stage_fast after the pointer checks; sticky = write only failing statuses
 int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* phi, int K, double Hstage,

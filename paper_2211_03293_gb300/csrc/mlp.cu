@@ -618,8 +618,30 @@ __global__ void guess_kernel(const double* y_in, const float* yhat, int ld, int 
   }
 }
 
+// step_exp[c] = round(tmean + tstd * yhat[c][col]) clamped to [kmin, kmax]
+__global__ void step_exp_kernel(const float* yhat, int ld, int col, int ncell, float tmean, float tstd, int kmin,
+                                int kmax, int8_t* step_exp) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const float v = fmaf(tstd, yhat[(size_t)c * ld + col], tmean);
+    int k = (int)rintf(v);
+    if (!(v == v)) k = 0;
+    step_exp[c] = (int8_t)min(kmax, max(kmin, k));
+  }
+}
+
 }  // namespace
 }  // namespace mri
+
+extern "C" int mri_learned_step_exp(const float* yhat, int ld_yhat, int col, int ncell, float tmean, float tstd,
+                                    int kmin, int kmax, int8_t* step_exp, void* stream) {
+  if (ncell < 0 || col < 0 || ld_yhat <= col || kmin > kmax || kmin < -128 || kmax > 127) return MRI_EINVAL;
+  if (ncell == 0) return MRI_OK;
+  if (!yhat || !step_exp) return MRI_EINVAL;
+  mri::step_exp_kernel<<<grid_for(ncell), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      yhat, ld_yhat, col, ncell, tmean, tstd, kmin, kmax, step_exp);
+  return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
+}
 
 extern "C" int mri_learned_features(const double* y, const double* p, const double* phi, int K, int ncell, int n,
                                     double Hstage, const float* mean, const float* inv_std, float* x, int ld_x,

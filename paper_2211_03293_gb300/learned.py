@@ -15,7 +15,7 @@ import math
 
 import numpy as np
 
-from . import (Mlp, mri_fast_opts, mri_learned_features, mri_learned_guess,
+from . import (Mlp, mri_fast_opts, mri_learned_features, mri_learned_guess, mri_learned_step_exp,
                mri_learned_targets, mri_mlp_adam, mri_mlp_forward, mri_mlp_grad, mri_stage_fast)
 
 
@@ -166,4 +166,97 @@ class LearnedStart:
             mri_learned_features(y_in[c0:c1], p[c0:c1], ph, Hstage, self.fmean, self.finv, x[:m], stream=stream)
             mri_mlp_forward(self.net, x[:m], yh[:m], stream=stream)
             mri_learned_guess(y_in[c0:c1], yh[:m], G, self.tmean, self.tstd, out[c0:c1], stream=stream)
+        return out
+
+
+class LearnedSteps:
+    """Substep-size predictor: a network with the same inputs (2n + 2 features, 3 x 256
+    SiLU) and one output, the log2 of the adaptive controller's mean accepted step
+    relative to the uniform substep, k = log2(n_sub / accepted steps), per cell and
+    stage.  Rounded and clamped it is the first-step exponent of an adaptive stage
+    (mri_stage_fast_guided's step_exp), so that cells far from the uniform step size
+    start near their own."""
+
+    def __init__(self, n, hidden=256, layers=3, batch=4096, seed=1):
+        import torch
+        self.n, self.batch = n, batch
+        self.n_in = _pad16(2 * n + 2)
+        self.n_out = 16
+        self.dims = [self.n_in] + [hidden] * layers + [self.n_out]
+        rng = np.random.default_rng(seed)
+        params = []
+        for i, o in zip(self.dims[:-1], self.dims[1:]):
+            params.append(rng.standard_normal((o, i)).astype(np.float32).ravel() * np.float32(np.sqrt(1.0 / i)))
+            params.append(np.zeros(o, dtype=np.float32))
+        self.net = Mlp(self.dims, batch, np.concatenate(params))
+        dev = torch.device("cuda")
+        self.fmean = torch.zeros(self.n_in, dtype=torch.float32, device=dev)
+        self.finv = torch.ones(self.n_in, dtype=torch.float32, device=dev)
+        self.kmean, self.kstd = 0.0, 1.0
+        w = np.zeros(self.n_out, dtype=np.float32)
+        w[0] = 1.0
+        self.w_out = torch.tensor(w, device=dev)
+        self.records = []
+        self.step = 0
+
+    def add(self, y_in, p, phi, Hstage, h, accepted):
+        """One stage's examples: the stage inputs and the accepted step counts of an
+        adaptive solve of it (cell_stats[:, 0], host or device)."""
+        import torch
+        ncell = y_in.shape[0]
+        x = torch.empty((ncell, self.n_in), dtype=torch.float32, device=y_in.device)
+        zero = torch.zeros(self.n_in, dtype=torch.float32, device=y_in.device)
+        one = torch.ones(self.n_in, dtype=torch.float32, device=y_in.device)
+        mri_learned_features(y_in, p, phi, Hstage, zero, one, x)
+        acc = accepted.cpu().numpy() if hasattr(accepted, "cpu") else np.asarray(accepted)
+        k = np.log2(n_substeps(Hstage, h) / np.maximum(acc, 1).astype(np.float64))
+        self.records.append((x, k))
+
+    def fit(self, epochs=100, lr=1e-3, seed=0, stream=None):
+        import torch
+        X = torch.cat([r[0] for r in self.records]).cpu().numpy().astype(np.float64)
+        k = np.concatenate([r[1] for r in self.records])
+        fm, fs = X.mean(0), X.std(0)
+        fs[fs < 1e-12] = 1.0
+        self.kmean, self.kstd = float(k.mean()), float(max(k.std(), 1e-6))
+        dev = self.fmean.device
+        self.fmean = torch.tensor(fm, dtype=torch.float32, device=dev)
+        self.finv = torch.tensor(1.0 / fs, dtype=torch.float32, device=dev)
+        Xn = ((X - fm) / fs).astype(np.float32)
+        Xn[:, 2 * self.n + 2:] = 0.0
+        Tn = np.zeros((Xn.shape[0], self.n_out), dtype=np.float32)
+        Tn[:, 0] = (k - self.kmean) / self.kstd
+        perm = np.random.default_rng(seed).permutation(Xn.shape[0])
+        nb = Xn.shape[0] // self.batch
+        if nb < 1:
+            raise ValueError("fewer examples than one minibatch")
+        Xd = torch.tensor(Xn[perm[:nb * self.batch]], device=dev).view(nb, self.batch, -1)
+        Td = torch.tensor(Tn[perm[:nb * self.batch]], device=dev).view(nb, self.batch, -1)
+        y = torch.empty((self.batch, self.n_out), dtype=torch.float32, device=dev)
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        hist = []
+        for ep in range(epochs):
+            rate = lr * 0.5 * (1.0 + math.cos(math.pi * ep / epochs))
+            for bi in range(nb):
+                mri_mlp_grad(self.net, Xd[bi], Td[bi], self.w_out, y, loss, stream=stream)
+                self.step += 1
+                mri_mlp_adam(self.net, rate, self.step, stream=stream)
+            hist.append(float(loss.item()))
+        return hist
+
+    def step_exp(self, y_in, p, phi, Hstage, kmin=-20, kmax=10, stream=None):
+        """Predicted first-step exponents (int8 [ncell], device)."""
+        import torch
+        ncell = y_in.shape[0]
+        dev = y_in.device
+        out = torch.empty(ncell, dtype=torch.int8, device=dev)
+        x = torch.empty((min(ncell, self.batch), self.n_in), dtype=torch.float32, device=dev)
+        yh = torch.empty((min(ncell, self.batch), self.n_out), dtype=torch.float32, device=dev)
+        for c0 in range(0, ncell, self.batch):
+            c1 = min(ncell, c0 + self.batch)
+            m = c1 - c0
+            ph = None if phi is None else phi[c0:c1]
+            mri_learned_features(y_in[c0:c1], p[c0:c1], ph, Hstage, self.fmean, self.finv, x[:m], stream=stream)
+            mri_mlp_forward(self.net, x[:m], yh[:m], stream=stream)
+            mri_learned_step_exp(yh[:m], 0, self.kmean, self.kstd, out[c0:c1], kmin, kmax, stream=stream)
         return out

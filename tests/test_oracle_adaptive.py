@@ -81,3 +81,26 @@ def test_adaptive_stage_adapts_per_cell(orc):
     assert np.all(st == 0)
     steps = ss[:, 0]
     assert steps.max() >= 3 * steps.min(), steps
+
+
+def test_adaptive_first_step_exponent(orc):
+    """A per-cell first step (uniform substep times 2^k): k = 0 is the default
+    exactly; other first steps change the step sequence but not the accuracy the
+    controller delivers against the fine fixed-step solution."""
+    w, m, y, p = _relaxed_box_cells(orc, n=8, seed=3)
+    phi = mechgen.random_forcing(4, y.shape[0], w.mech.n, 1)
+    Hs = w.H / 4
+    tol = 1e-7
+    o = orc.opts(method=3, adaptive=1, ctrl_rtol=tol, ctrl_atol_Y=tol * 1e-6, ctrl_atol_T=tol)
+    base, st0, ss0 = m.stage_fast(y, p, phi, Hs, w.h, o)
+    same, st1, ss1 = m.stage_fast(y, p, phi, Hs, w.h, o, step_exp=np.zeros(y.shape[0], np.int8))
+    np.testing.assert_array_equal(same, base)
+    np.testing.assert_array_equal(ss1, ss0)
+    ref, rst, _ = m.stage_fast(y, p, phi, Hs, w.h / 256, orc.opts(method=3))
+    assert np.all(rst == 0)
+    k = np.array([-6, -3, -1, 1, 2, 3, -2, 0], np.int8)
+    out, st, ss = m.stage_fast(y, p, phi, Hs, w.h, o, step_exp=k)
+    assert np.all(st == 0)
+    assert not np.array_equal(ss[:, 1], ss0[:, 1])          # other step sequences were taken
+    err = np.max(np.abs(out - ref) / np.maximum(np.abs(ref), 1e-6))
+    assert err < 3e-7, err

@@ -157,3 +157,33 @@ def test_imex2_steps_match_oracle(mri, orc, name, cells):
     torch.cuda.synchronize()
     assert int((st != 0).sum()) == 0 and all(k > 0 for k in its)
     assert_parity(y.cpu().numpy(), ref, what=f"IMEX2 two steps {name}")
+
+
+def test_imex2_step_in_a_cuda_graph_equals_the_direct_call(mri):
+    """The second-order step with cg_check_every = 0 recorded in a CUDA graph and
+    replayed gives bitwise the direct call's result (the kernels are deterministic)."""
+    import torch
+    w = mechgen.workload("box32", cells_per_side=8)
+    g = dict(w.grid, D=w.grid["D"] * 200)
+    grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
+    gm = mri.mri_mech_load(w.mech.to_blob())
+    p = torch.tensor(w.p, device="cuda")
+    y0 = torch.tensor(w.y0, device="cuda")
+    mri.mri_stage_fast(y0, p, None, 0.0, w.H / 3, w.h, gm,
+                       mri.mri_fast_opts_default(method=w.method, jac_policy=1, ramp=w.ramp))
+    ws = torch.empty(mri.mri_step_imex2_workspace_size(grid, w.mech.n), dtype=torch.uint8, device="cuda")
+    opts = mri.mri_fast_opts_default(method=w.method, jac_policy=1)
+    direct = y0.clone()
+    mri.mri_step_imex2(direct, p, grid, 0.0, w.H, w.h, gm, opts, ws, cg_tol=1e-13, cg_max_iter=40, cg_check_every=0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    y = y0.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        mri.mri_step_imex2(y, p, grid, 0.0, w.H, w.h, gm, opts, ws, cg_tol=1e-13, cg_max_iter=40, cg_check_every=0,
+                           stream=s)
+    y.copy_(y0)
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, direct)

@@ -702,7 +702,60 @@ __device__ __forceinline__ void lu_solve_regs(const MT* A, int n, int ld, const 
   __syncwarp();
 }
 
-// n <= 64: the register solve; larger systems gather P b in place and run the
+// 32 < n <= 64: the register solve with a forward layout of its own.  With rows
+// lane and 32 + lane per lane, the short block (rows 32..n-1) stays active through
+// every forward step, so each step costs two FMA instructions.  The forward pass
+// instead holds rows nb + lane (nb = n - 32, the long block) and rows lane < nb
+// (the short block, needed only for the first nb columns): nb + (n - 1) instead of
+// 32 + (n - 1) FMA instructions.  One pair of shuffles then moves the solution to
+// the backward layout (rows lane and 32 + lane), where the short block is needed
+// only for the last columns.  Every row receives its updates in the same order as
+// in lu_solve_regs, so the results are the same.
+template <typename MT>
+__device__ __forceinline__ void lu_solve_regs2(const MT* A, int n, int ld, const int* perm, const MT* dinv, MT* b,
+                                               int lane) {
+  const int nb = n - 32;                 // 1..32
+  const int ra = nb + lane;              // long-block row of this lane
+  MT xa = b[perm[ra]];
+  MT xb = (lane < nb) ? b[perm[lane]] : MT(0);
+  // L y = P b
+#pragma unroll 1
+  for (int j = 0; j < nb; ++j) {         // columns held by the short block
+    const MT xj = __shfl_sync(0xffffffffu, xb, j);
+    if (lane > j && lane < nb) xb = fma_t(-A[lane * ld + j], xj, xb);
+    xa = fma_t(-A[ra * ld + j], xj, xa);
+  }
+#pragma unroll 1
+  for (int j = nb; j < n - 1; ++j) {     // columns held by the long block
+    const MT xj = __shfl_sync(0xffffffffu, xa, j - nb);
+    if (ra > j) xa = fma_t(-A[ra * ld + j], xj, xa);
+  }
+  xa *= dinv[ra];
+  if (lane < nb) xb *= dinv[lane];
+  // to rows lane (x0) and 32 + lane (x1)
+  const MT ta = __shfl_sync(0xffffffffu, xa, (lane - nb) & 31);
+  const MT tb = __shfl_sync(0xffffffffu, xa, (lane + 32 - nb) & 31);
+  MT x0 = (lane < nb) ? xb : ta;
+  MT x1 = (lane < nb) ? tb : MT(0);
+  // (D^-1 U) x = D^-1 y
+#pragma unroll 1
+  for (int j = n - 1; j >= 32; --j) {
+    const MT xj = __shfl_sync(0xffffffffu, x1, j - 32);
+    x0 = fma_t(-A[lane * ld + j], xj, x0);
+    if (32 + lane < j) x1 = fma_t(-A[(32 + lane) * ld + j], xj, x1);
+  }
+#pragma unroll 1
+  for (int j = 31; j >= 1; --j) {
+    const MT xj = __shfl_sync(0xffffffffu, x0, j);
+    if (lane < j) x0 = fma_t(-A[lane * ld + j], xj, x0);
+  }
+  __syncwarp();
+  b[lane] = x0;
+  if (lane < nb) b[32 + lane] = x1;
+  __syncwarp();
+}
+
+// n <= 64: the register solves; larger systems gather P b in place and run the
 // shared-memory substitutions of lu_solve_warp<true> (the same arithmetic).
 template <typename MT>
 __device__ __forceinline__ void lu_solve_perm(const MT* A, int n, int ld, const int* perm, const MT* dinv, MT* b,
@@ -710,7 +763,7 @@ __device__ __forceinline__ void lu_solve_perm(const MT* A, int n, int ld, const 
   if (n <= 32) {
     lu_solve_regs<1, MT>(A, n, ld, perm, dinv, b, lane);
   } else if (n <= 64) {
-    lu_solve_regs<2, MT>(A, n, ld, perm, dinv, b, lane);
+    lu_solve_regs2<MT>(A, n, ld, perm, dinv, b, lane);
   } else {
     MT g[4];
 #pragma unroll

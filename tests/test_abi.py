@@ -19,7 +19,7 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "mri.h")).read() + open(os.path.join(ROOT, "include", "mri_probe.h")).read()
+    src = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("mri.h", "mri_probe.h", "mri_mlp.h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(mri_[a-z0-9_]+)\s*\(", src)))
 
@@ -51,6 +51,7 @@ def test_defaults_and_status_strings(lib):
     assert (o.jac_policy, o.precision, o.warps_per_block, o.blocks_per_sm, o.time_budget_s) == (0, 0, 0, 0, 0.0)
     assert (o.matrix_cache, o.matrix_cache_bytes) == (None, 0)
     assert (o.adaptive, o.ctrl_rtol, o.ctrl_atol_Y, o.ctrl_atol_T) == (0, 1e-6, 1e-12, 1e-6)
+    assert o.newton_safety == 3e-4
     assert lib.mri_status_str(0) == "ok"
     assert "Newton" in lib.mri_status_str(-2)
 
@@ -108,3 +109,37 @@ def test_stage_argument_validation_on_host(lib):
     assert L.mri_slow_rhs(fake, fake, 10, ct.byref(g), 0.0, None) == lib.MRI_EINVAL
     assert L.mri_lu_solve_batched(fake, fake, 0, 1, None, None) == lib.MRI_EINVAL
     assert L.mri_lu_solve_batched(fake, fake, 129, 1, None, None) == lib.MRI_EINVAL
+
+
+def test_imex_and_diffusion_argument_validation_on_host(lib):
+    """The implicit-diffusion entry points check their arguments before any launch."""
+    L = lib._lib
+    fake = ct.c_void_p(0x1000)   # never dereferenced: the checks fire first
+    g = lib.grid(8, 8, 8, 1e-4, (1, 0, 0), 1e-5, 2)
+    need = L.mri_diffusion_workspace_size(ct.byref(g), 5)
+    assert need >= 3 * 8 ** 3 * 5 * 8
+    assert L.mri_diffusion_workspace_size(ct.byref(g), 0) == 0
+    it = ct.c_int()
+    args = dict(a=1e-3, tol=1e-12, max_iter=10, check=8, ws=fake, wsb=need)
+
+    def solve(n=5, **kw):
+        a = dict(args, **kw)
+        return L.mri_diffusion_solve(fake, fake, n, ct.byref(g), a["a"], a["tol"], a["max_iter"], a["check"],
+                                     a["ws"], a["wsb"], ct.byref(it), None, None)
+    assert solve(n=0) == lib.MRI_EINVAL
+    assert solve(n=1025) == lib.MRI_EINVAL
+    assert solve(a=-1.0) == lib.MRI_EINVAL
+    assert solve(tol=0.0) == lib.MRI_EINVAL
+    assert solve(check=-1) == lib.MRI_EINVAL
+    assert solve(wsb=need - 8) == lib.MRI_ENOMEM
+    assert solve(ws=None) == lib.MRI_ENOMEM
+    o = lib.mri_fast_opts_default()
+    assert L.mri_step_imex2(fake, fake, ct.byref(g), 0.0, 1e-7, 1e-9, 7, fake, ct.byref(o), 1e-12, 10, 8, fake,
+                            1 << 30, None, None, None, None, None, None) == lib.MRI_EINVAL
+    assert L.mri_step_imex1(fake, fake, ct.byref(g), 0.0, -1e-7, 1e-9, fake, ct.byref(o), 1e-12, 10, 8, fake,
+                            1 << 30, None, None, None, None, None, None) == lib.MRI_EINVAL
+    budget = lib.mri_fast_opts_default(time_budget_s=1.0)
+    assert L.mri_step_imex1(fake, fake, ct.byref(g), 0.0, 1e-7, 1e-9, fake, ct.byref(budget), 1e-12, 10, 8, fake,
+                            1 << 30, None, None, None, None, None, None) == lib.MRI_EINVAL
+    assert L.mri_step_imex2_workspace_size(ct.byref(g), 5) > L.mri_step_imex1_workspace_size(ct.byref(g), 5) > 0
+

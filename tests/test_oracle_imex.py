@@ -125,3 +125,16 @@ def test_imex2_converges_at_second_order(orc):
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     print("errors", errs, "rates", rates)
     assert np.all(rates > 1.7) and np.all(rates < 2.5), (errs, rates)
+
+
+def test_imex2_without_diffusion_is_one_mri3_step(orc):
+    """With D = 0 both Crank-Nicolson half steps are the identity (up to the rounding
+    of the Fourier round trips), so the step is the MRI3 step with the advection."""
+    w = mechgen.workload("line64", cells_per_side=16)
+    m = orc.Mech(w.mech)
+    g = dict(w.grid, D=0.0)
+    out, st, _ = orc.imex2_step(m, w.y0, w.p, g, w.H, w.h, orc.opts(method=w.method, ramp=w.ramp))
+    assert np.all(st == 0)
+    ref, rst, _ = m.mri_step(w.y0, w.p, g, w.H, w.h, orc.opts(method=w.method, ramp=w.ramp))
+    assert np.all(rst == 0)
+    np.testing.assert_allclose(out, ref, rtol=1e-13, atol=1e-18)

@@ -257,3 +257,16 @@ def test_mri_matches_brute_force_single_rate(orc):
     est = np.abs(one - half).max(0) / scale * 8 / 7
     assert np.all(err <= 10 * est + 1e-13), (err, est)
     assert err.max() < 1e-4
+
+
+def test_mri3_slow_evaluations_match_table2(orc):
+    """Table 2 counts 97 slow evaluations for the third-order MRI method over 32 steps:
+    one per stage start (the columns of the coupling matrix in use) per step, plus
+    the initial evaluation (tests/golden/table2_mri3_slow_evals.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_mri3_slow_evals.txt")
+    rec = dict(line.split() for line in open(path) if line.strip() and not line.startswith("#"))
+    G = orc.mri_coupling()
+    per_step = int(np.count_nonzero(np.any(G != 0.0, axis=0)))
+    assert per_step == 3
+    assert per_step * int(rec["steps"]) + 1 == int(rec["slow_evals"])

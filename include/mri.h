@@ -23,7 +23,18 @@
  *     legacy default stream); the return value covers host-side argument
  *     checks and launch errors only.  Per-cell results (Newton failure, bad
  *     input state) are written to cell_status on the device;
- *   - no call aborts or traps: errors are negative return codes.
+ *   - no call aborts or traps: errors are negative return codes;
+ *   - a mechanism belongs to the device that was current when mri_mech_load ran:
+ *     every call that uses it must be made with that device current (MRI_EINVAL
+ *     otherwise, before anything is launched);
+ *   - fast-stage launches on one mechanism may run concurrently on different
+ *     streams: each takes its own device work-queue counter, eager launches from a
+ *     ring of 256 (so at most 256 of them in flight at once) and launches recorded
+ *     into a CUDA graph by stream capture from a second ring of 256 that eager
+ *     launches never use, since a graph keeps its counter for every replay.  Graphs
+ *     whose captured launches wrapped that ring (more than 256 captured stage
+ *     launches on one mechanism) may share a counter and must not be replayed at
+ *     the same time.
  */
 #ifndef MRI_H
 #define MRI_H
@@ -368,8 +379,11 @@ int mri_step_imex1(double* y, const double* p, const mri_grid* grid, double t, d
  * cg_max_iter, cg_check_every).  mri_method: MRI_KW3.  workspace:
  * mri_step_imex2_workspace_size bytes.  Status, stats and n_failed as mri_step;
  * cg_iterations (host, nullable) the CG iterations of both half steps (-1 with
- * cg_check_every = 0); cg_info (device, nullable) that of the second half step as
- * in mri_diffusion_solve.  With cg_check_every = 0 the step does not synchronise. */
+ * cg_check_every = 0); cg_info (device, nullable, 2 ints) covers both half steps:
+ * [0] 1 only if both converged, [1] their iterations summed.  With host checks
+ * (cg_check_every > 0) a first half step that misses its tolerance ends the call
+ * with MRI_ECONV (cg_info then describes that half step alone).  With
+ * cg_check_every = 0 the step does not synchronise. */
 size_t mri_step_imex2_workspace_size(const mri_grid* grid, int n);
 int mri_step_imex2(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
                    int mri_method, const mri_mech* mech, const mri_fast_opts* opts, double cg_tol,

@@ -32,6 +32,14 @@ int mri_probe_exp_pair(const double* x, double* y, double* z, long long n, void*
  * Returns 0, -1 or -3. */
 int mri_probe_log(const double* x, double* y, long long n, void* stream);
 
+/* Test hook: record `device` as the device a loaded mechanism belongs to and return
+ * the device it was recorded on before (-1 for a NULL mechanism).  Every call that
+ * uses a mechanism checks that its device is the current one; with this hook a
+ * single-GPU test can make that check fail (and put the right device back after).
+ * Nothing else reads the recorded device. */
+typedef struct mri_mech mri_mech;
+int mri_probe_mech_device(mri_mech* mech, int device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,6 +124,7 @@ _lib.mri_method_coupling.argtypes = [ct.c_int, ct.POINTER(ct.c_double), ct.POINT
                                      ct.POINTER(ct.c_int)]
 _lib.mri_probe_fp64_fma.argtypes = [_vp, ct.c_longlong, ct.c_int, ct.POINTER(ct.c_double), _vp]
 _lib.mri_probe_exp.argtypes = [_vp, _vp, ct.c_longlong, _vp]
+_lib.mri_probe_mech_device.argtypes = [_vp, ct.c_int]
 _lib.mri_status_str.argtypes = [ct.c_int]
 _lib.mri_status_str.restype = ct.c_char_p
 
@@ -137,7 +138,7 @@ EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_de
             "mri_learned_guess", "mri_learned_step_exp", "mri_probe_log", "mri_probe_exp_pair",
             "mri_matrix_cache_size", "mri_diffusion_workspace_size", "mri_diffusion_solve",
             "mri_step_imex1_workspace_size", "mri_step_imex1", "mri_step_imex2_workspace_size",
-            "mri_step_imex2")
+            "mri_step_imex2", "mri_probe_mech_device")
 
 
 class MriError(RuntimeError):
@@ -242,6 +243,11 @@ def with_matrix_cache(opts: mri_fast_opts, cache) -> mri_fast_opts:
 
 def mri_mech_load(blob: bytes) -> Mech:
     return Mech(blob)
+
+
+def mri_probe_mech_device(mech: Mech, device: int) -> int:
+    """Test hook: record `device` as the mechanism's device; returns the previous one."""
+    return int(_lib.mri_probe_mech_device(mech.handle, int(device)))
 
 
 def mri_stage_fast(y, p, phi, t0, Hstage, h, mech: Mech, opts: mri_fast_opts, cell_status=None, cell_stats=None,

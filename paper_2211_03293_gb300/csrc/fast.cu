@@ -1530,10 +1530,19 @@ static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, 
 
 // Each launch takes its own counter of the mechanism's ring, so that launches in
 // flight on different streams do not share one (up to kQueueSlots of them); the
-// counter is zeroed in stream order before the launch.
+// counter is zeroed in stream order before the launch.  A launch recorded under stream
+// capture takes a counter from the second ring, which eager launches never use: the
+// graph keeps that counter for every replay, so eager launches that wrap their own
+// ring cannot collide with a replay in flight.
 static int take_queue(const Mech& m, StageArgs& a, cudaStream_t st) {
   Mech& mm = const_cast<Mech&>(m);
-  a.queue = mm.d_queue + (__atomic_fetch_add(&mm.queue_next, 1u, __ATOMIC_RELAXED) % kQueueSlots);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MRI_ECUDA;
+  if (cap == cudaStreamCaptureStatusNone)
+    a.queue = mm.d_queue + (__atomic_fetch_add(&mm.queue_next, 1u, __ATOMIC_RELAXED) % kQueueSlots);
+  else
+    a.queue = mm.d_queue + kQueueSlots +
+              (__atomic_fetch_add(&mm.graph_next, 1u, __ATOMIC_RELAXED) % kGraphQueueSlots);
   return cudaMemsetAsync(a.queue, 0, sizeof(int), st) == cudaSuccess ? MRI_OK : MRI_ECUDA;
 }
 
@@ -1666,10 +1675,17 @@ bool fast_opts_ok(const mri_fast_opts* o) {
          o->newton_safety > 0 && o->newton_safety <= 1.0;
 }
 
+int mech_device_check(const Mech& m) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MRI_ECUDA;
+  return dev == m.device ? MRI_OK : MRI_EINVAL;
+}
+
 int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* phi, int K, double Hstage,
                            double h, const Mech& m, const mri_fast_opts& o, int32_t* cell_status,
                            int32_t* cell_stats, int32_t* n_failed, cudaStream_t st, bool sticky) {
   if (!fast_opts_ok(&o) || ncell < 0 || K < 0 || K > kMaxK) return MRI_EINVAL;
+  if (const int rc = mech_device_check(m)) return rc;
   if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
   if (ncell > 0 && (!y || !p || (K > 0 && !phi))) return MRI_EINVAL;
   return launch_stage_fast(y, p, ncell, phi, K, Hstage, h, m, o, o.ramp, cell_status, cell_stats, n_failed, st,
@@ -1732,6 +1748,7 @@ extern "C" int mri_stage_fast_guided(double* y, const double* p, int ncell, cons
     if (ncell > 0 && (!guess || (double)guess_steps != nsub)) return MRI_EINVAL;
   }
   if (ncell > 0 && (!y || !p || (K > 0 && !phi))) return MRI_EINVAL;
+  if (const int rc = mri::mech_device_check(*reinterpret_cast<const Mech*>(mech))) return rc;
   return mri::launch_stage_fast(y, p, ncell, phi, K, Hstage, h, *reinterpret_cast<const Mech*>(mech), *opts,
                                 opts->ramp, cell_status, cell_stats, n_failed, static_cast<cudaStream_t>(stream),
                                 false, guess, start, n_fallback, step_exp);
@@ -1744,13 +1761,11 @@ extern "C" int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, 
   if (opts->warps_per_block != 0 || opts->blocks_per_sm > 1 || opts->time_budget_s != 0.0 || opts->matrix_cache)
     return MRI_EINVAL;
   if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return MRI_ECUDA;
   for (int g = 0; g < ngroups; ++g) {
     const mri_stage_group& G = groups[g];
     if (!G.mech || G.ncell < 0 || G.K < 0 || G.K > mri::kMaxK) return MRI_EINVAL;
     if (G.ncell > 0 && (!G.y || !G.p || (G.K > 0 && !G.phi))) return MRI_EINVAL;
-    if (reinterpret_cast<const Mech*>(G.mech)->device != dev) return MRI_EINVAL;
+    if (const int rc = mri::mech_device_check(*reinterpret_cast<const Mech*>(G.mech))) return rc;
   }
   return mri::launch_stage_fast_batch(groups, ngroups, Hstage, h, *opts, n_failed, static_cast<cudaStream_t>(stream));
 }
@@ -1775,6 +1790,7 @@ extern "C" int mri_fast_rhs(const double* y, const double* p, int ncell, const m
   if (!mech || ncell < 0 || (ncell > 0 && (!y || !p || !f))) return MRI_EINVAL;
   if (ncell == 0) return MRI_OK;
   const Mech* m = reinterpret_cast<const Mech*>(mech);
+  if (const int rc = mri::mech_device_check(*m)) return rc;
   int warps, blocks;
   size_t smem;
   if (!mri::plan_launch(m->L, ncell, warps, blocks, smem)) return MRI_EINVAL;
@@ -1789,6 +1805,7 @@ extern "C" int mri_fast_jac(const double* y, const double* p, int ncell, const m
   if (!mech || ncell < 0 || (ncell > 0 && (!y || !p || !J))) return MRI_EINVAL;
   if (ncell == 0) return MRI_OK;
   const Mech* m = reinterpret_cast<const Mech*>(mech);
+  if (const int rc = mri::mech_device_check(*m)) return rc;
   int warps, blocks;
   size_t smem;
   if (!mri::plan_launch(m->L, ncell, warps, blocks, smem)) return MRI_EINVAL;

@@ -9,9 +9,10 @@
 // a constant diagonal, so z = r / diag needs no array.  Every iteration is three
 // passes over the state: the stencil apply fused with the per-component partial sums
 // of p.Ap, the x / r update fused with the partial sums of r.z, and the direction
-// update; between them one block turns the partial sums into alpha and beta.  All
-// sums run in a fixed order (per thread, then over the block's cell slots, then
-// over the blocks), so a solve is deterministic.  A component stops updating once its
+// update.  The last block to finish each of the first two passes (a grid-wide arrival
+// counter, no waiting) turns the partial sums into alpha and beta, so an iteration is
+// three launches.  All sums run in a fixed order (per thread, then over the block's
+// cell slots, then over the blocks), so a solve is deterministic.  A component stops updating once its
 // residual meets the tolerance; a device "finished" flag turns the launches after
 // convergence into no-ops, and the host may read it every few iterations.
 #include <cmath>
@@ -36,6 +37,7 @@ struct Lap7 {
 struct CgState {
   int finished;
   int iterations;
+  unsigned arrive;   // blocks of the current pass that have written their partial sums
 };
 
 struct CgScal {          // per component
@@ -81,14 +83,42 @@ __device__ __forceinline__ void block_partial(double v, int n, int rt, double* _
   }
 }
 
+// sum over the blocks' partials of component q by one warp, in a fixed order (the
+// partials of other blocks are read through L2)
+__device__ __forceinline__ double sum_parts(const double* part, int nblk, int q, int lane) {
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += __ldcg(part + (size_t)q * nblk + b);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+// After a block has written its partial sums: true in the one block that arrives
+// last (it then sees every block's partials).  The counter is reset by that block, so
+// the next pass starts from zero.  Nothing waits.
+__device__ __forceinline__ bool last_block(CgState* cs) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(&cs->arrive, 1u);
+    s_last = (t == gridDim.x - 1) ? 1 : 0;
+    if (s_last) cs->arrive = 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
 // mode 0: r = b - A x, partial sums of <r, r> and <b, b> (start)
-// mode 1: Ap = A p, partial sums of <p, Ap>
+// mode 1: Ap = A p, partial sums of <p, Ap>; the last block sets alpha = <r, z> / <p, A p>
 template <int MODE>
 __global__ void __launch_bounds__(kPassMax) apply_pass_kernel(const double* __restrict__ x,
                                                                  const double* __restrict__ bvec,
                                                                  double* __restrict__ out, Lap7 s, int rt,
                                                                  double* __restrict__ part1,
-                                                                 double* __restrict__ part2, const CgState* cs) {
+                                                                 double* __restrict__ part2, CgScal* sc,
+                                                                 CgState* cs) {
   if (MODE == 1 && cs->finished) return;   // uniform over the grid
   const int q = threadIdx.x % rt, slot = threadIdx.x / rt, S = blockDim.x / rt;
   const long long ncell = (long long)s.nx * s.ny * s.nz;
@@ -112,15 +142,25 @@ __global__ void __launch_bounds__(kPassMax) apply_pass_kernel(const double* __re
   if (MODE == 0) {
     __syncthreads();
     block_partial(a2, s.n, rt, part2);
+    return;
+  }
+  if (!last_block(cs)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int qq = warp; qq < s.n; qq += nw) {
+    const double pq = sum_parts(part1, gridDim.x, qq, lane);
+    if (lane == 0) sc[qq].alpha = (sc[qq].done || !(pq > 0.0)) ? 0.0 : sc[qq].rz / pq;
   }
 }
 
-// x += alpha p, r -= alpha Ap, partial sums of <r, r> (components still iterating)
+// x += alpha p, r -= alpha Ap, partial sums of <r, r> (components still iterating); the
+// last block sets beta = <r, z>_new / <r, z>_old, tests convergence and counts the
+// iteration
 __global__ void __launch_bounds__(kPassMax) update_pass_kernel(double* __restrict__ x, double* __restrict__ r,
                                                                   const double* __restrict__ p,
                                                                   const double* __restrict__ Ap, long long ncell,
-                                                                  int n, int rt, const CgScal* sc,
-                                                                  double* __restrict__ part, const CgState* cs) {
+                                                                  int n, int rt, CgScal* sc,
+                                                                  double* __restrict__ part, double inv_diag,
+                                                                  double tol, CgState* cs) {
   if (cs->finished) return;
   const int q = threadIdx.x % rt, slot = threadIdx.x / rt, S = blockDim.x / rt;
   double acc = 0.0;
@@ -135,6 +175,29 @@ __global__ void __launch_bounds__(kPassMax) update_pass_kernel(double* __restric
     }
   }
   block_partial(acc, n, rt, part);
+  if (!last_block(cs)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int active = 0;
+  for (int qq = warp; qq < n; qq += nw) {
+    const double rr = sum_parts(part, gridDim.x, qq, lane);
+    CgScal t = sc[qq];
+    if (!t.done) {
+      const double rz = rr * inv_diag;
+      t.beta = (t.rz > 0.0) ? rz / t.rz : 0.0;
+      t.rz = rz;
+      if (rr <= tol * tol * t.bb) t.done = 1;
+    } else {
+      t.beta = 0.0;
+    }
+    __syncwarp();
+    if (lane == 0) sc[qq] = t;
+    active |= !t.done;
+  }
+  const int any = __syncthreads_or(active);
+  if (threadIdx.x == 0) {
+    cs->iterations += 1;
+    if (!any) cs->finished = 1;
+  }
 }
 
 // START: p = r / diag for every component; else p = r / diag + beta p for the
@@ -152,15 +215,6 @@ __global__ void dir_kernel(double* __restrict__ p, const double* __restrict__ r,
       if (!sc[q].done) p[e] = fma(sc[q].beta, p[e], r[e] * inv_diag);
     }
   }
-}
-
-// sum over the blocks' partials of component q by one warp, in a fixed order
-__device__ __forceinline__ double sum_parts(const double* part, int nblk, int q, int lane) {
-  double s = 0.0;
-  for (int b = lane; b < nblk; b += 32) s += part[(size_t)q * nblk + b];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
 }
 
 // Start: <r, z> = <r, r> / diag and <b, b>; a component with b = 0 is measured
@@ -190,46 +244,7 @@ __global__ void __launch_bounds__(kScalThreads) cg_init_kernel(const double* par
   if (threadIdx.x == 0) {
     cs->finished = any ? 0 : 1;
     cs->iterations = 0;
-  }
-}
-
-// alpha = <r, z> / <p, A p>
-__global__ void __launch_bounds__(kScalThreads) cg_alpha_kernel(const double* part_pq, int nblk, int n, CgScal* sc,
-                                                                const CgState* cs) {
-  if (cs->finished) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = warp; q < n; q += nw) {
-    const double pq = sum_parts(part_pq, nblk, q, lane);
-    if (lane == 0) sc[q].alpha = (sc[q].done || !(pq > 0.0)) ? 0.0 : sc[q].rz / pq;
-  }
-}
-
-// beta = <r, z>_new / <r, z>_old and the convergence test
-__global__ void __launch_bounds__(kScalThreads) cg_beta_kernel(const double* part_rr, int nblk, int n,
-                                                               double inv_diag, double tol, CgScal* sc,
-                                                               CgState* cs) {
-  if (cs->finished) return;     // uniform over the block: read before anyone writes
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int active = 0;
-  for (int q = warp; q < n; q += nw) {
-    const double rr = sum_parts(part_rr, nblk, q, lane);
-    CgScal s = sc[q];
-    if (!s.done) {
-      const double rz = rr * inv_diag;
-      s.beta = (s.rz > 0.0) ? rz / s.rz : 0.0;
-      s.rz = rz;
-      if (rr <= tol * tol * s.bb) s.done = 1;
-    } else {
-      s.beta = 0.0;
-    }
-    __syncwarp();
-    if (lane == 0) sc[q] = s;
-    active |= !s.done;
-  }
-  const int any = __syncthreads_or(active);
-  if (threadIdx.x == 0) {
-    cs->iterations += 1;
-    if (!any) cs->finished = 1;
+    cs->arrive = 0u;
   }
 }
 
@@ -237,6 +252,12 @@ __global__ void __launch_bounds__(kScalThreads) cg_beta_kernel(const double* par
 __global__ void cg_info_kernel(const CgState* cs, int32_t* info) {
   info[0] = cs->finished;
   info[1] = cs->iterations;
+}
+
+// cg_info of two solves in a row: converged when both are, iterations summed
+__global__ void cg_info_pair_kernel(const int32_t* first, int32_t* info) {
+  info[0] = (first[0] != 0 && info[0] != 0) ? 1 : 0;
+  info[1] += first[1];
 }
 
 // out = u + s v
@@ -298,7 +319,7 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
   const long long want = (ncell + S - 1) / S;
   const int nblk = (int)(want < kRedBlocks ? want : kRedBlocks);
   if (iters) *iters = 0;
-  apply_pass_kernel<0><<<nblk, pt, 0, st>>>(x, b, r, op, rt, part1, part2, nullptr);
+  apply_pass_kernel<0><<<nblk, pt, 0, st>>>(x, b, r, op, rt, part1, part2, nullptr, nullptr);
   cg_init_kernel<<<1, kScalThreads, 0, st>>>(part1, part2, nblk, n, inv_diag, tol, sc, cs);
   dir_kernel<true><<<eb, 256, 0, st>>>(p, r, len, n, inv_diag, sc, cs);
   if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
@@ -310,10 +331,8 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
         return MRI_ECUDA;
       if (h.finished) break;
     }
-    apply_pass_kernel<1><<<nblk, pt, 0, st>>>(p, nullptr, Ap, op, rt, part1, nullptr, cs);
-    cg_alpha_kernel<<<1, kScalThreads, 0, st>>>(part1, nblk, n, sc, cs);
-    update_pass_kernel<<<nblk, pt, 0, st>>>(x, r, p, Ap, ncell, n, rt, sc, part1, cs);
-    cg_beta_kernel<<<1, kScalThreads, 0, st>>>(part1, nblk, n, inv_diag, tol, sc, cs);
+    apply_pass_kernel<1><<<nblk, pt, 0, st>>>(p, nullptr, Ap, op, rt, part1, nullptr, sc, cs);
+    update_pass_kernel<<<nblk, pt, 0, st>>>(x, r, p, Ap, ncell, n, rt, sc, part1, inv_diag, tol, cs);
     dir_kernel<false><<<eb, 256, 0, st>>>(p, r, len, n, inv_diag, sc, cs);
     if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
   }
@@ -369,6 +388,7 @@ extern "C" int mri_step_imex1(double* y, const double* p, const mri_grid* grid, 
     return MRI_EINVAL;
   if (!mri::fast_opts_ok(opts) || opts->time_budget_s != 0.0) return MRI_EINVAL;
   const mri::Mech* m = reinterpret_cast<const mri::Mech*>(mech);
+  if (const int rc = mri::mech_device_check(*m)) return rc;
   const int n = m->L.n;
   if (n > 1024) return MRI_EINVAL;
   if (!workspace || workspace_bytes < mri_step_imex1_workspace_size(grid, n)) return MRI_ENOMEM;
@@ -404,7 +424,8 @@ extern "C" int mri_step_imex1(double* y, const double* p, const mri_grid* grid, 
 extern "C" size_t mri_step_imex2_workspace_size(const mri_grid* grid, int n) {
   if (!mri::grid_ok2(grid) || n < 1) return 0;
   const size_t len = (size_t)grid->nx * grid->ny * grid->nz * n;
-  return 2 * len * sizeof(double) + mri_diffusion_workspace_size(grid, n) + mri_step_workspace_size(grid, n);
+  // plus the first half step's cg_info (two int32, padded to 16 bytes)
+  return 2 * len * sizeof(double) + mri_diffusion_workspace_size(grid, n) + mri_step_workspace_size(grid, n) + 16;
 }
 
 namespace mri {
@@ -436,6 +457,7 @@ extern "C" int mri_step_imex2(double* y, const double* p, const mri_grid* grid, 
     return MRI_EINVAL;
   if (!mri::fast_opts_ok(opts) || opts->time_budget_s != 0.0) return MRI_EINVAL;
   const mri::Mech* m = reinterpret_cast<const mri::Mech*>(mech);
+  if (const int rc = mri::mech_device_check(*m)) return rc;
   const int n = m->L.n;
   if (n > 1024) return MRI_EINVAL;
   if (!workspace || workspace_bytes < mri_step_imex2_workspace_size(grid, n)) return MRI_ENOMEM;
@@ -445,6 +467,7 @@ extern "C" int mri_step_imex2(double* y, const double* p, const mri_grid* grid, 
   double* rhs = fI + len;
   void* cgws = rhs + len;
   void* stepws = static_cast<unsigned char*>(cgws) + mri_diffusion_workspace_size(grid, n);
+  int32_t* info1 = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(stepws) + mri_step_workspace_size(grid, n));
   // explicit slow partition of the MRI step: advection (the grid's order); the
   // diffusion is the 7-point Laplacian of the Crank-Nicolson half steps
   mri_grid gE = *grid, gI = *grid;
@@ -453,12 +476,22 @@ extern "C" int mri_step_imex2(double* y, const double* p, const mri_grid* grid, 
   gI.order = 2;
   const double a = 0.25 * H;
   int it1 = 0, it2 = 0;
-  int rc = mri::cn_diffusion(y, n, &gI, a, cg_tol, cg_max_iter, cg_check_every, fI, rhs, cgws, &it1, nullptr, st);
+  // a first half step that misses its tolerance: MRI_ECONV with host checks, and in
+  // cg_info (combined with the second half step's) either way
+  int rc = mri::cn_diffusion(y, n, &gI, a, cg_tol, cg_max_iter, cg_check_every, fI, rhs, cgws, &it1,
+                             cg_info ? info1 : nullptr, st);
+  if (rc == MRI_ECONV && cg_info &&
+      cudaMemcpyAsync(cg_info, info1, 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return MRI_ECUDA;
   if (rc != MRI_OK) return rc;
   rc = mri_step(y, p, &gE, t, H, h, mri_method, mech, opts, stepws, mri_step_workspace_size(grid, n), cell_status,
                 cell_stats, n_failed, stream);
   if (rc != MRI_OK) return rc;
   rc = mri::cn_diffusion(y, n, &gI, a, cg_tol, cg_max_iter, cg_check_every, fI, rhs, cgws, &it2, cg_info, st);
   if (cg_iterations) *cg_iterations = (cg_check_every > 0) ? it1 + it2 : -1;
+  if (cg_info && (rc == MRI_OK || rc == MRI_ECONV)) {
+    mri::cg_info_pair_kernel<<<1, 1, 0, st>>>(info1, cg_info);
+    if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
+  }
   return rc;
 }

@@ -86,13 +86,19 @@ __host__ __device__ inline size_t mc_stride(const Layout& L, bool prec32) {
   return (b + 127) / 128 * 128;
 }
 
-constexpr int kQueueSlots = 256;   // work-queue counters per mechanism (one per launch in flight)
+// Work-queue counters per mechanism: one per stage launch in flight.  Eager launches
+// take theirs from one ring and launches recorded under stream capture from a second
+// one, so a CUDA graph, which keeps its counter for as long as it lives, never shares
+// a counter with an eager launch.
+constexpr int kQueueSlots = 256;        // eager launches
+constexpr int kGraphQueueSlots = 256;   // launches recorded into graphs
 
 struct Mech {             // what mri_mech points at
   Layout L;
   void* d_table = nullptr;   // device copy of the table
-  int* d_queue = nullptr;    // kQueueSlots work-queue counters
-  unsigned queue_next = 0;   // next counter to hand out (round robin)
+  int* d_queue = nullptr;    // kQueueSlots + kGraphQueueSlots work-queue counters
+  unsigned queue_next = 0;   // next eager counter to hand out (round robin)
+  unsigned graph_next = 0;   // next captured-launch counter to hand out (round robin)
   int device = -1;
 };
 
@@ -201,6 +207,9 @@ int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, 
                       int start = MRI_START_PREDICTOR, int32_t* n_fallback = nullptr,
                       const int8_t* step_exp = nullptr);
 bool fast_opts_ok(const mri_fast_opts* o);
+// MRI_OK when the current device is the one the mechanism's tables were loaded on,
+// MRI_EINVAL when it is another, MRI_ECUDA when the device cannot be queried
+int mech_device_check(const Mech& m);
 // mri_stage_fast after the pointer checks; sticky = write only failing statuses
 int mri_stage_fast_checked(double* y, const double* p, int ncell, const double* phi, int K, double Hstage,
                            double h, const Mech& m, const mri_fast_opts& o, int32_t* cell_status,

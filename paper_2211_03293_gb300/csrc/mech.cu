@@ -8,6 +8,7 @@
 
 #include "fastmath.cuh"
 #include "internal.cuh"
+#include "../../include/mri_probe.h"
 
 namespace mri {
 namespace {
@@ -437,7 +438,7 @@ extern "C" int mri_mech_load(const void* blob, size_t nbytes, mri_mech** out) {
     delete m;
     return MRI_ECUDA;
   }
-  if (cudaMalloc(&m->d_queue, sizeof(int) * mri::kQueueSlots) != cudaSuccess) {
+  if (cudaMalloc(&m->d_queue, sizeof(int) * (mri::kQueueSlots + mri::kGraphQueueSlots)) != cudaSuccess) {
     cudaFree(m->d_table);
     delete m;
     return MRI_ECUDA;
@@ -466,4 +467,12 @@ extern "C" int mri_mech_info(const mri_mech* mech, int* n_species, int* n_reacti
   if (n_species) *n_species = m->L.Ns;
   if (n_reactions) *n_reactions = m->L.R;
   return MRI_OK;
+}
+
+extern "C" int mri_probe_mech_device(mri_mech* mech, int device) {
+  if (!mech) return -1;
+  mri::Mech* m = reinterpret_cast<mri::Mech*>(mech);
+  const int old = m->device;
+  m->device = device;
+  return old;
 }

@@ -166,14 +166,28 @@ extern "C" size_t mri_step_workspace_size(const mri_grid* grid, int n) {
 
 using mri::mri_stage_fast_checked;
 
+namespace mri {
+namespace {
+
+// The host-side checks of an MRI step's arguments, workspace aside: MRI_OK, MRI_EINVAL
+// (bad argument, or a mechanism loaded on another device) or MRI_ECUDA.
+int step_args_check(const double* y, const double* p, const mri_grid* grid, double H, double h, int mri_method,
+                    const mri_mech* mech, const mri_fast_opts* opts) {
+  if (!grid_ok(grid) || !mech || !opts || !y || !p || mri_method != MRI_KW3) return MRI_EINVAL;
+  if (!(H > 0) || !(h > 0) || !std::isfinite(H) || !std::isfinite(h)) return MRI_EINVAL;
+  if (!fast_opts_ok(opts) || opts->time_budget_s != 0.0) return MRI_EINVAL;
+  return mech_device_check(*reinterpret_cast<const Mech*>(mech));
+}
+
+}  // namespace
+}  // namespace mri
+
 extern "C" int mri_step(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
                         int mri_method, const mri_mech* mech, const mri_fast_opts* opts, void* workspace,
                         size_t workspace_bytes, int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed,
                         void* stream) {
   (void)t;
-  if (!mri::grid_ok(grid) || !mech || !opts || !y || !p || mri_method != MRI_KW3) return MRI_EINVAL;
-  if (!(H > 0) || !(h > 0) || !std::isfinite(H) || !std::isfinite(h)) return MRI_EINVAL;
-  if (!mri::fast_opts_ok(opts) || opts->time_budget_s != 0.0) return MRI_EINVAL;
+  if (const int rc = mri::step_args_check(y, p, grid, H, h, mri_method, mech, opts)) return rc;
   const mri::Mech* m = reinterpret_cast<const mri::Mech*>(mech);
   const int n = m->L.n;
   const size_t need = mri_step_workspace_size(grid, n);
@@ -251,7 +265,9 @@ int static_scratch(void** out) {
 extern "C" int mri_step_noalloc(double* y, const double* p, const mri_grid* grid, double t, double H, double h,
                                 int mri_method, const mri_mech* mech, const mri_fast_opts* opts,
                                 int32_t* cell_status, int32_t* cell_stats, int32_t* n_failed, void* stream) {
-  if (!mri::grid_ok(grid) || !mech || !opts) return MRI_EINVAL;
+  // every argument check of mri_step first, so that an invalid call returns without
+  // touching the CUDA runtime (the scratch lookup below runs only for valid calls)
+  if (const int rc = mri::step_args_check(y, p, grid, H, h, mri_method, mech, opts)) return rc;
   const mri::Mech* m = reinterpret_cast<const mri::Mech*>(mech);
   const size_t need = mri_step_workspace_size(grid, m->L.n);
   if (need == 0) return MRI_EINVAL;

@@ -187,3 +187,46 @@ def test_imex2_step_in_a_cuda_graph_equals_the_direct_call(mri):
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(y, direct)
+
+
+def test_imex2_cg_info_covers_both_half_steps(mri):
+    """cg_info of the second-order step reports both Crank-Nicolson half steps: with no
+    host checks and an iteration cap below what the first half step needs, it shows no
+    convergence and the iterations of both; uncapped, it shows convergence and the
+    same total as the host-checked step."""
+    import torch
+    w = mechgen.workload("box32", cells_per_side=8)
+    g = dict(w.grid, D=w.grid["D"] * 200)
+    grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
+    gI = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], (0.0, 0.0, 0.0), g["D"], 2)
+    n = w.mech.n
+    gm = mri.mri_mech_load(w.mech.to_blob())
+    p = torch.tensor(w.p, device="cuda")
+    o = mri.mri_fast_opts_default(method=w.method, jac_policy=1, ramp=w.ramp)
+    y0 = torch.tensor(w.y0, device="cuda")
+    H = w.H / 2
+    ws = torch.empty(mri.mri_step_imex2_workspace_size(grid, n), dtype=torch.uint8, device="cuda")
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    y = y0.clone()
+    total = mri.mri_step_imex2(y, p, grid, 0.0, H, w.h, gm, o, ws, cg_tol=1e-13, cg_check_every=1)
+    # the first half step alone through the public calls: (I - aL) x = (I + aL) y0, x from y0
+    a = H / 4
+    fI = torch.empty_like(y0)
+    mri.mri_slow_rhs(y0, fI, gI)
+    rhs = y0 + a * fI
+    x = y0.clone()
+    cws = torch.empty(mri.mri_diffusion_workspace_size(gI, n), dtype=torch.uint8, device="cuda")
+    it1 = mri.mri_diffusion_solve(x, rhs, gI, a, cws, tol=1e-13, max_iter=1000, check_every=1)
+    assert 2 <= it1 < total
+    y = y0.clone()
+    assert mri.mri_step_imex2(y, p, grid, 0.0, H, w.h, gm, o, ws, cg_tol=1e-13, cg_max_iter=1000,
+                              cg_check_every=0, cg_info=info) == -1
+    assert info.tolist() == [1, total]
+    cap = it1 - 1
+    y = y0.clone()
+    info.fill_(7)
+    mri.mri_step_imex2(y, p, grid, 0.0, H, w.h, gm, o, ws, cg_tol=1e-13, cg_max_iter=cap, cg_check_every=0,
+                       cg_info=info)
+    conv, its = info.tolist()
+    assert conv == 0
+    assert cap < its <= 2 * cap

@@ -1,27 +1,39 @@
 """Benchmark of the MRI fast-partition solve on GB300.
 
-Workload (synthetic, seeded): the 32^3 periodic box -- 40 species / 170
-reactions (12 third-body, 8 Troe falloff), temperature from 8 Gaussian hot
-spots (300..2500 K), Dirichlet mass fractions, 4th-order central
-advection-diffusion as the slow partition, explicit MRI3 (Knoth-Wolke, MIS form)
-with SDIRK3 fast substeps, H = 5e-8 s, h = H/10, Newton tolerance 1e-10.
-One bench step = one MRI slow step over the whole box (three f^S evaluations,
-three stage forcings, three fast stages) through the C ABI.
+Headline workload (synthetic, seeded): the 32^3 periodic box -- 40 species / 170
+reactions (12 third-body, 8 Troe falloff), temperature from 8 Gaussian hot spots
+(300..2500 K), Dirichlet mass fractions, 4th-order central advection-diffusion as
+the slow partition, explicit MRI3 (Knoth-Wolke, MIS form) with SDIRK3 fast
+substeps, H = 5e-8 s, h = H/10, Newton tolerance 1e-10.  One bench step = one MRI
+slow step over the whole box (three f^S evaluations, three stage forcings, three
+fast stages) through the C ABI.
 
-Metric: fast-chemistry cell-steps per second, a cell-step being one SDIRK
-substep of one cell (all its stages and Newton iterations), counted from the
-kernels' own per-cell counters.  Three forms are timed: the plain FP64 path,
-the mixed-precision path (FP32 Newton matrix / LU, FP64 rates and residual) and
-the learned start on the mixed path (a bf16 network trained on the first steps
-predicts Newton starts; its inference is inside the timed steps).  Each form
-uses the persistent kernel's autotuned launch shape and keeps Newton matrices
-across calls, and is gated against the CPU oracle (sampled cells of a full-size
-stage, relative error <= 1e-6, per-field maxima and RMS reported); the headline
-is the fastest form that passes.
+Metric: fast-chemistry cell-steps per second, a cell-step being one SDIRK substep
+of one cell (all its stages and Newton iterations), counted from the kernels' own
+per-cell counters.  Every timed fast stage is gated against the CPU oracle: before
+each stage the inputs (state and forcing) of sampled cells are copied aside outside
+the timed intervals, and afterwards the oracle integrates the same stages; the
+largest relative error (mass fractions above 1e-10, and T) must stay <= 1e-6.
+
+Forms and workloads (each on its own configuration):
+* box32 (32^3): plain FP64, mixed precision (FP32 Newton matrix and LU, FP64
+  rates, residual and update) and the learned start on the mixed form; the
+  headline is the fastest form that passes its gate;
+* box64 (64^3): the precision form (and the plain form beside it), with the error
+  against the FP64 oracle per field;
+* front128 (128^3 planar flame front): the batched form -- a second-order IMEX
+  multirate step (Crank-Nicolson half steps of the diffusion by Jacobi-PCG around
+  the MRI3 step with explicit advection), mixed precision, autotuned launch shape,
+  solve layout and schedule, device work queue -- timed call by call, replayed
+  from a CUDA graph and end to end through mri_step_imex2; beside it the same step
+  with the static cell-to-warp mapping and with the plain FP64 form;
+* the mixed 9/40/80-species reactor batch in one launch, with per-group times;
+* the Jacobi-PCG diffusion solve alone against the HBM roofline.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch one process per GPU with torch.distributed.run; every rank
-integrates its own replica of the box (weak scaling, no data-path collective).
+integrates its own replica of each workload (weak scaling, no data-path
+collective).
 """
 from __future__ import annotations
 
@@ -40,8 +52,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fast-chem cell-steps/s per MRI slow step, plain FP64 vs tuned, at rel err ≤1e-6"
 UNIT = "cell-steps/s"
-WORKLOAD = "box32"
 GATE_TOL = 1e-6
+GATE_CELLS = 32
 # FP64 roofline: the FMA pipe issues 2 DFMA per clock per SM on GB300 (measured), 152 SMs,
 # 2 flops per FMA; at the maximum SM clock of 2070 MHz this is the figure below.  The bench
 # measures the rate live (mri_probe_fp64_fma) and uses that measurement as the peak.
@@ -55,11 +67,15 @@ FLOPS_PER_TRANSCENDENTAL = 20.0
 # Newton-matrix cache in use, from the ncu captures summarised in
 # profiles/stage_fast_fp64_box16.md and profiles/stage_fast_mixed_box16.md (4096-cell
 # launches; traffic grows with the cells processed, so a launch over `cells` moves
-# cells times this).  Keep in step with the kernel: a changed kernel needs a new
-# capture before these figures are reported again.
-STAGE_DRAM_BYTES_PER_CELL = {0: (61920512 + 2869504) / 4096, 1: (33669888 + 3328) / 4096}
-FORMS = {0: "plain FP64", 1: "mixed: FP32 Newton matrix and LU, FP64 rates, residual and update",
-         2: "learned: mixed form with Newton started from a bf16 MLP's prediction where the predictor has none"}
+# cells times this).  None: the kernel changed since the capture.
+STAGE_DRAM_BYTES_PER_CELL = {0: None, 1: None}
+FORM_NAMES = {"plain": "plain FP64", "mixed": "mixed: FP32 Newton matrix and LU, FP64 rates, residual and update",
+              "learned": "learned: mixed form with Newton started from a bf16 MLP's prediction where the "
+                         "predictor has none",
+              "batched": "batched: mixed form, autotuned shape/solve layout/schedule, device work queue, "
+                         "IMEX step graph-captured",
+              "static": "batched with the static cell-to-warp mapping instead of the work queue",
+              "plain_imex": "plain FP64 in the same IMEX step"}
 
 
 # ----------------------------------------------------------------------------- flop model
@@ -178,26 +194,82 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- GPU arm
 
-class Bench:
-    def __init__(self, args, world):
+class Gate:
+    """Inputs and outputs of sampled cells of every timed fast stage, checked against
+    the oracle afterwards.  Snapshots are small device gathers taken between the
+    timed intervals."""
+
+    def __init__(self, case, ncells=GATE_CELLS, seed=11):
+        import torch
+        rng = np.random.default_rng(seed)
+        self.case = case
+        self.idx_np = np.sort(rng.choice(case.ncell, min(ncells, case.ncell), replace=False))
+        self.idx = torch.tensor(self.idx_np, device=case.dev)
+        self.pending = None
+        self.records = []
+
+    def before(self, y, phi, Hs, ramp):
+        self.pending = (y.index_select(0, self.idx), phi.index_select(0, self.idx), Hs, ramp)
+
+    def after(self, y):
+        yi, ph, Hs, ramp = self.pending
+        self.records.append((yi, ph, Hs, ramp, y.index_select(0, self.idx)))
+        self.pending = None
+
+    def check(self):
+        """Per-field maximum and RMS relative error of every recorded stage against the
+        oracle's stage from the same inputs."""
+        import oracle
+        c = self.case
+        w = c.w
+        m = oracle.Mech(w.mech)
+        p = w.p[self.idx_np]
+        ry, rt, worst = [], [], 0.0
+        nrec = len(self.records)
+        for yi, ph, Hs, ramp, yo in self.records:
+            ref, st, _ = m.stage_fast(yi.cpu().numpy(), p, ph.cpu().numpy(), Hs, w.h,
+                                      oracle.opts(method=w.method, rtol=w.newton_rtol, ramp=ramp))
+            got = yo.cpu().numpy()
+            scale = np.abs(ref)
+            scale[:, :-1] = np.maximum(scale[:, :-1], 1e-10)
+            rel = np.abs(got - ref) / scale
+            worst = max(worst, float(rel.max()))
+            big = ref[:, :-1] > 1e-10
+            ry.append(rel[:, :-1][big])
+            rt.append(rel[:, -1])
+        self.records = []
+        if not ry:
+            return None
+        ry, rt = np.concatenate(ry), np.concatenate(rt)
+        return {"stages": nrec, "cells": int(len(self.idx_np)),
+                "max_rel_err": worst, "tolerance": GATE_TOL, "passed": worst <= GATE_TOL,
+                "Y_max": float(ry.max()), "Y_rms": float(np.sqrt(np.mean(ry ** 2))), "T_max": float(rt.max()),
+                "T_rms": float(np.sqrt(np.mean(rt ** 2)))}
+
+
+class Case:
+    """One workload on the GPU: mechanism, grid, state buffers and the MRI steps
+    through the C ABI."""
+
+    def __init__(self, name, args, cells_per_side=None):
         import torch
 
         import mechgen
         import paper_2211_03293_gb300 as mri
 
-        self.mri, self.torch, self.args, self.world = mri, torch, args, world
+        self.mri, self.torch, self.args = mri, torch, args
+        self.name = name
         self.dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-        torch.cuda.set_device(self.dev)
-        self.w = w = mechgen.workload(WORKLOAD, seed=0, cells_per_side=args.cells_per_side)
+        self.w = w = mechgen.workload(name, seed=0, cells_per_side=cells_per_side)
         g = w.grid
         self.ncell = w.y0.shape[0]
         self.n = w.mech.n
         self.mech = mri.mri_mech_load(w.mech.to_blob())
         self.grid = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], g["D"], g["order"])
+        self.gridE = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], g["u"], 0.0, g["order"])
+        self.gridI = mri.grid(g["nx"], g["ny"], g["nz"], g["dx"], (0.0, 0.0, 0.0), g["D"], 2)
         self.c, self.G = mri.mri_method_coupling(mri.MRI_KW3)
         self.stream = torch.cuda.Stream(device=self.dev)
-        self.shape = {}
-        self.cache = {}
         dev = self.dev
         self.p = torch.tensor(w.p, device=dev)
         self.fS = torch.empty((3, self.ncell, self.n), dtype=torch.float64, device=dev)
@@ -206,289 +278,625 @@ class Bench:
         self.status = torch.zeros(self.ncell, dtype=torch.int32, device=dev)
         self.nfail = torch.zeros(1, dtype=torch.int32, device=dev)
         self.nfallback = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)    # 256 MB > 129 MB L2
-        probe = torch.empty(N_SM * 8 * 256 * 4, dtype=torch.float64, device=dev)
-        self.fp64_peak_tflops = 2.0 * mri.mri_probe_fp64_fma(probe, iters=4096) / 1e12
-        try:
-            self.gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-        except Exception:
-            self.gpu_id = str(dev.index)
+        self.tuned = {}          # form -> opts chosen by the autotuner
+        self.cache = {}          # precision -> Newton-matrix cache
+        self.gate = Gate(self)
+        self.flush = Case.flush_buffer(dev)
 
-    def newton_safety(self, prec):
-        """The plain FP64 form keeps the library's default acceptance of modified-Newton
-        iterates; the tuned forms (mixed and learned) use the bench's setting."""
-        return 3e-4 if prec == 0 else self.args.tuned_newton_safety
+    _flush = None
 
-    def opts(self, prec, ramp=0):
-        w = self.w
-        wpb, bps = self.shape.get(prec, (0, 0))
-        o = self.mri.mri_fast_opts_default(method=w.method, newton_rtol=w.newton_rtol, ramp=ramp,
-                                           jac_policy=self.args.jac, precision=prec, warps_per_block=wpb,
-                                           blocks_per_sm=bps, newton_safety=self.newton_safety(prec))
+    @staticmethod
+    def flush_buffer(dev):
+        import torch
+        if Case._flush is None:
+            Case._flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+        return Case._flush
+
+    def prec(self, form):
+        return 0 if form in ("plain", "plain_imex") else 1
+
+    def opts(self, form, ramp=0):
+        mri = self.mri
+        prec = self.prec(form)
+        if form in self.tuned:
+            o = mri.mri_fast_opts.from_buffer_copy(self.tuned[form])
+            o.ramp = ramp
+        else:
+            o = mri.mri_fast_opts_default(method=self.w.method, newton_rtol=self.w.newton_rtol, ramp=ramp,
+                                          jac_policy=mri.MRI_JAC_LAZY, precision=prec,
+                                          newton_safety=3e-4 if prec == 0 else self.args.tuned_newton_safety)
+        if form == "static":
+            o.schedule = mri.MRI_SCHED_STATIC
         cache = self.cache.get(prec)
-        return o if cache is None else self.mri.with_matrix_cache(o, cache)
+        return o if cache is None else mri.with_matrix_cache(o, cache)
 
-    def autotune(self, y, prec):
-        """Pick the launch shape of the fast stage by timing the candidates on the
-        first stage of the next step (copies of the state and of its forcing)."""
+    def new_cache(self, prec):
+        torch = self.torch
+        self.cache[prec] = torch.zeros(self.mri.mri_matrix_cache_size(self.mech, self.ncell, prec),
+                                       dtype=torch.uint8, device=self.dev)
+
+    def autotune(self, y, form, subsample=1):
+        """Pick the launch shape, solve layout and schedule of the fast stage by timing
+        the candidates on the first stage of the next step (copies of the state and of
+        its forcing; every subsample-th cell for the large workloads)."""
         from paper_2211_03293_gb300.autotune import autotune_stage
-        mri, c, G, w = self.mri, self.c, self.G, self.w
-        with self.torch.cuda.stream(self.stream):
+        mri, c, G, w, torch = self.mri, self.c, self.G, self.w, self.torch
+        with torch.cuda.stream(self.stream):
             mri.mri_slow_rhs(y, self.fS[0], self.grid, stream=self.stream)
             mri.mri_stage_forcing(self.fS, 1, G[1], self.phi, stream=self.stream)
-            best, table = autotune_stage(self.mech, y, self.p, self.phi, (c[1] - c[0]) * w.H, w.h, self.opts(prec),
-                                         repeats=2, stream=self.stream)
-        self.shape[prec] = (best.warps_per_block, best.blocks_per_sm)
+            ys = y[::subsample].contiguous()
+            ps = self.p[::subsample].contiguous()
+            phs = self.phi[::subsample].contiguous()
+            o = self.opts(form)
+            o.matrix_cache, o.matrix_cache_bytes = None, 0     # trial runs touch no cache
+            best, table = autotune_stage(self.mech, ys, ps, phs, (c[1] - c[0]) * w.H, w.h, o, repeats=2,
+                                         stream=self.stream)
+        self.tuned[form] = best
         wpb, blocks, smem = mri.mri_stage_fast_shape(self.mech, best, self.ncell, 1)
         return {"warps_per_block": wpb, "blocks": blocks, "blocks_per_sm": max(best.blocks_per_sm, 1),
-                "smem_bytes": smem, "autotuned": [[a, b_, round(ms, 3)] for a, b_, ms in table]}
+                "lu_variant": best.lu_variant, "schedule": best.schedule, "smem_bytes": smem,
+                "cells_timed": int(ys.shape[0]),
+                "autotuned": [[a, b_, v, s, round(ms, 3)] for a, b_, v, s, ms in table]}
 
-    def graph_steps(self, y, prec):
-        """The same MRI step recorded once in a CUDA graph and replayed args.steps times
-        (L2 flushed between replays); returns (ms per step, substeps run)."""
-        torch, args = self.torch, self.args
-        graph = torch.cuda.CUDAGraph()
-        self.stream.synchronize()
-        with torch.cuda.graph(graph, stream=self.stream):
-            self.step(y, prec, False, None)
-        self.stats.zero_()
-        torch.cuda.synchronize()
-        evs = []
-        with torch.cuda.stream(self.stream):
-            for _ in range(args.steps):
-                self.flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(self.stream)
-                graph.replay()
-                e1.record(self.stream)
-                evs.append((e0, e1))
-        torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        sub = int(self.stats[:, 0].sum().item())
-        del graph
-        return ms, sub
+    # -------------------------------------------------------------- MRI3 step, stage by stage
 
-    def step(self, y, prec, first, ev_stage, model=None):
-        """One MRI slow step through the ABI; CUDA events around each fast stage.
-        With a learned model every stage first evaluates the network (features,
-        forward pass, guess) and starts Newton from its guess where the analytic
-        predictor has no derivative yet."""
-        mri, c, G, w = self.mri, self.c, self.G, self.w
+    def mri3_step(self, y, form, first=False, ev=None, gate=None, model=None):
+        """One MRI3 slow step through the ABI.  ev: list that receives (start, end) CUDA
+        events around each of the step's timed intervals; the gate's snapshots run
+        between them."""
+        mri, c, G, w, torch, st = self.mri, self.c, self.G, self.w, self.torch, self.stream
         for i in range(1, 4):
-            mri.mri_slow_rhs(y, self.fS[i - 1], self.grid, stream=self.stream)
-            mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=self.stream)
-            o = self.opts(prec, w.ramp if (first and i == 1) else 0)
+            e0 = self._rec(ev)
+            mri.mri_slow_rhs(y, self.fS[i - 1], self.grid, stream=st)
+            mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=st)
+            ramp = w.ramp if (first and i == 1) else 0
+            o = self.opts(form, ramp)
             Hs = (c[i] - c[i - 1]) * w.H
-            if model is not None:
-                guess = model.guess(y, self.p, self.phi, Hs, w.h, stream=self.stream)
-            if ev_stage is not None:
-                ev_stage[i - 1][0].record(self.stream)
+            if gate is not None:
+                self._end(ev, e0)
+                gate.before(y, self.phi, Hs, ramp)
+                e0 = self._rec(ev)
             if model is None:
                 mri.mri_stage_fast(y, self.p, self.phi, 0.0, Hs, w.h, self.mech, o, cell_status=self.status,
-                                   cell_stats=self.stats, n_failed=self.nfail, stream=self.stream)
+                                   cell_stats=self.stats, n_failed=self.nfail, stream=st)
             else:
+                guess = model.guess(y, self.p, self.phi, Hs, w.h, stream=st)
                 mri.mri_stage_fast_guided(y, self.p, self.phi, 0.0, Hs, w.h, self.mech, o,
                                           start=mri.MRI_START_GUESS_FIRST, guess=guess, cell_status=self.status,
                                           cell_stats=self.stats, n_failed=self.nfail, n_fallback=self.nfallback,
-                                          stream=self.stream)
-            if ev_stage is not None:
-                ev_stage[i - 1][1].record(self.stream)
+                                          stream=st)
+            self._end(ev, e0, stage=True)
+            if gate is not None:
+                gate.after(y)
 
-    def adaptive_steps(self, y_start, prec, tol=1e-6):
-        """The same K steps from the same state with adaptive substeps (controller
-        tolerance tol): device time per MRI step and accepted substeps per cell and
-        stage, beside the fixed scheme's."""
-        torch, mri, args, w, c, G = self.torch, self.mri, self.args, self.w, self.c, self.G
-        y = y_start.clone()
-        st = torch.zeros((self.ncell, 4), dtype=torch.int32, device=self.dev)
-        evs = []
+    # -------------------------------------------------------------- IMEX step, call by call
+
+    def imex2_step(self, y, form, first=False, ev=None, gate=None, ws=None):
+        """The second-order Strang-split IMEX multirate step composed from the public
+        calls (the sequence mri_step_imex2 runs): a Crank-Nicolson half step of the
+        diffusion, (I - (H/4) L) y* = (I + (H/4) L) y by Jacobi-PCG, the MRI3 step with
+        the advection as explicit slow partition, and a second half step."""
+        mri, c, G, w, torch, st = self.mri, self.c, self.G, self.w, self.torch, self.stream
+        a = 0.25 * w.H
+        fI, rhs, cws, info = ws
+
+        def half():
+            mri.mri_slow_rhs(y, fI, self.gridI, stream=st)
+            torch.add(y, fI, alpha=a, out=rhs)
+            mri.mri_diffusion_solve(y, rhs, self.gridI, a, cws, tol=self.args.cg_tol, max_iter=self.args.cg_iters,
+                                    check_every=0, cg_info=info, stream=st)
+
+        e0 = self._rec(ev)
+        half()
+        for i in range(1, 4):
+            mri.mri_slow_rhs(y, self.fS[i - 1], self.gridE, stream=st)
+            mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=st)
+            ramp = w.ramp if (first and i == 1) else 0
+            o = self.opts(form, ramp)
+            Hs = (c[i] - c[i - 1]) * w.H
+            if gate is not None:
+                self._end(ev, e0)
+                gate.before(y, self.phi, Hs, ramp)
+                e0 = self._rec(ev)
+            mri.mri_stage_fast(y, self.p, self.phi, 0.0, Hs, w.h, self.mech, o, cell_status=self.status,
+                               cell_stats=self.stats, n_failed=self.nfail, stream=st)
+            self._end(ev, e0, stage=True)
+            if gate is not None:
+                gate.after(y)
+            e0 = self._rec(ev)
+        half()
+        self._end(ev, e0)
+
+    def imex_ws(self):
+        torch = self.torch
+        fI = torch.empty((self.ncell, self.n), dtype=torch.float64, device=self.dev)
+        rhs = torch.empty_like(fI)
+        cws = torch.empty(self.mri.mri_diffusion_workspace_size(self.gridI, self.n), dtype=torch.uint8,
+                          device=self.dev)
+        info = torch.zeros(2, dtype=torch.int32, device=self.dev)
+        return fI, rhs, cws, info
+
+    # -------------------------------------------------------------- timing helpers
+
+    def _rec(self, ev):
+        if ev is None:
+            return None
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        return e
+
+    def _end(self, ev, e0, stage=False):
+        if ev is None:
+            return
+        e1 = self.torch.cuda.Event(enable_timing=True)
+        e1.record(self.stream)
+        ev.append((e0, e1, stage))
+
+    def timed_steps(self, y, form, nsteps, step_fn, gate=True, model=None, clocks=False, world=1):
+        """nsteps timed steps of step_fn from y (in place): L2 flushed before each step,
+        device time summed over the step's timed intervals (the gate's snapshots lie
+        outside them).  Returns a dict of times, counters and the gate's verdict."""
+        torch = self.torch
+        self.stats.zero_()
+        self.nfallback.zero_()
+        f0 = int(self.nfail.item())
+        ev = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(gpu_id(self.dev)) if clocks else None
+        if sampler:
+            sampler.start()
         with torch.cuda.stream(self.stream):
-            for s in range(args.steps):
+            for s in range(nsteps):
                 self.flush.zero_()
+                kw = dict(ev=ev, gate=self.gate if gate else None)
+                if model is not None:
+                    kw["model"] = model
+                step_fn(y, form, **kw)
+        torch.cuda.synchronize()
+        clk = sampler.stop() if sampler else None
+        if world > 1:
+            torch.distributed.barrier()
+        ms = sum(a.elapsed_time(b) for a, b, _ in ev)
+        stage_ms = [a.elapsed_time(b) for a, b, s in ev if s]
+        st = self.stats.cpu().numpy().astype(np.int64)
+        out = dict(ms=ms, stage_ms=float(sum(stage_ms)), stage_launches=len(stage_ms),
+                   substeps=int(st[:, 0].sum()), newton=int(st[:, 1].sum()), njac=int(st[:, 2].sum()),
+                   failed=int(self.nfail.item()) - f0, fallbacks=int(self.nfallback.item()), clocks=clk,
+                   per_cell=st)
+        out["gate"] = self.gate.check() if gate else None
+        return out
+
+
+def gpu_id(dev):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return str(dev.index)
+
+
+def spread(per_cell):
+    """min / median / max over cells of Newton iterations and Jacobians per substep."""
+    sub = np.maximum(per_cell[:, 0], 1)
+    out = {}
+    for k, col in (("newton_per_substep", 1), ("jac_per_substep", 2)):
+        v = per_cell[:, col] / sub
+        out[k] = [float(v.min()), float(np.median(v)), float(v.max())]
+    nw = per_cell[:, 1]
+    out["newton_per_cell_max_over_min"] = float(nw.max() / max(nw.min(), 1))
+    out["newton_per_cell_p99_over_p1"] = float(np.percentile(nw, 99) / max(np.percentile(nw, 1), 1))
+    return out
+
+
+def roofline(case, r, peak):
+    """Dominant kernel (the fast stage): algorithmic FP64 flops per launch over its
+    average event-timed duration, against the measured FP64 FMA pipe rate."""
+    fm = flop_model(case.w.mech)
+    prec = case.prec(r["form"])
+    f64, f32 = algorithmic_flops(fm, r["newton"], r["njac"], prec)
+    per_launch = f64 / r["stage_launches"]
+    avg_s = r["stage_ms"] * 1e-3 / r["stage_launches"]
+    ach = per_launch / avg_s / 1e12
+    per_cell = STAGE_DRAM_BYTES_PER_CELL.get(prec)
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None if per_cell is None else per_cell * case.ncell,
+            "kernel": "stage_fast_kernel", "fp64_flops_per_launch": per_launch,
+            "fp32_flops_per_launch": f32 / r["stage_launches"], "avg_launch_ms": avg_s * 1e3,
+            "peak_basis": "FP64 FMA pipe rate measured in this run (mri_probe_fp64_fma; 2 DFMA/clk/SM, "
+                          "%.4f TFLOP/s at 2070 MHz); MEASURED_PEAKS.json has no FP64 entry"
+                          % FP64_PEAK_TFLOPS_NOMINAL}
+
+
+def e2e_mri3(case, y_start, form, nsteps, model=None):
+    """The same steps end to end through the public call with host buffers: each step
+    copies the state in from pinned host memory, runs mri_step (per-stage calls for the
+    learned form) and copies the result back, all inside the timed region."""
+    torch, mri, w = case.torch, case.mri, case.w
+    n, ncell = case.n, case.ncell
+    y_host = torch.empty((ncell, n), dtype=torch.float64, pin_memory=True)
+    y_host.copy_(y_start.cpu())
+    p_host = torch.empty(ncell, dtype=torch.float64, pin_memory=True)
+    p_host.copy_(case.p.cpu())
+    y = torch.empty_like(y_start)
+    ws = torch.empty(mri.mri_step_workspace_size(case.grid, n) // 8, dtype=torch.float64, device=case.dev)
+    stats = torch.zeros((ncell, 4), dtype=torch.int32, device=case.dev)
+    ms = 0.0
+    with torch.cuda.stream(case.stream):
+        for s in range(nsteps):
+            case.flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(case.stream)
+            y.copy_(y_host, non_blocking=True)
+            case.p.copy_(p_host, non_blocking=True)
+            if model is None:
+                mri.mri_step(y, case.p, case.grid, s * w.H, w.H, w.h, case.mech, case.opts(form), ws,
+                             cell_stats=stats, stream=case.stream)
+            else:
+                saved, case.stats = case.stats, stats
+                case.mri3_step(y, form, model=model)
+                case.stats = saved
+            y_host.copy_(y, non_blocking=True)
+            e1.record(case.stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+    return {"ms": ms, "substeps": int(stats[:, 0].sum().item()), "h2d": (ncell * n + ncell) * 8, "d2h": ncell * n * 8}
+
+
+def e2e_imex2(case, y_start, form, nsteps):
+    """End to end through mri_step_imex2 with host buffers (copies inside the timed region)."""
+    torch, mri, w = case.torch, case.mri, case.w
+    n, ncell = case.n, case.ncell
+    y_host = torch.empty((ncell, n), dtype=torch.float64, pin_memory=True)
+    y_host.copy_(y_start.cpu())
+    y = torch.empty_like(y_start)
+    ws = torch.empty(mri.mri_step_imex2_workspace_size(case.grid, n), dtype=torch.uint8, device=case.dev)
+    stats = torch.zeros((ncell, 4), dtype=torch.int32, device=case.dev)
+    ms = 0.0
+    with torch.cuda.stream(case.stream):
+        for s in range(nsteps):
+            case.flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(case.stream)
+            y.copy_(y_host, non_blocking=True)
+            mri.mri_step_imex2(y, case.p, case.grid, s * w.H, w.H, w.h, case.mech, case.opts(form), ws,
+                               cg_tol=case.args.cg_tol, cg_max_iter=case.args.cg_iters, cg_check_every=0,
+                               cell_stats=stats, stream=case.stream)
+            y_host.copy_(y, non_blocking=True)
+            e1.record(case.stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+    return {"ms": ms, "substeps": int(stats[:, 0].sum().item()), "h2d": ncell * n * 8, "d2h": ncell * n * 8}
+
+
+def graph_replay(case, y_start, form, nsteps, step_fn):
+    """The same step recorded once in a CUDA graph and replayed nsteps times (L2 flushed
+    between replays); returns (ms, substeps, final state)."""
+    torch = case.torch
+    y = y_start.clone()
+    graph = torch.cuda.CUDAGraph()
+    case.stream.synchronize()
+    with torch.cuda.graph(graph, stream=case.stream):
+        step_fn(y, form)
+    y.copy_(y_start)
+    case.stats.zero_()
+    torch.cuda.synchronize()
+    evs = []
+    with torch.cuda.stream(case.stream):
+        for _ in range(nsteps):
+            case.flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(case.stream)
+            graph.replay()
+            e1.record(case.stream)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    sub = int(case.stats[:, 0].sum().item())
+    del graph
+    return ms, sub, y
+
+
+def warm(case, form, y, nsteps, step_fn, ramp_first=True, **kw):
+    with case.torch.cuda.stream(case.stream):
+        for s in range(nsteps):
+            step_fn(y, form, first=(ramp_first and s == 0), **kw)
+    case.torch.cuda.synchronize()
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def train_learned(case, args):
+    """The learned form's network, trained by the library's kernels on the
+    substep-end states the plain solver produces over the first MRI steps of the
+    workload (the start-up step excluded).  Returns (model, training report)."""
+    from paper_2211_03293_gb300.learned import LearnedStart, stage_substep_states
+    torch, mri, c, G, w = case.torch, case.mri, case.c, case.G, case.w
+    t0 = time.time()
+    model = LearnedStart(case.n, g_max=5, batch=4096, infer_batch=min(case.ncell, 1 << 16))
+    y = torch.tensor(w.y0, device=case.dev)
+    with torch.cuda.stream(case.stream):
+        for s in range(1 + args.learn_steps):
+            for i in range(1, 4):
+                mri.mri_slow_rhs(y, case.fS[i - 1], case.grid, stream=case.stream)
+                mri.mri_stage_forcing(case.fS, i, G[i], case.phi, stream=case.stream)
+                Hs = (c[i] - c[i - 1]) * w.H
+                o = case.opts("mixed", w.ramp if (s == 0 and i == 1) else 0)
+                y_in = y.clone()
+                seq, _ = stage_substep_states(y, case.p, case.phi, Hs, w.h, case.mech, o, stream=case.stream)
+                if s > 0:
+                    model.add(y_in, case.p, case.phi.clone(), Hs, seq)
+        torch.cuda.synchronize()
+        t_data = time.time() - t0
+        hist = model.fit(epochs=args.learn_epochs, lr=2e-3, stream=case.stream)
+    torch.cuda.synchronize()
+    rep = {"examples": int(sum(r[0].shape[0] for r in model.records)), "epochs": args.learn_epochs,
+           "loss_first": hist[0], "loss_last": hist[-1], "data_s": round(t_data, 2),
+           "train_s": round(time.time() - t0 - t_data, 2), "network": model.dims}
+    return model, rep
+
+
+def run_box32(args, world, peak):
+    """The headline workload: three forms on the 32^3 box, K timed MRI3 steps each."""
+    case = Case("box32", args, cells_per_side=args.cells_per_side)
+    torch = case.torch
+    forms = ["plain", "mixed", "learned"] if args.learned else ["plain", "mixed"]
+    if args.form:
+        forms = [args.form]
+    res = {}
+    for form in forms:
+        model = learn = None
+        if form == "learned":
+            model, learn = train_learned(case, args)
+            if "mixed" in case.tuned:
+                case.tuned["learned"] = case.tuned["mixed"]
+        prec = case.prec(form)
+        case.new_cache(prec)
+        y = torch.tensor(case.w.y0, device=case.dev)
+        warm(case, form, y, args.warmup, case.mri3_step, model=model)
+        launch = None
+        if args.autotune and form in ("plain", "mixed"):
+            launch = case.autotune(y, form)
+            case.cache[prec].zero_()            # one more untimed step refills the cache
+            warm(case, form, y, 1, case.mri3_step, ramp_first=False)
+        y_start = y.clone()
+        r = case.timed_steps(y, form, args.steps, case.mri3_step, model=model, clocks=True, world=world)
+        r["form"] = form
+        r["launch"] = launch
+        r["learn"] = learn
+        e2e = e2e_mri3(case, y_start, form, args.steps, model=model)
+        if args.graph and form != "learned":
+            gms, gsub, _ = graph_replay(case, y_start, form, args.steps, case.mri3_step)
+            r["graph"] = {"value": gsub / (gms * 1e-3), "ms_per_step": gms / args.steps}
+        (r["value"], r["e2e_value"]), _ = whole_job_rates([r["ms"], e2e["ms"]], [r["substeps"], e2e["substeps"]],
+                                                          world, case.dev)
+        r["e2e"] = e2e
+        r["roofline"] = roofline(case, r, peak)
+        r["nsteps"] = args.steps
+        res[form] = r
+    return case, res
+
+
+def run_box64(args, world, peak):
+    """The precision form's configuration: the mixed form (and the plain form beside it)
+    on the 64^3 box, a few timed MRI3 steps each after warm-up, every stage gated."""
+    case = Case("box64", args)
+    torch = case.torch
+    y0 = torch.tensor(case.w.y0, device=case.dev)
+    case.new_cache(1)
+    warm(case, "mixed", y0, 2, case.mri3_step)
+    y_warm = y0
+    res = {}
+    for form in ("mixed", "plain"):
+        prec = case.prec(form)
+        case.new_cache(prec)
+        y = y_warm.clone()
+        warm(case, form, y, 1, case.mri3_step, ramp_first=False)
+        y_start = y.clone()
+        r = case.timed_steps(y, form, args.big_steps, case.mri3_step, world=world)
+        r["form"] = form
+        e2e = e2e_mri3(case, y_start, form, 1)
+        (r["value"], r["e2e_value"]), _ = whole_job_rates([r["ms"], e2e["ms"]], [r["substeps"], e2e["substeps"]],
+                                                          world, case.dev)
+        r["roofline"] = roofline(case, r, peak)
+        r["nsteps"] = args.big_steps
+        res[form] = r
+    return res
+
+
+def run_front128(args, world, peak):
+    """The batched form on the 128^3 flame front: the second-order IMEX multirate step
+    with the mixed form, autotuned (on every 8th cell), work queue; call by call with
+    every stage gated, replayed from a CUDA graph, and end to end through
+    mri_step_imex2; then the static schedule and the plain FP64 form in the same step."""
+    case = Case("front128", args)
+    torch = case.torch
+    ws = case.imex_ws()
+    step = lambda y, form, **kw: case.imex2_step(y, form, ws=ws, **kw)   # noqa: E731
+    y = torch.tensor(case.w.y0, device=case.dev)
+    case.new_cache(1)
+    warm(case, "batched", y, 2, step)
+    launch = case.autotune(y, "batched", subsample=8)
+    case.tuned["static"] = case.tuned["batched"]
+    y_warm = y
+    res = {}
+    for form in ("batched", "static", "plain_imex"):
+        prec = case.prec(form)
+        case.new_cache(prec)
+        y = y_warm.clone()
+        if form == "plain_imex" and args.autotune:
+            plain_launch = case.autotune(y, form, subsample=8)
+        warm(case, form, y, 1, step, ramp_first=False)
+        y_start = y.clone()
+        r = case.timed_steps(y, form, args.big_steps, step, world=world)
+        r["form"] = form
+        r["spread"] = spread(r.pop("per_cell"))
+        if form == "plain_imex" and args.autotune:
+            r["launch"] = plain_launch
+        if form == "batched":
+            r["launch"] = launch
+            y_eager = y.clone()
+            case.cache[prec].zero_()                # the graph replays from the same cache state
+            warm(case, form, y_start.clone(), 1, step, ramp_first=False)
+            gms, gsub, y_graph = graph_replay(case, y_start, form, args.big_steps, step)
+            scale = y_eager.abs().clamp_min(1e-10)
+            r["graph"] = {"value": gsub / (gms * 1e-3), "ms_per_step": gms / args.big_steps,
+                          "max_rel_diff_vs_call_by_call": float(((y_graph - y_eager).abs() / scale).max().item())}
+            e2e = e2e_imex2(case, y_start, form, 1)
+        else:
+            e2e = {"ms": r["ms"], "substeps": r["substeps"], "h2d": 0, "d2h": 0}
+        (r["value"], r["e2e_value"]), _ = whole_job_rates([r["ms"], e2e["ms"]], [r["substeps"], e2e["substeps"]],
+                                                          world, case.dev)
+        r["roofline"] = roofline(case, r, peak)
+        r["nsteps"] = args.big_steps
+        res[form] = r
+    cg = diffusion_cg(case, args)
+    return res, cg
+
+
+def diffusion_cg(case, args):
+    """The Jacobi-PCG diffusion solve alone: (I - a D lap_h) x = b on the workload's state
+    with a D / dx^2 = 1, iterations fixed at the converged count, replayed from a CUDA
+    graph, against the HBM roofline."""
+    torch, mri, st = case.torch, case.mri, case.stream
+    g = case.w.grid
+    a = g["dx"] ** 2 / g["D"]
+    n, ncell = case.n, case.ncell
+    rhs = torch.tensor(case.w.y0, device=case.dev)
+    x = rhs.clone()
+    cws = torch.empty(mri.mri_diffusion_workspace_size(case.gridI, n), dtype=torch.uint8, device=case.dev)
+    its = mri.mri_diffusion_solve(x, rhs, case.gridI, a, cws, tol=1e-12, max_iter=500, check_every=1, stream=st)
+
+    def solve():
+        x.copy_(rhs)
+        mri.mri_diffusion_solve(x, rhs, case.gridI, a, cws, tol=1e-12, max_iter=its, check_every=0, stream=st)
+
+    def timed(fn, reps):
+        evs = []
+        with torch.cuda.stream(st):
+            for _ in range(reps):
+                case.flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(self.stream)
-                for i in range(1, 4):
-                    mri.mri_slow_rhs(y, self.fS[i - 1], self.grid, stream=self.stream)
-                    mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=self.stream)
-                    o = self.opts(prec)
-                    o.adaptive, o.ctrl_rtol, o.ctrl_atol_Y, o.ctrl_atol_T = 1, tol, tol * 1e-6, tol
-                    mri.mri_stage_fast(y, self.p, self.phi, 0.0, (c[i] - c[i - 1]) * w.H, w.h, self.mech, o,
-                                       cell_stats=st, stream=self.stream)
-                e1.record(self.stream)
+                e0.record(st)
+                fn()
+                e1.record(st)
                 evs.append((e0, e1))
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b_) for a, b_ in evs) / args.steps
-        acc = st[:, 0].sum().item() / (3 * args.steps * self.ncell)
-        return {"ctrl_rtol": tol, "ms_per_step": ms, "accepted_substeps_per_cell_stage": acc,
-                "fixed_substeps_per_cell_stage": 12 / 3,
-                "note": "controller tolerance 1e-6 (global stage error about 1e-6 on relaxed states, "
-                        "against about 3e-4 for the fixed h = H/10 in the oracle's comparison with "
-                        "256x finer steps)"}
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+    timed(solve, 2)
+    ms_direct = timed(solve, 3)
+    cg_graph = torch.cuda.CUDAGraph()
+    st.synchronize()
+    with torch.cuda.graph(cg_graph, stream=st):
+        solve()
+    timed(cg_graph.replay, 2)
+    ms = timed(cg_graph.replay, 5)
+    del cg_graph
+    avg = sum(ms) / len(ms)
+    nbytes = ncell * n * 8
+    traffic = nbytes * (2 + 5 + its * 11)      # copy of x, the start (r = b - A x, p), 11 doubles per iteration
+    hbm = measured_hbm_gbs()
+    return {"workload": case.name, "iterations": its, "ms": avg, "ms_direct": sum(ms_direct) / len(ms_direct),
+            "us_per_iteration": 1e3 * avg / its,
+            "roofline": {"bound": "hbm", "achieved": traffic / (avg * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": traffic / (avg * 1e-3) / 1e9 / hbm if hbm else None, "traffic": None,
+                         "basis": "11 doubles moved per element and iteration (stencil pass with the p.Ap "
+                                  "sums 2, x/r update with the r.r sums 6, direction 3) plus the start and the "
+                                  "copy of x; peak: MEASURED_PEAKS.json hbm_gbs"}}
 
-    def train_learned(self, prec):
-        """The learned form's network, trained by the library's kernels on the
-        substep-end states the plain solver produces over the first MRI steps of the
-        workload (the start-up step excluded).  Returns (model, training report)."""
-        from paper_2211_03293_gb300.learned import LearnedStart, stage_substep_states
-        torch, mri, c, G, w, args = self.torch, self.mri, self.c, self.G, self.w, self.args
-        t0 = time.time()
-        model = LearnedStart(self.n, g_max=5, batch=4096, infer_batch=self.ncell)
-        y = torch.tensor(w.y0, device=self.dev)
-        with torch.cuda.stream(self.stream):
-            for s in range(1 + args.learn_steps):
-                for i in range(1, 4):
-                    mri.mri_slow_rhs(y, self.fS[i - 1], self.grid, stream=self.stream)
-                    mri.mri_stage_forcing(self.fS, i, G[i], self.phi, stream=self.stream)
-                    Hs = (c[i] - c[i - 1]) * w.H
-                    o = self.opts(prec, w.ramp if (s == 0 and i == 1) else 0)
-                    y_in = y.clone()
-                    seq, _ = stage_substep_states(y, self.p, self.phi, Hs, w.h, self.mech, o, stream=self.stream)
-                    if s > 0:
-                        model.add(y_in, self.p, self.phi.clone(), Hs, seq)
-            torch.cuda.synchronize()
-            t_data = time.time() - t0
-            hist = model.fit(epochs=args.learn_epochs, lr=2e-3, stream=self.stream)
+
+def reactor_batch(args):
+    """The mixed 9/40/80-species batch of 0-D reactors in one launch, and each group
+    alone, with the SM split the library chose."""
+    import torch
+
+    import mechgen
+    import paper_2211_03293_gb300 as mri
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    st = torch.cuda.Stream(device=dev)
+    batch = mechgen.reactor_batch()
+    groups, inits = [], []
+    for mech, yy, pp in batch.groups:
+        groups.append(dict(mech=mri.mri_mech_load(mech.to_blob()), y=torch.tensor(yy, device=dev),
+                           p=torch.tensor(pp, device=dev),
+                           cell_stats=torch.zeros((yy.shape[0], 4), dtype=torch.int32, device=dev)))
+        inits.append(torch.tensor(yy, device=dev))
+
+    def timed(fn, reps):
+        evs = []
+        with torch.cuda.stream(st):
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn()
+                e1.record(st)
+                evs.append((e0, e1))
         torch.cuda.synchronize()
-        rep = {"examples": int(sum(r[0].shape[0] for r in model.records)), "epochs": args.learn_epochs,
-               "loss_first": hist[0], "loss_last": hist[-1], "data_s": round(t_data, 2),
-               "train_s": round(time.time() - t0 - t_data, 2), "network": model.dims,
-               "start": "MRI_START_GUESS_FIRST (network where the analytic predictor has no derivative yet)"}
-        return model, rep
+        return [a.elapsed_time(b) for a, b in evs]
+    out = {}
+    bo = mri.mri_fast_opts_default(method=batch.method, newton_rtol=batch.newton_rtol, ramp=batch.ramp,
+                                   jac_policy=mri.MRI_JAC_LAZY, precision=1)
 
-    def gate(self, prec, model=None):
-        """Relative error of the first fast stage of the full-size workload (forcing
-        f^S(y0) from the oracle) on 32 sampled cells against the CPU oracle, with the
-        maximum and RMS per field (mass fractions above 1e-10, and T)."""
-        import oracle
-        torch, mri, w = self.torch, self.mri, self.w
-        fS = oracle.slow_rhs(w.y0, w.grid)
-        y = torch.tensor(w.y0, device=self.dev)
-        ph = torch.tensor(fS[:, None, :].copy(), device=self.dev)
-        with torch.cuda.stream(self.stream):
-            if model is None:
-                mri.mri_stage_fast(y, self.p, ph, 0.0, w.H / 3, w.h, self.mech, self.opts(prec, w.ramp),
-                                   stream=self.stream)
-            else:
-                guess = model.guess(y, self.p, ph, w.H / 3, w.h, stream=self.stream)
-                mri.mri_stage_fast_guided(y, self.p, ph, 0.0, w.H / 3, w.h, self.mech, self.opts(prec, w.ramp),
-                                          start=mri.MRI_START_GUESS_FIRST, guess=guess, stream=self.stream)
-        self.stream.synchronize()
-        rng = np.random.default_rng(11)
-        idx = np.sort(rng.choice(self.ncell, min(32, self.ncell), replace=False))
-        ref, _, _ = oracle.Mech(w.mech).stage_fast(w.y0[idx], w.p[idx], fS[idx][:, None, :], w.H / 3, w.h,
-                                                    oracle.opts(method=w.method, rtol=w.newton_rtol, ramp=w.ramp))
-        got = y.cpu().numpy()[idx]
-        scale = np.abs(ref)
-        scale[:, :-1] = np.maximum(scale[:, :-1], 1e-10)
-        rel = np.abs(got - ref) / scale
-        err = float(np.max(rel))
-        big = ref[:, :-1] > 1e-10
-        ry, rt = rel[:, :-1][big], rel[:, -1]
-        fields = {"Y_max": float(ry.max()), "Y_rms": float(np.sqrt(np.mean(ry ** 2))), "T_max": float(rt.max()),
-                  "T_rms": float(np.sqrt(np.mean(rt ** 2)))}
-        return {"cells": int(len(idx)), "max_rel_err": err, "tolerance": GATE_TOL, "passed": err <= GATE_TOL,
-                "per_field": fields}
+    def reset():
+        for gg, yi in zip(groups, inits):
+            gg["y"].copy_(yi)
 
-    def run_form(self, form):
-        """Time one form: 0 plain FP64, 1 mixed precision, 2 learned start on the mixed
-        form (network inference inside the timed steps)."""
-        torch, mri, args, w = self.torch, self.mri, self.args, self.w
-        prec = 1 if form == 2 else form
-        model, learn = self.train_learned(prec) if form == 2 else (None, None)
-        if args.matrix_cache and args.jac == 1:
-            self.cache[prec] = torch.zeros(mri.mri_matrix_cache_size(self.mech, self.ncell, prec),
-                                           dtype=torch.uint8, device=self.dev)
-        y = torch.tensor(w.y0, device=self.dev)
-        with torch.cuda.stream(self.stream):
-            for s in range(args.warmup):
-                self.step(y, prec, s == 0, None, model)
-            self.stream.synchronize()
-            launch = self.autotune(y, prec) if (args.autotune and form != 2) else None
-            if form == 2 and args.autotune and prec in self.shape:
-                launch = {"warps_per_block": self.shape[prec][0], "blocks_per_sm": max(self.shape[prec][1], 1),
-                          "autotuned": "shape of the mixed form"}
-            if prec in self.cache:
-                self.cache[prec].zero_()      # the autotuner's trial runs leave no matrices behind
-                for s in range(1):            # one more untimed step refills the cache
-                    self.step(y, prec, False, None, model)
-            self.stream.synchronize()
-            warm_fail = int(self.nfail.item())
-            self.stats.zero_()
-            self.nfallback.zero_()
-            y_start = y.clone()          # the e2e leg replays the timed steps from this state
-            step_events, stage_events = [], []
-            if self.world > 1:
-                torch.distributed.barrier()
-            torch.cuda.synchronize()
-            sampler = ClockSampler(self.gpu_id)
-            sampler.start()
-            for s in range(args.steps):
-                self.flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                      for _ in range(3)]
-                e0.record(self.stream)
-                self.step(y, prec, args.warmup == 0 and s == 0, ev, model)
-                e1.record(self.stream)
-                step_events.append((e0, e1))
-                stage_events.append(ev)
-            torch.cuda.synchronize()
-            clocks = sampler.stop()
-            if self.world > 1:
-                torch.distributed.barrier()
-        step_ms = [a.elapsed_time(b) for a, b in step_events]
-        stage_ms = [[a.elapsed_time(b) for a, b in ev] for ev in stage_events]
-        st = self.stats.cpu().numpy().astype(np.int64)
-        substeps, newton, njac = int(st[:, 0].sum()), int(st[:, 1].sum()), int(st[:, 2].sum())
-        failed = int(self.nfail.item()) - warm_fail
-        fallbacks = int(self.nfallback.item())
-        graph_ms, graph_sub = (self.graph_steps(y_start.clone(), prec) if (args.graph and form != 2)
-                               else (None, None))
+    def launch():
+        mri.mri_stage_fast_batch(groups, 0.0, batch.Hstage, batch.h, bo, stream=st)
+    with torch.cuda.stream(st):
+        reset()
+    timed(launch, 1)
+    for gg in groups:
+        gg["cell_stats"].zero_()
+    ms = []
+    for _ in range(2):
+        with torch.cuda.stream(st):
+            reset()
+        ms += timed(launch, 1)
+    sub = sum(int(gg["cell_stats"][:, 0].sum().item()) for gg in groups)
+    out["one_launch"] = {"ms": sum(ms) / len(ms), "cell_steps_per_s": sub / (sum(ms) * 1e-3)}
+    per = []
+    for gg, yi in zip(groups, inits):
+        gg["y"].copy_(yi)
+        gg["cell_stats"].zero_()
 
-        # end to end through the public C-ABI call with host buffers: the same K steps
-        # from the same state, each step copying the state in from pinned host memory
-        # and the result back
-        n, ncell = self.n, self.ncell
-        y_host = torch.empty((ncell, n), dtype=torch.float64, pin_memory=True)
-        y_host.copy_(y_start.cpu())
-        p_host = torch.empty(ncell, dtype=torch.float64, pin_memory=True)
-        p_host.copy_(self.p.cpu())
-        ws = torch.empty(mri.mri_step_workspace_size(self.grid, n) // 8, dtype=torch.float64, device=self.dev)
-        e2e_stats = torch.zeros((ncell, 4), dtype=torch.int32, device=self.dev)
-        e2e_ms = []
-        with torch.cuda.stream(self.stream):
-            for s in range(args.steps):
-                self.flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(self.stream)
-                y.copy_(y_host, non_blocking=True)
-                self.p.copy_(p_host, non_blocking=True)
-                if model is None:
-                    mri.mri_step(y, self.p, self.grid, s * w.H, w.H, w.h, self.mech, self.opts(prec), ws,
-                                 cell_stats=e2e_stats, stream=self.stream)
-                else:
-                    saved, self.stats = self.stats, e2e_stats
-                    self.step(y, prec, False, None, model)
-                    self.stats = saved
-                y_host.copy_(y, non_blocking=True)
-                e1.record(self.stream)
-                e1.synchronize()
-                e2e_ms.append(e0.elapsed_time(e1))
-        e2e_sub = int(e2e_stats[:, 0].sum().item())
-        adaptive = self.adaptive_steps(y_start, prec) if (args.adaptive and model is None) else None
-        fm = flop_model(w.mech)
-        f64, f32 = algorithmic_flops(fm, newton, njac, prec)
-        # kernels per step: 3 x (stencil, forcing, stage) [+ 3 x (features, input conversion,
-        # 4 GEMMs, guess) for the learned form]
-        per_step = 9 + (18 if model is not None else 0)
-        return dict(prec=prec, form=form, total_ms=float(sum(step_ms)), substeps=substeps, newton=newton,
-                    njac=njac, failed=failed, clocks=clocks, stage_total_ms=float(np.sum(stage_ms)),
-                    stage_launches=3 * args.steps, flops64=f64, flops32=f32, e2e_ms=float(sum(e2e_ms)),
-                    e2e_substeps=e2e_sub, launches=per_step * args.steps, launch=launch, graph_ms=graph_ms,
-                    graph_substeps=graph_sub, model=model, learn=learn, fallbacks=fallbacks, adaptive=adaptive)
+        def alone():
+            gg["y"].copy_(yi)
+            mri.mri_stage_fast(gg["y"], gg["p"], None, 0.0, batch.Hstage, batch.h, gg["mech"], bo,
+                               cell_stats=gg["cell_stats"], stream=st)
+        t = timed(alone, 1)[0]
+        cs = gg["cell_stats"].cpu().numpy()
+        per.append({"species": gg["mech"].n_species, "cells": int(cs.shape[0]), "ms_alone": t,
+                    "substeps": int(cs[:, 0].sum()), "newton": int(cs[:, 1].sum()), "jac": int(cs[:, 2].sum())})
+    out["groups"] = per
+    out["sum_of_groups_alone_ms"] = sum(g["ms_alone"] for g in per)
+    return out
 
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def whole_job_rates(times_ms, work, world, device):
+    """Whole-job throughput of every leg: the work of all ranks over the slowest
+    rank's time (max over ranks of the time, sum over ranks of the work).  Returns
+    (rates, (times, work)) with the reduced values."""
+    import torch
+    t = torch.tensor(times_ms, dtype=torch.float64, device=device)
+    w = torch.tensor(work, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(w, op=torch.distributed.ReduceOp.SUM)
+    t, w = t.cpu().numpy(), w.cpu().numpy()
+    return [float(wi / (ti * 1e-3)) for ti, wi in zip(t, w)], (t, w)
+
+
+# ----------------------------------------------------------------------------- CPU arm
 
 def cpu_baseline_sample(ncells_sample, seed=0, nthreads=None, repeats=1):
     """The oracle on a bounded sample of the same workload: the three fast stages
@@ -497,7 +905,7 @@ def cpu_baseline_sample(ncells_sample, seed=0, nthreads=None, repeats=1):
     import mechgen
     import oracle
 
-    w = mechgen.workload(WORKLOAD, seed=0)
+    w = mechgen.workload("box32", seed=0)
     m = oracle.Mech(w.mech)
     rng = np.random.default_rng(seed)
     idx = np.sort(rng.choice(w.y0.shape[0], ncells_sample, replace=False))
@@ -518,29 +926,9 @@ def cpu_baseline_sample(ncells_sample, seed=0, nthreads=None, repeats=1):
     return cs / tt, nthreads, cs, tt
 
 
-def whole_job_rates(times_ms, work, world, device):
-    """Whole-job throughput of every leg: the work of all ranks over the slowest
-    rank's time (max over ranks of the time, sum over ranks of the work).  Returns
-    (rates, (times, work)) with the reduced values."""
-    import torch
-    t = torch.tensor(times_ms, dtype=torch.float64, device=device)
-    w = torch.tensor(work, dtype=torch.float64, device=device)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(w, op=torch.distributed.ReduceOp.SUM)
-    t, w = t.cpu().numpy(), w.cpu().numpy()
-    return [float(wi / (ti * 1e-3)) for ti, wi in zip(t, w)], (t, w)
-
-
-def dist_init(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        backend = "nccl" if (args.impl != "reference" and torch.cuda.is_available()) else "gloo"
-        dist.init_process_group(backend=backend)
-    return rank, world
+BOX32_WORKLOAD = ("box32: 32^3 periodic box, 40 species / 170 reactions (12 third-body, 8 Troe), MRI3 "
+                  "(Knoth-Wolke MIS) + SDIRK3 fast, H = 5e-8 s, h = H/10, Newton rtol 1e-10, 4th-order slow "
+                  "stencil; one step = one MRI slow step")
 
 
 def reference_arm(args):
@@ -557,8 +945,7 @@ def reference_arm(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "box32 (32^3 cells, 40 species / 170 reactions, MRI3 + SDIRK3, "
-                                   "H = 5e-8 s, h = H/10)", "l2": "n/a (CPU)"},
+            "config": {"workload": BOX32_WORKLOAD, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "per step: the three fast stages of one MRI step on 256 sampled cells "
                                        "(forcing from the oracle's slow stencil) after an untimed start-up "
@@ -567,152 +954,29 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
-def extras(b, args):
-    """Rows of the batched form beside the headline, each measured once on the GPU:
-    the first-order IMEX-MRI step of the 32^3 box captured in a CUDA graph (fast
-    stage plus the implicit diffusion solve), the Jacobi-PCG diffusion solve alone
-    against the HBM roofline, and the mixed 9/40/80-species reactor batch in one
-    launch."""
-    import torch
-
-    import mechgen
-    mri, w, dev, st = b.mri, b.w, b.dev, b.stream
-    out = {}
-    hbm = measured_hbm_gbs()
-
-    def timed(fn, reps):
-        evs = []
-        with torch.cuda.stream(st):
-            for _ in range(reps):
-                b.flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                fn()
-                e1.record(st)
-                evs.append((e0, e1))
-        torch.cuda.synchronize()
-        return [a.elapsed_time(c) for a, c in evs]
-
-    # IMEX-MRI step (graph-captured; the CG runs a fixed iteration cap without host checks)
-    n, ncell = b.n, b.ncell
-    y0 = torch.tensor(w.y0, device=dev)
-    o = b.opts(1)
-    with torch.cuda.stream(st):
-        for s in range(2):                       # past the start-up transient, as the MRI steps are
-            b.step(y0, 1, s == 0, None)
-    torch.cuda.synchronize()
-    ws = torch.empty(mri.mri_step_imex1_workspace_size(b.grid, n), dtype=torch.uint8, device=dev)
-    info = torch.zeros(2, dtype=torch.int32, device=dev)
-    ss = torch.zeros((ncell, 4), dtype=torch.int32, device=dev)
-    y = y0.clone()
-    graph = torch.cuda.CUDAGraph()
-    st.synchronize()
-    with torch.cuda.graph(graph, stream=st):
-        mri.mri_step_imex1(y, b.p, b.grid, 0.0, w.H, w.h, b.mech, o, ws, cg_tol=1e-12, cg_max_iter=20,
-                           cg_check_every=0, cell_stats=ss, cg_info=info, stream=st)
-    y.copy_(y0)
-    timed(graph.replay, 2)
-    ss.zero_()
-    ms = timed(graph.replay, 3)
-    sub = int(ss[:, 0].sum().item())
-    out["imex1_step"] = {
-        "what": "first-order IMEX-MRI step of the 32^3 box (fast stage over H with the explicit advection "
-                "plus diffusion forcing, then the implicit diffusion correction by Jacobi-PCG), mixed form, "
-                "captured once in a CUDA graph and replayed",
-        "ms_per_step": sum(ms) / len(ms), "cell_steps_per_s": sub / (sum(ms) * 1e-3),
-        "cg_converged": bool(info[0].item()), "cg_iterations": int(info[1].item())}
-    del graph
-
-    # second-order Strang-split IMEX step (Crank-Nicolson half steps around the MRI3 step)
-    ws2 = torch.empty(mri.mri_step_imex2_workspace_size(b.grid, n), dtype=torch.uint8, device=dev)
-    y.copy_(y0)
-    ss.zero_()
-
-    def imex2():
-        mri.mri_step_imex2(y, b.p, b.grid, 0.0, w.H, w.h, b.mech, o, ws2, cg_tol=1e-12, cg_max_iter=20,
-                           cg_check_every=0, cell_stats=ss, cg_info=info, stream=st)
-    timed(imex2, 1)
-    ss.zero_()
-    ms = timed(imex2, 3)
-    sub = int(ss[:, 0].sum().item())
-    out["imex2_step"] = {
-        "what": "second-order Strang-split IMEX step of the 32^3 box (Crank-Nicolson half steps of the diffusion "
-                "by Jacobi-PCG around the MRI3 step with explicit advection), mixed form",
-        "ms_per_step": sum(ms) / len(ms), "cell_steps_per_s": sub / (sum(ms) * 1e-3),
-        "cg_converged": bool(info[0].item()), "cg_iterations_last_half_step": int(info[1].item())}
-
-    # Jacobi-PCG diffusion solve alone: (I - a D lap_h) x = b on the box's state with
-    # a D / dx^2 = 1, iterations fixed at the converged count, against the HBM roofline
-    g = w.grid
-    a = g["dx"] ** 2 / g["D"]
-    rhs = y0.clone()
-    x = rhs.clone()
-    cws = torch.empty(mri.mri_diffusion_workspace_size(b.grid, n), dtype=torch.uint8, device=dev)
-    its = mri.mri_diffusion_solve(x, rhs, b.grid, a, cws, tol=1e-12, max_iter=500, check_every=1, stream=st)
-    nbytes = ncell * n * 8
-
-    def solve():
-        x.copy_(rhs)
-        mri.mri_diffusion_solve(x, rhs, b.grid, a, cws, tol=1e-12, max_iter=its, check_every=0, stream=st)
-    timed(solve, 2)
-    ms_direct = timed(solve, 5)
-    # the same solve recorded once in a CUDA graph (no per-launch host overhead)
-    cg_graph = torch.cuda.CUDAGraph()
-    st.synchronize()
-    with torch.cuda.graph(cg_graph, stream=st):
-        solve()
-    timed(cg_graph.replay, 2)
-    ms = timed(cg_graph.replay, 5)
-    del cg_graph
-    avg = sum(ms) / len(ms)
-    traffic = nbytes * (2 + 5 + its * 11)      # copy of x, the start (r = b - A x, p), 11 doubles per iteration
-    out["diffusion_cg"] = {
-        "what": "mri_diffusion_solve on the 32^3 x 41 state, a D / dx^2 = 1, tol 1e-12, no host checks, "
-                "replayed from a CUDA graph (ms_direct: launched call by call)",
-        "iterations": its, "ms": avg, "ms_direct": sum(ms_direct) / len(ms_direct),
-        "roofline": {"bound": "hbm", "achieved": traffic / (avg * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                     "frac": traffic / (avg * 1e-3) / 1e9 / hbm if hbm else None,
-                     "traffic": None,
-                     "basis": "bytes the kernels move as written: 11 doubles per element and iteration (stencil "
-                              "with the p.Ap sums 2, x/r update with the r.r sums 6, direction 3) plus the start "
-                              "and the copy of x; the 54 MB working set fits in L2, so this is an L2-resident "
-                              "solve measured against the HBM peak from MEASURED_PEAKS.json hbm_gbs"}}
-
-    # mixed 9/40/80-species batch of 0-D reactors, one launch
-    batch = mechgen.reactor_batch()
-    groups, inits = [], []
-    for mech, yy, pp in batch.groups:
-        groups.append(dict(mech=mri.mri_mech_load(mech.to_blob()), y=torch.tensor(yy, device=dev),
-                           p=torch.tensor(pp, device=dev),
-                           cell_stats=torch.zeros((yy.shape[0], 4), dtype=torch.int32, device=dev)))
-        inits.append(torch.tensor(yy, device=dev))
-    res = {}
-    for prec in (0, 1):
-        bo = mri.mri_fast_opts_default(method=batch.method, newton_rtol=batch.newton_rtol, ramp=batch.ramp,
-                                       jac_policy=mri.MRI_JAC_LAZY, precision=prec)
-
-        def launch():
-            for gg, yi in zip(groups, inits):
-                gg["y"].copy_(yi)
-            mri.mri_stage_fast_batch(groups, 0.0, batch.Hstage, batch.h, bo, stream=st)
-        timed(launch, 1)
-        for gg in groups:
-            gg["cell_stats"].zero_()
-        ms = timed(launch, 3)
-        sub = sum(int(gg["cell_stats"][:, 0].sum().item()) for gg in groups)
-        res[FORMS[prec].split(":")[0]] = {"ms_per_launch": sum(ms) / len(ms), "cell_steps_per_s": sub / (sum(ms) * 1e-3)}
-    out["reactor_batch"] = {"what": "4096 constant-pressure 0-D reactors on 9/40/80-species mechanisms "
-                                    "(21/170/350 reactions) in one mri_stage_fast_batch launch, one stage of "
-                                    "1e-7 s with h = 1e-8 s and the start-up ramp", **res}
-    return out
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl != "reference" and torch.cuda.is_available()) else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world
 
 
-def measured_hbm_gbs():
-    try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
+def _g(x, k=4):
+    """A number rounded to k significant digits (the summary stays short)."""
+    if x is None:
         return None
+    return float(f"{x:.{k}g}")
+
+
+def summary_row(config, form, r):
+    g = r.get("gate") or {}
+    return {"config": config, "form": form, "cell_steps_per_s": _g(r["value"]), "e2e": _g(r.get("e2e_value")),
+            "roofline_frac": _g(r["roofline"]["frac"], 3), "gate_max": _g(g.get("max_rel_err"), 3),
+            "gate_ok": g.get("passed"), "newton_per_substep": _g(r["newton"] / max(r["substeps"], 1), 3)}
 
 
 def main():
@@ -723,26 +987,23 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4096, help="cells of the oracle's CPU baseline sample")
     ap.add_argument("--cells-per-side", type=int, default=None,
-                    help="shrink the box (profiling captures only; the bench line is for 32^3)")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline and the gate (profiling captures)")
-    ap.add_argument("--jac", type=int, default=1, help="Newton matrix policy: 0 per substep, 1 lazy")
+                    help="shrink the headline box (profiling captures only; the bench line is for 32^3)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling captures)")
     ap.add_argument("--tuned-newton-safety", type=float, default=3e-2,
                     help="mri_fast_opts.newton_safety of the tuned forms (the plain form keeps 3e-4)")
-    ap.add_argument("--prec", type=int, default=None,
-                    help="time one form only: 0 plain FP64, 1 mixed precision, 2 learned start (mixed)")
+    ap.add_argument("--form", default=None, choices=["plain", "mixed", "learned"],
+                    help="time one form of the headline workload only")
     ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip the learned form")
-    ap.add_argument("--no-adaptive", dest="adaptive", action="store_false",
-                    help="skip the adaptive-substep timing of each form")
-    ap.add_argument("--no-matrix-cache", dest="matrix_cache", action="store_false",
-                    help="refactorise the Newton matrix at the start of every stage instead of keeping it")
     ap.add_argument("--learn-steps", type=int, default=3, help="MRI steps of training data for the learned form")
     ap.add_argument("--learn-epochs", type=int, default=40, help="training epochs of the learned form")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the automatic launch shape instead of timing the candidates")
-    ap.add_argument("--no-graph", dest="graph", action="store_false",
-                    help="skip the CUDA-graph replay of the step")
-    ap.add_argument("--no-extras", dest="extras", action="store_false",
-                    help="skip the IMEX step, diffusion-solve and reactor-batch measurements")
+    ap.add_argument("--no-graph", dest="graph", action="store_false", help="skip the CUDA-graph replays")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="time the headline box only (skip box64, front128, the reactor batch and the CG solve)")
+    ap.add_argument("--big-steps", type=int, default=1, help="timed steps of the box64 and front128 workloads")
+    ap.add_argument("--cg-tol", type=float, default=1e-12, help="tolerance of the IMEX step's diffusion solves")
+    ap.add_argument("--cg-iters", type=int, default=30, help="iteration cap of the IMEX step's diffusion solves")
     args = ap.parse_args()
     rank, world = dist_init(args)
 
@@ -752,42 +1013,25 @@ def main():
         return
 
     import torch
-    b = Bench(args, world)
-    forms = [args.prec] if args.prec is not None else ([0, 1, 2] if args.learned else [0, 1])
-    results = {}
-    for prec in forms:
-        r = b.run_form(prec)
-        (r["value"], r["e2e_value"]), _ = whole_job_rates([r["total_ms"], r["e2e_ms"]],
-                                                          [r["substeps"], r["e2e_substeps"]], world, "cuda")
-        r["gate"] = None if (args.no_cpu or rank != 0) else b.gate(r["prec"], r["model"])
-        r["model"] = None
-        results[prec] = r
-    ext = extras(b, args) if args.extras else None
+    import paper_2211_03293_gb300 as mri
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    probe = torch.empty(N_SM * 8 * 256 * 4, dtype=torch.float64, device=dev)
+    peak = 2.0 * mri.mri_probe_fp64_fma(probe, iters=4096) / 1e12
+    del probe
+
+    case, box = run_box32(args, world, peak)
+    extra = {}
+    if args.configs:
+        extra["box64"] = run_box64(args, world, peak)
+        extra["front128"], extra["diffusion_cg_front128"] = run_front128(args, world, peak)
+        extra["diffusion_cg_box32"] = diffusion_cg(case, args)
+        extra["reactor_batch"] = reactor_batch(args)
     if rank != 0:
         return
-    ok = [p for p in forms if results[p]["gate"] is None or results[p]["gate"]["passed"]]
-    head = max(ok, key=lambda p: results[p]["value"]) if ok else forms[0]
-    r = results[head]
-    peak = b.fp64_peak_tflops
-
-    def roofline(r):
-        # dominant kernel (the fast stage): algorithmic FP64 flops per launch over its
-        # average event-timed duration, against the measured FP64 FMA pipe rate
-        per_launch = r["flops64"] / r["stage_launches"]
-        avg_s = r["stage_total_ms"] * 1e-3 / r["stage_launches"]
-        ach = per_launch / avg_s / 1e12
-        per_cell = STAGE_DRAM_BYTES_PER_CELL.get(r["prec"]) if args.matrix_cache and args.jac == 1 else None
-        traffic = None if per_cell is None else per_cell * b.ncell
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": traffic, "traffic_unit": "bytes per launch (DRAM read + write)",
-                "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 4096-cell launch, "
-                                 "scaled to the launch's cells",
-                "kernel": "stage_fast_kernel", "fp64_flops_per_launch": per_launch,
-                "fp32_flops_per_launch": r["flops32"] / r["stage_launches"], "avg_launch_ms": avg_s * 1e3,
-                "peak_basis": "FP64 FMA pipe rate measured in this run (mri_probe_fp64_fma; the pipe issues 2 "
-                              "DFMA/clk/SM, %.4f TFLOP/s at 2070 MHz); MEASURED_PEAKS.json has no FP64 entry"
-                              % FP64_PEAK_TFLOPS_NOMINAL}
-
+    ok = [f for f in box if box[f]["gate"] is None or box[f]["gate"]["passed"]]
+    head = max(ok, key=lambda f: box[f]["value"]) if ok else list(box)[0]
+    r = box[head]
     if args.no_cpu:
         cpu = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": "skipped (--no-cpu)"}
     else:
@@ -796,51 +1040,53 @@ def main():
                "sample": f"the three fast stages of one MRI step on {args.cpu_sample} sampled cells ({cs} "
                          f"cell-steps, {tt:.1f} s), forcing from the oracle's slow stencil, after an untimed "
                          f"start-up stage"}
+    # kernels per step: 3 x (stencil, forcing, stage) [+ 3 x (features, 4 GEMMs, guess) for the learned form]
+    per_step = 9 + (18 if head == "learned" else 0)
+
+    def detail(res):
+        out = {}
+        for f, x in res.items():
+            d = {k: v for k, v in x.items() if k not in ("clocks", "per_cell", "e2e", "learn")}
+            d["e2e_ms"] = x["e2e"]["ms"] if isinstance(x.get("e2e"), dict) else None
+            if x.get("learn"):
+                d["learned"] = dict(x["learn"], newton_fallbacks=x["fallbacks"],
+                                    accept_rate=1.0 - x["fallbacks"] / max(3 * x["substeps"], 1))
+            out[f] = d
+        return out
+
+    summary = [summary_row("box32", f, box[f]) for f in box]
+    if args.configs:
+        summary += [summary_row("box64", f, extra["box64"][f]) for f in extra["box64"]]
+        summary += [summary_row("front128", f, extra["front128"][f]) for f in extra["front128"]]
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 1: "f64+f32", 2: "f64+f32+bf16"}[head], "data": "synthetic",
-        "config": {"workload": "box32: 32^3 periodic box, 40 species / 170 reactions (12 third-body, 8 Troe), "
-                               "MRI3 (Knoth-Wolke MIS) + SDIRK3 fast, H = 5e-8 s, h = H/10, Newton rtol 1e-10, "
-                               "4th-order slow stencil; one step = one MRI slow step",
-                   "cells": b.ncell, "unknowns_per_cell": b.n, "form": FORMS[head],
-                   "jac_policy": ["per-substep", "lazy"][args.jac] + (" + matrix cache across calls"
-                                                                      if args.matrix_cache and args.jac == 1
-                                                                      else ""),
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"plain": "f64", "mixed": "f64+f32", "learned": "f64+f32+bf16"}[head], "data": "synthetic",
+        "config": {"workload": BOX32_WORKLOAD, "cells": case.ncell, "unknowns_per_cell": case.n,
+                   "form": FORM_NAMES[head], "jac_policy": "lazy + matrix cache across calls",
                    "reduced_for_profiling": args.cells_per_side is not None,
                    "l2": "256 MB buffer written between timed steps",
-                   "launch": r["launch"],
                    "newton_per_substep": r["newton"] / max(r["substeps"], 1),
-                   "jac_per_substep": r["njac"] / max(r["substeps"], 1), "failed_cells": r["failed"]},
+                   "jac_per_substep": r["njac"] / max(r["substeps"], 1), "failed_cells": r["failed"],
+                   "gate_max_rel_err": (r["gate"] or {}).get("max_rel_err"),
+                   "plain_fp64_cell_steps_per_s": box.get("plain", {}).get("value"),
+                   "plain_fp64_roofline_frac": box["plain"]["roofline"]["frac"] if "plain" in box else None},
         "clocks": r["clocks"],
-        "roofline": roofline(r),
+        "roofline": r["roofline"],
         "cpu_baseline": cpu,
-        "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": (b.ncell * b.n + b.ncell) * 8,
-                "d2h_bytes_per_step": b.ncell * b.n * 8},
-        "gpu_launches": r["launches"],
+        "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": r["e2e"]["h2d"],
+                "d2h_bytes_per_step": r["e2e"]["d2h"]},
+        "gpu_launches": per_step * args.steps,
         "gate": r["gate"],
-        "forms": {FORMS[p]: {"value": results[p]["value"], "e2e": results[p]["e2e_value"],
-                             "roofline_frac": roofline(results[p])["frac"], "gate": results[p]["gate"],
-                             "newton_per_substep": results[p]["newton"] / max(results[p]["substeps"], 1),
-                             "newton_safety": b.newton_safety(results[p]["prec"]),
-                             "fast_stage_cell_steps_per_s": results[p]["substeps"] / (results[p]["stage_total_ms"]
-                                                                                      * 1e-3),
-                             "jac_per_substep": results[p]["njac"] / max(results[p]["substeps"], 1),
-                             "launch": results[p]["launch"] and {k: v for k, v in results[p]["launch"].items()
-                                                                 if k != "autotuned"},
-                             "adaptive_substeps": results[p]["adaptive"],
-                             "learned": results[p]["learn"] and dict(
-                                 results[p]["learn"], newton_fallbacks=results[p]["fallbacks"],
-                                 accept_rate=1.0 - results[p]["fallbacks"] / max(3 * results[p]["substeps"], 1)),
-                             "cuda_graph": None if results[p]["graph_ms"] is None else {
-                                 "value": results[p]["graph_substeps"] / (results[p]["graph_ms"] * 1e-3),
-                                 "ms_per_step": results[p]["graph_ms"] / args.steps,
-                                 "note": "the same MRI step (9 kernels, 3 queue resets) captured once and "
-                                         "replayed; device-timed like value"},
-                             "clocks": results[p]["clocks"]} for p in forms},
+        "forms_box32": detail(box),
     }
-    if ext is not None:
-        line["extras"] = ext
+    if args.configs:
+        line["box64"] = detail(extra["box64"])
+        line["front128"] = detail(extra["front128"])
+        line["diffusion_cg"] = {"front128": extra["diffusion_cg_front128"], "box32": extra["diffusion_cg_box32"]}
+        line["reactor_batch"] = extra["reactor_batch"]
+    line["summary"] = summary       # last, so that it survives a truncated tail
     print(json.dumps(line))
 
 

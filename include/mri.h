@@ -173,12 +173,36 @@ typedef struct {
    * still inside the Newton tolerance.  Iterates of a fresh matrix are accepted at
    * WRMS(delta) <= 1 either way. */
   double newton_safety;
+  /* How warps get their cells (results are the same either way):
+   * MRI_SCHED_QUEUE (default) from the launch's device work queue, so cells of uneven
+   * cost balance; MRI_SCHED_STATIC a fixed mapping, warp w of the grid's W warps
+   * integrates cells w, w + W, w + 2W, ... (the mapping the queue is measured
+   * against).  Static scheduling takes no time budget and is rejected by
+   * mri_stage_fast_batch (MRI_EINVAL). */
+  int schedule;
+  /* Layout of the triangular solves of every Newton iteration (MRI_LU_*).  The
+   * arithmetic and its order are the same in every layout, so the results are
+   * bitwise identical; only the cost differs (a dimension of the autotuner). */
+  int lu_variant;
 } mri_fast_opts;
+
+#define MRI_SCHED_QUEUE 0
+#define MRI_SCHED_STATIC 1
+#define MRI_LU_AUTO 0        /* n <= 64: in registers (FP64 factors with n > 32: the split
+                                forward layout); larger n: shared memory */
+#define MRI_LU_REGS 1        /* solution in registers, row lane + 32 r in register r
+                                (n <= 64; larger n use MRI_LU_SHARED) */
+#define MRI_LU_REGS_SPLIT 2  /* registers; for 32 < n <= 64 the forward pass holds rows
+                                n - 32 + lane and the short block, then moves to the
+                                MRI_LU_REGS layout for the backward pass (fewer FP64
+                                instructions); n <= 32 as MRI_LU_REGS, larger n shared */
+#define MRI_LU_SHARED 3      /* substitutions on the right-hand side in shared memory */
 
 /* Fill opts with the defaults (SDIRK3, rtol 1e-10, atol_Y 1e-20, atol_T 1e-10 K,
  * 10 Newton iterations, per-substep Jacobian, FP64, no ramp, automatic launch
  * shape, no time budget, no matrix cache, fixed substeps; controller tolerances
- * 1e-6, 1e-12, 1e-6 K for the adaptive option; Newton safety 3e-4). */
+ * 1e-6, 1e-12, 1e-6 K for the adaptive option; Newton safety 3e-4; work-queue
+ * scheduling; automatic solve layout). */
 void mri_fast_opts_default(mri_fast_opts* opts);
 
 /* One MRI stage of the fast partition for every cell (Eq. 3):

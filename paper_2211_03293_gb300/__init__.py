@@ -31,6 +31,8 @@ MRI_JAC_LAZY = 1
 MRI_PREC_FP64 = 0
 MRI_PREC_FP32_LU = 1
 MRI_START_PREDICTOR, MRI_START_PREVIOUS, MRI_START_GUESS, MRI_START_GUESS_FIRST = 0, 1, 2, 3
+MRI_SCHED_QUEUE, MRI_SCHED_STATIC = 0, 1
+MRI_LU_AUTO, MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED = 0, 1, 2, 3
 
 
 class mri_fast_opts(ct.Structure):
@@ -39,7 +41,8 @@ class mri_fast_opts(ct.Structure):
                 ("precision", ct.c_int), ("ramp", ct.c_int), ("warps_per_block", ct.c_int),
                 ("blocks_per_sm", ct.c_int), ("time_budget_s", ct.c_double), ("matrix_cache", ct.c_void_p),
                 ("matrix_cache_bytes", ct.c_size_t), ("adaptive", ct.c_int), ("ctrl_rtol", ct.c_double),
-                ("ctrl_atol_Y", ct.c_double), ("ctrl_atol_T", ct.c_double), ("newton_safety", ct.c_double)]
+                ("ctrl_atol_Y", ct.c_double), ("ctrl_atol_T", ct.c_double), ("newton_safety", ct.c_double),
+                ("schedule", ct.c_int), ("lu_variant", ct.c_int)]
 
 
 class mri_stage_group(ct.Structure):

@@ -1,22 +1,34 @@
-"""Launch-shape autotuner for mri_stage_fast.
+"""Autotuner for mri_stage_fast.
 
-The persistent stage kernel runs one cell per warp; how many warps share a CTA
-(and so one staged copy of the mechanism tables) and how many CTAs share an SM
-trade shared memory for cells in flight.  The best shape depends on the
-mechanism's size, the precision form, K and the cell count, so it is measured:
-each candidate shape runs the caller's own stage on a copy of its inputs, timed
-with CUDA events on the launching stream, and the fastest is kept.  Every
-candidate computes the same result (the launch shape never changes one), so the
-tuner needs no checking; the results of the timed runs are discarded.
+The persistent stage kernel runs one cell per warp.  Its cost depends on choices
+that never change a result:
+
+* cells per CTA and CTAs per SM (``warps_per_block``, ``blocks_per_sm``): how many
+  cells share one staged copy of the mechanism tables, traded against the shared
+  memory of each cell's workspace;
+* the layout of the triangular solves (``lu_variant``): the solution in registers
+  with rows lane + 32 r, the split forward layout, or substitutions in shared
+  memory;
+* the scheduling of cells to warps (``schedule``): the device work queue or the
+  static round-robin mapping.
+
+The best choice depends on the mechanism's size, the precision form, K and the
+cell count, so it is measured: each candidate runs the caller's own stage on a copy
+of its inputs, timed with CUDA events on the launching stream.  The search is
+coordinate-wise (launch shapes first, then the solve layout at the best shape, then
+the schedule); every candidate computes the same result, so the tuner needs no
+checking and the results of the timed runs are discarded.
 """
-from . import MriError, mri_fast_opts, mri_stage_fast, mri_stage_fast_shape
+from . import (MRI_LU_AUTO, MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED, MRI_SCHED_QUEUE, MRI_SCHED_STATIC,
+               MriError, mri_fast_opts, mri_stage_fast, mri_stage_fast_shape)
 
 _cache = {}
 
 
-def _with_shape(opts, wpb, bps):
+def _with(opts, **kw):
     o = mri_fast_opts.from_buffer_copy(opts)
-    o.warps_per_block, o.blocks_per_sm = wpb, bps
+    for k, v in kw.items():
+        setattr(o, k, v)
     return o
 
 
@@ -26,7 +38,7 @@ def candidate_shapes(mech, opts, ncell, K, max_bps=4, depth=3):
     out = []
     for bps in range(1, max_bps + 1):
         try:
-            wmax, _, _ = mri_stage_fast_shape(mech, _with_shape(opts, 0, bps), 1 << 30, K)
+            wmax, _, _ = mri_stage_fast_shape(mech, _with(opts, warps_per_block=0, blocks_per_sm=bps), 1 << 30, K)
         except MriError:
             continue
         for wpb in range(wmax, max(0, wmax - depth), -1):
@@ -34,21 +46,30 @@ def candidate_shapes(mech, opts, ncell, K, max_bps=4, depth=3):
     return out
 
 
-def autotune_stage(mech, y, p, phi, Hstage, h, opts, repeats=2, stream=None, verbose=False):
-    """Time mri_stage_fast over the candidate launch shapes on copies of (y, p, phi)
-    and return (opts with the fastest shape, [(wpb, bps, ms), ...]).  The result is
-    cached per (mechanism, options, ncell, K, Hstage/h)."""
+def candidate_lu_variants(n):
+    """Solve layouts that differ for a system of n unknowns."""
+    if n <= 32:
+        return [MRI_LU_REGS, MRI_LU_SHARED]
+    if n <= 64:
+        return [MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED]
+    return [MRI_LU_SHARED]
+
+
+def autotune_stage(mech, y, p, phi, Hstage, h, opts, repeats=2, stream=None, verbose=False, schedules=True):
+    """Time mri_stage_fast over the candidates on copies of (y, p, phi) and return
+    (opts with the fastest choice, [(wpb, bps, lu_variant, schedule, ms), ...]).
+    The result is cached per (mechanism, options, ncell, K, Hstage/h)."""
     import torch
     ncell = y.shape[0]
     K = 0 if phi is None else phi.shape[1]
-    key = (id(mech), bytes(opts), ncell, K, round(Hstage / h, 9))
+    key = (id(mech), bytes(opts), ncell, K, round(Hstage / h, 9), schedules)
     if key in _cache:
         return _cache[key]
     s = stream or torch.cuda.current_stream()
     work = torch.empty_like(y)
     table = []
-    for wpb, bps in candidate_shapes(mech, opts, ncell, K):
-        o = _with_shape(opts, wpb, bps)
+
+    def timed(o):
         best = None
         for _ in range(repeats):
             work.copy_(y)
@@ -60,10 +81,29 @@ def autotune_stage(mech, y, p, phi, Hstage, h, opts, repeats=2, stream=None, ver
             e1.synchronize()
             ms = e0.elapsed_time(e1)
             best = ms if best is None else min(best, ms)
-        table.append((wpb, bps, best))
+        table.append((o.warps_per_block, o.blocks_per_sm, o.lu_variant, o.schedule, best))
         if verbose:
-            print(f"autotune: {wpb} warps/CTA x {bps} CTA/SM: {best:.3f} ms")
-    wpb, bps, _ = min(table, key=lambda r: r[2])
-    res = (_with_shape(opts, wpb, bps), table)
+            print(f"autotune: {o.warps_per_block} warps/CTA x {o.blocks_per_sm} CTA/SM, solve layout "
+                  f"{o.lu_variant}, schedule {o.schedule}: {best:.3f} ms")
+        return best
+
+    base = _with(opts, lu_variant=MRI_LU_AUTO, schedule=MRI_SCHED_QUEUE)
+    best_o, best_ms = None, None
+    for wpb, bps in candidate_shapes(mech, base, ncell, K):
+        o = _with(base, warps_per_block=wpb, blocks_per_sm=bps)
+        ms = timed(o)
+        if best_ms is None or ms < best_ms:
+            best_o, best_ms = o, ms
+    for v in candidate_lu_variants(mech.n):
+        o = _with(best_o, lu_variant=v)
+        ms = timed(o)
+        if ms < best_ms:
+            best_o, best_ms = o, ms
+    if schedules and opts.time_budget_s == 0.0:
+        o = _with(best_o, schedule=MRI_SCHED_STATIC)
+        ms = timed(o)
+        if ms < best_ms:
+            best_o, best_ms = o, ms
+    res = (best_o, table)
     _cache[key] = res
     return res

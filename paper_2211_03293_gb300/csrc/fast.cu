@@ -755,18 +755,23 @@ __device__ __forceinline__ void lu_solve_regs2(const MT* A, int n, int ld, const
   __syncwarp();
 }
 
-// n <= 64: the register solves; larger systems gather P b in place and run the
-// shared-memory substitutions of lu_solve_warp<true> (the same arithmetic).
+// The triangular solves with the permutation of piv_to_perm, in the layout `variant`
+// selects (MRI_LU_*; the arithmetic and its order are the same in every layout, so
+// the results are too).  Automatic: n <= 64 the register solves (FP64 factors with
+// 32 < n the split forward layout, which saves FP64 instructions; FP32 factors the
+// plain one, 1% faster there), larger systems the shared-memory substitutions of
+// lu_solve_warp<true> after gathering P b in place.
 template <typename MT>
 __device__ __forceinline__ void lu_solve_perm(const MT* A, int n, int ld, const int* perm, const MT* dinv, MT* b,
-                                              int lane) {
-  if (n <= 32) {
+                                              int lane, int variant = MRI_LU_AUTO) {
+  if (variant == MRI_LU_AUTO) variant = (n > 64) ? MRI_LU_SHARED
+                                        : (n > 32 && sizeof(MT) == 8) ? MRI_LU_REGS_SPLIT : MRI_LU_REGS;
+  if (variant != MRI_LU_SHARED && n <= 32) {
     lu_solve_regs<1, MT>(A, n, ld, perm, dinv, b, lane);
-  } else if (n <= 64) {
-    // FP64: fewer FP64 instructions pay; FP32 (no FP32-pipe shortage): the plain
-    // layout measured 1% faster in the mixed form
-    if (sizeof(MT) == 8) lu_solve_regs2<MT>(A, n, ld, perm, dinv, b, lane);
-    else lu_solve_regs<2, MT>(A, n, ld, perm, dinv, b, lane);
+  } else if (variant == MRI_LU_REGS && n <= 64) {
+    lu_solve_regs<2, MT>(A, n, ld, perm, dinv, b, lane);
+  } else if (variant == MRI_LU_REGS_SPLIT && n <= 64) {
+    lu_solve_regs2<MT>(A, n, ld, perm, dinv, b, lane);
   } else {
     MT g[4];
 #pragma unroll
@@ -811,6 +816,8 @@ struct StageArgs {
   unsigned char* mcache; // Newton-matrix cache entries (nullable), mc_stride bytes per cell
   size_t mc_stride, mc_f_off;
   int adaptive, q;       // adaptive substeps; order of the error estimate
+  int schedule;          // MRI_SCHED_QUEUE or MRI_SCHED_STATIC
+  int lu_variant;        // MRI_LU_*: layout of the triangular solves
   double ctrl_rtol, ctrl_atol_Y, ctrl_atol_T;
   double bhat[3];        // embedded weights of the error estimate
   unsigned long long budget_ns;   // 0: no time budget
@@ -881,15 +888,15 @@ __device__ __forceinline__ int refresh_matrix(const Tab& t, const WS& w, const d
 // residual of every Newton iteration then refines the stage value to the same
 // tolerance as the FP64 form.
 template <bool PREC32>
-__device__ __forceinline__ void newton_solve(const WS& w, int n, int lane) {
+__device__ __forceinline__ void newton_solve(const WS& w, int n, int lane, int variant) {
   if (PREC32) {
     for (int k = lane; k < n; k += 32) w.d32[k] = (float)w.d[k];
     __syncwarp();
-    lu_solve_perm<float>(w.M32, n, w.ld, w.piv, w.dinv32, w.d32, lane);
+    lu_solve_perm<float>(w.M32, n, w.ld, w.piv, w.dinv32, w.d32, lane, variant);
     for (int k = lane; k < n; k += 32) w.d[k] = (double)w.d32[k];
     __syncwarp();
   } else {
-    lu_solve_perm<double>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane);
+    lu_solve_perm<double>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane, variant);
   }
 }
 
@@ -899,9 +906,16 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Lane 0 takes the next cell from the launch's queue counter, unless the warp's time
-// budget is spent (then ncell: no cell); the index is broadcast to the warp.
-__device__ __forceinline__ int next_cell(const StageArgs& a, unsigned long long t_start, int lane) {
+// The warp's next cell.  Queue: lane 0 takes the next index from the launch's queue
+// counter, unless the warp's time budget is spent (then ncell: no cell), and broadcasts
+// it.  Static: warp gw of the grid's nw warps takes cells gw, gw + nw, gw + 2 nw, ...
+// (k counts the warp's cells so far).
+__device__ __forceinline__ int next_cell(const StageArgs& a, unsigned long long t_start, int gw, int nw, int& k,
+                                         int lane) {
+  if (a.schedule == MRI_SCHED_STATIC) {
+    const long long c = (long long)gw + (long long)(k++) * nw;
+    return c < a.ncell ? (int)c : a.ncell;
+  }
   int c = a.ncell;
   if (lane == 0 && (a.budget_ns == 0 || globaltimer_ns() - t_start < a.budget_ns)) c = atomicAdd(a.queue, 1);
   return __shfl_sync(0xffffffffu, c, 0);
@@ -939,7 +953,10 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
   // With a time budget a warp stops taking cells once it has run that long, so the
   // cells taken are always a prefix of the range.
   const unsigned long long t_start = a.budget_ns ? globaltimer_ns() : 0ull;
-  int cell = next_cell(a, t_start, lane);
+  const int wpb = (int)(blockDim.x >> 5);
+  const int gw = (int)blockIdx.x * wpb + warp, nw = (int)gridDim.x * wpb;   // static schedule only
+  int taken = 0;
+  int cell = next_cell(a, t_start, gw, nw, taken, lane);
   for (; cell < a.ncell; ) {
     double* yc = a.y + (size_t)cell * n;
     const double p = a.p[cell];
@@ -1134,7 +1151,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
             njac++;
             fresh = true;
           }
-          newton_solve<PREC32>(w, n, lane);
+          newton_solve<PREC32>(w, n, lane, a.lu_variant);
           float nrm = wrms_update(w.d, w.Z, n, a.rtol, a.atol_Y, a.atol_T, lane);
           // redo with a fresh matrix when the stale one contracts by less than 10x, or
           // when its contraction rate would not reach the tolerance three iterations
@@ -1153,7 +1170,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
             M_age = 0;
             for (int k = lane; k < n; k += 32) w.d[k] = w.res[k];
             __syncwarp();
-            newton_solve<PREC32>(w, n, lane);
+            newton_solve<PREC32>(w, n, lane, a.lu_variant);
             nrm = wrms_update(w.d, w.Z, n, a.rtol, a.atol_Y, a.atol_T, lane);
           }
           for (int k = lane; k < n; k += 32) w.Z[k] += w.d[k];
@@ -1261,7 +1278,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
       if (a.n_failed && status != MRI_CELL_OK) atomicAdd(a.n_failed, 1);
     }
     __syncwarp();
-    cell = next_cell(a, t_start, lane);
+    cell = next_cell(a, t_start, gw, nw, taken, lane);
   }
 }
 
@@ -1517,6 +1534,8 @@ static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, 
   a.ws_stride = ws_offsets(m.L, o.precision == MRI_PREC_FP32_LU, K).total;
   a.budget_ns = o.time_budget_s > 0 ? (unsigned long long)std::ceil(o.time_budget_s * 1e9) : 0ull;
   a.adaptive = o.adaptive;
+  a.schedule = o.schedule;
+  a.lu_variant = o.lu_variant;
   a.ctrl_rtol = o.ctrl_rtol; a.ctrl_atol_Y = o.ctrl_atol_Y; a.ctrl_atol_T = o.ctrl_atol_T;
   if (o.adaptive) a.ramp = 0;   // the controller finds its own start-up steps
   if (o.matrix_cache) {
@@ -1672,7 +1691,9 @@ bool fast_opts_ok(const mri_fast_opts* o) {
          (o->adaptive == 0 || (o->ctrl_rtol > 0 && std::isfinite(o->ctrl_rtol) && o->ctrl_atol_Y >= 0 &&
                                o->ctrl_atol_T >= 0 && std::isfinite(o->ctrl_atol_Y) &&
                                std::isfinite(o->ctrl_atol_T))) &&
-         o->newton_safety > 0 && o->newton_safety <= 1.0;
+         o->newton_safety > 0 && o->newton_safety <= 1.0 &&
+         (o->schedule == MRI_SCHED_QUEUE || (o->schedule == MRI_SCHED_STATIC && o->time_budget_s == 0.0)) &&
+         o->lu_variant >= MRI_LU_AUTO && o->lu_variant <= MRI_LU_SHARED;
 }
 
 int mech_device_check(const Mech& m) {
@@ -1716,6 +1737,8 @@ extern "C" void mri_fast_opts_default(mri_fast_opts* o) {
   o->ctrl_atol_Y = 1e-12;
   o->ctrl_atol_T = 1e-6;
   o->newton_safety = 3e-4;
+  o->schedule = MRI_SCHED_QUEUE;
+  o->lu_variant = MRI_LU_AUTO;
 }
 
 extern "C" size_t mri_matrix_cache_size(const mri_mech* mech, int ncell, int precision) {
@@ -1758,7 +1781,8 @@ extern "C" int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, 
                                     const mri_fast_opts* opts, int32_t* n_failed, void* stream) {
   (void)t0;
   if (!groups || ngroups < 1 || ngroups > MRI_MAX_GROUPS || !mri::fast_opts_ok(opts)) return MRI_EINVAL;
-  if (opts->warps_per_block != 0 || opts->blocks_per_sm > 1 || opts->time_budget_s != 0.0 || opts->matrix_cache)
+  if (opts->warps_per_block != 0 || opts->blocks_per_sm > 1 || opts->time_budget_s != 0.0 || opts->matrix_cache ||
+      opts->schedule != MRI_SCHED_QUEUE)
     return MRI_EINVAL;
   if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
   for (int g = 0; g < ngroups; ++g) {

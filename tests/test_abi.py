@@ -52,6 +52,7 @@ def test_defaults_and_status_strings(lib):
     assert (o.matrix_cache, o.matrix_cache_bytes) == (None, 0)
     assert (o.adaptive, o.ctrl_rtol, o.ctrl_atol_Y, o.ctrl_atol_T) == (0, 1e-6, 1e-12, 1e-6)
     assert o.newton_safety == 3e-4
+    assert (o.schedule, o.lu_variant) == (lib.MRI_SCHED_QUEUE, lib.MRI_LU_AUTO)
     assert lib.mri_status_str(0) == "ok"
     assert "Newton" in lib.mri_status_str(-2)
 
@@ -87,7 +88,8 @@ def test_stage_argument_validation_on_host(lib):
                dict(warps_per_block=17), dict(warps_per_block=-1), dict(blocks_per_sm=9),
                dict(time_budget_s=-1.0), dict(time_budget_s=float("nan")), dict(adaptive=2),
                dict(adaptive=1, ctrl_rtol=0.0), dict(adaptive=1, ctrl_atol_T=-1.0), dict(newton_safety=0.0),
-               dict(newton_safety=1.5), dict(newton_safety=float("nan"))):
+               dict(newton_safety=1.5), dict(newton_safety=float("nan")), dict(schedule=2),
+               dict(schedule=1, time_budget_s=1.0), dict(lu_variant=4), dict(lu_variant=-1)):
         bad = lib.mri_fast_opts_default(**kw)
         assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, fake, ct.byref(bad), None, None, None,
                                 None) == lib.MRI_EINVAL
@@ -97,7 +99,7 @@ def test_stage_argument_validation_on_host(lib):
     assert L.mri_stage_fast_batch(grp, 0, 0.0, 1e-8, 1e-9, ct.byref(o), None, None) == lib.MRI_EINVAL
     assert L.mri_stage_fast_batch(grp, 9, 0.0, 1e-8, 1e-9, ct.byref(o), None, None) == lib.MRI_EINVAL
     for kw in (dict(warps_per_block=2), dict(blocks_per_sm=2), dict(time_budget_s=1.0),
-               dict(matrix_cache=0x1000, matrix_cache_bytes=1 << 20)):
+               dict(matrix_cache=0x1000, matrix_cache_bytes=1 << 20), dict(schedule=1)):
         bad = lib.mri_fast_opts_default(**kw)
         assert L.mri_stage_fast_batch(grp, 1, 0.0, 1e-8, 1e-9, ct.byref(bad), None, None) == lib.MRI_EINVAL
     # a whole MRI step takes no time budget

@@ -63,4 +63,25 @@ def test_adaptive_full_size_first_stage_sampled(mri, orc):
     same = ss[idx, 0] == rss[:, 0]
     assert same.mean() >= 0.9, (ss[idx, 0], rss[:, 0])
     assert_parity(got[idx][same], ref[same], what="adaptive 32^3 first stage (sampled)")
-    print("accepted steps per cell: min", ss[:, 0].min(), "median", np.median(ss[:, 0]), "max", ss[:, 0].max())
+    # every sampled cell, including those whose controller took another path (an estimate
+    # within rounding of a threshold), against a solution 100 times tighter, within the
+    # controller's tolerance
+    check_against_tight_solution(orc, w, got[idx], w.y0[idx], w.p[idx], phi[idx], w.H / 3, 1e-6)
+    print("accepted steps per cell: min", ss[:, 0].min(), "median", np.median(ss[:, 0]), "max", ss[:, 0].max(),
+          "; cells on another step sequence:", int((~same).sum()), "of", len(idx))
+
+
+def check_against_tight_solution(orc, w, got, y, p, phi, Hs, tol, factor=10.0, **kw):
+    """Results of cells whose accepted-step sequence differs from the oracle's, against
+    the oracle's adaptive solution at a 100 times tighter controller tolerance: the error
+    in the controller's own weights (rtol |y| + atol) must stay within factor times its
+    tolerance."""
+    if got.shape[0] == 0:
+        return
+    tight, st, _ = orc.Mech(w.mech).stage_fast(y, p, phi, Hs, w.h, orc.opts(method=3, rtol=1e-12,
+                                                                               **ctrl(tol / 100.0)), **kw)
+    assert np.all(st == 0)
+    atol = np.full(got.shape[1], tol * 1e-6)
+    atol[-1] = tol
+    err = np.abs(got - tight) / (tol * np.abs(tight) + atol)
+    assert err.max() <= factor, err.max()

@@ -41,9 +41,13 @@ def test_launch_shape_does_not_change_results(mri, prec):
     phi = mechgen.random_forcing(2, y.shape[0], w.mech.n, 1)
     gm = mri.mri_mech_load(w.mech.to_blob())
     runs = []
-    for wpb, bps in [(0, 0), (1, 0), (3, 0), (0, 2), (2, 2), (1, 3)]:
-        o = mri.mri_fast_opts_default(method=3, ramp=w.ramp, jac_policy=1, precision=prec, warps_per_block=wpb,
-                                      blocks_per_sm=bps)
+    shapes = [dict(warps_per_block=wpb, blocks_per_sm=bps) for wpb, bps in
+              [(0, 0), (1, 0), (3, 0), (0, 2), (2, 2), (1, 3)]]
+    # the solve layouts and the static schedule change the cost only, never a bit of the result
+    shapes += [dict(lu_variant=v) for v in (mri.MRI_LU_REGS, mri.MRI_LU_REGS_SPLIT, mri.MRI_LU_SHARED)]
+    shapes += [dict(schedule=mri.MRI_SCHED_STATIC), dict(schedule=mri.MRI_SCHED_STATIC, warps_per_block=2)]
+    for kw in shapes:
+        o = mri.mri_fast_opts_default(method=3, ramp=w.ramp, jac_policy=1, precision=prec, **kw)
         runs.append(host(*launch(mri, gm, y, p, phi, w.H / 3, w.h, o)[:3]))
     for r in runs[1:]:
         for a, b in zip(runs[0], r):
@@ -70,8 +74,10 @@ def test_autotuner_picks_a_timed_shape_with_the_same_result(mri):
     cands = candidate_shapes(gm, o, y.shape[0], 0)
     assert (mri.mri_stage_fast_shape(gm, o, 1 << 30, 0)[0], 1) in cands
     best, table = autotune_stage(gm, yd, pd, None, w.H / 5, w.h, o, repeats=1)
-    assert len(table) == len(cands) and all(ms > 0 for _, _, ms in table)
-    assert (best.warps_per_block, best.blocks_per_sm) == min(table, key=lambda r: r[2])[:2]
+    # every launch shape, then the three solve layouts at the best shape, then the static schedule
+    assert len(table) == len(cands) + 3 + 1 and all(r[-1] > 0 for r in table)
+    fastest = min(table, key=lambda r: r[-1])
+    assert (best.warps_per_block, best.blocks_per_sm, best.lu_variant, best.schedule) == fastest[:4]
     np.testing.assert_array_equal(yd.cpu().numpy(), y)          # the tuner worked on copies
     a = host(launch(mri, gm, y, p, None, w.H / 5, w.h, o)[0])[0]
     b = host(launch(mri, gm, y, p, None, w.H / 5, w.h, best)[0])[0]

@@ -78,3 +78,9 @@ def test_step_predictor_saves_attempts_and_keeps_parity(mri, orc):
     same = ss_k[idx, 0] == rss[:, 0]
     assert same.mean() >= 0.9, (ss_k[idx, 0], rss[:, 0])
     assert_parity(out_k.cpu().numpy()[idx][same], ref[same], what="predicted first steps vs oracle")
+    # every sampled cell, those on another step sequence included, against a 100 times
+    # tighter oracle solution, within the controller's tolerance
+    from test_gpu_adaptive import check_against_tight_solution
+    yi, pi, phii = y.cpu().numpy()[idx], p.cpu().numpy()[idx], phi.cpu().numpy()[idx]
+    check_against_tight_solution(orc, w, out_k.cpu().numpy()[idx], yi, pi, phii, Hs, ctrl["ctrl_rtol"],
+                                 step_exp=kk[idx])

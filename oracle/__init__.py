@@ -54,6 +54,9 @@ def lib():
         L.orc_lu_solve.argtypes = [ct.c_int, _dp, _ip, _dp]
         L.orc_sdirk_tableau.argtypes = [ct.c_int, _dp, _dp, _dp, _ip]
         L.orc_mri_tableau.argtypes = [_dp, _dp, _ip]
+        L.orc_erk_tableau.argtypes = [ct.c_int, _dp, _dp, _dp, _ip]
+        L.orc_erk_scalar.argtypes = [ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_double, ct.c_int,
+                                     ct.c_double, _dp]
         L.orc_mri_coupling.argtypes = [_dp, _ip]
         L.orc_stage_fast.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, _dp, ct.c_int, ct.c_double, ct.c_double,
                                      ct.POINTER(Opts), _ip, _ip, ct.c_int]
@@ -220,6 +223,21 @@ def sdirk_embedded(method):
     bhat, q = np.zeros(3), ct.c_int32()
     assert lib().orc_sdirk_embedded(method, _d(bhat), ct.byref(q)) == 0
     return bhat[:method], q.value
+
+
+def erk_tableau(method):
+    """(A, b, c) of the explicit fast method 12 (Heun), 13 (Kutta 3) or 14 (RK4)."""
+    A, b, c, s = np.zeros(16), np.zeros(4), np.zeros(4), ct.c_int32()
+    assert lib().orc_erk_tableau(method, _d(A), _d(b), _d(c), ct.byref(s)) == 0
+    s = s.value
+    return A[: s * s].reshape(s, s), b[:s], c[:s]
+
+
+def erk_scalar(method, problem, lam, t0, t1, nsteps, y0):
+    out = np.zeros(1)
+    if lib().orc_erk_scalar(method, problem, lam, t0, t1, nsteps, y0, _d(out)) != 0:
+        raise RuntimeError("explicit scalar integration failed")
+    return out[0]
 
 
 def mri_tableau():

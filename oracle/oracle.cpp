@@ -413,6 +413,47 @@ Tableau sdirk(int method) {
   return t;
 }
 
+// ---------------------------------------------------------------- explicit fast methods
+// The paper's explicit fast integrators (Sec. 3.2, the MRI-P(k) family) are classical
+// explicit Runge-Kutta methods; three of them from their textbook definitions:
+//   Heun (order 2):   c = (0, 1),           a21 = 1,                      b = (1/2, 1/2)
+//   Kutta (order 3):  c = (0, 1/2, 1),      a21 = 1/2, a31 = -1, a32 = 2,  b = (1/6, 2/3, 1/6)
+//   classical RK4:    c = (0, 1/2, 1/2, 1), a21 = a32 = 1/2, a43 = 1,      b = (1/6, 1/3, 1/3, 1/6)
+// Method codes 12, 13, 14 (order + 10).
+
+struct ErkTab {
+  int s = 0;
+  double A[4][4] = {};
+  double b[4] = {};
+  double c[4] = {};
+};
+
+bool is_erk(int method) { return method == 12 || method == 13 || method == 14; }
+
+ErkTab erk(int method) {
+  ErkTab t;
+  if (method == 12) {
+    t.s = 2;
+    t.A[1][0] = 1.0;
+    t.b[0] = 0.5; t.b[1] = 0.5;
+    t.c[1] = 1.0;
+  } else if (method == 13) {
+    t.s = 3;
+    t.A[1][0] = 0.5;
+    t.A[2][0] = -1.0; t.A[2][1] = 2.0;
+    t.b[0] = 1.0 / 6.0; t.b[1] = 2.0 / 3.0; t.b[2] = 1.0 / 6.0;
+    t.c[1] = 0.5; t.c[2] = 1.0;
+  } else if (method == 14) {
+    t.s = 4;
+    t.A[1][0] = 0.5;
+    t.A[2][1] = 0.5;
+    t.A[3][2] = 1.0;
+    t.b[0] = 1.0 / 6.0; t.b[1] = 1.0 / 3.0; t.b[2] = 1.0 / 3.0; t.b[3] = 1.0 / 6.0;
+    t.c[1] = 0.5; t.c[2] = 0.5; t.c[3] = 1.0;
+  }
+  return t;
+}
+
 // ---------------------------------------------------------------- generic stiff step
 
 struct Problem {   // one independent unit of a fast IVP (a cell)
@@ -501,6 +542,39 @@ int sdirk_step(const Problem& P, const Tableau& tab, double t, double h, double*
   return 0;
 }
 
+// One explicit Runge-Kutta substep from (t, y) of size h for v' = rhs(t, v) + r(theta):
+// K_i = rhs(t + c_i h, Y_i) + r(rhohat_i), Y_i = y + h sum_{j<i} a_ij K_j, with rhohat_i
+// = (tau + c_i h)/Hs as in sdirk_step; y <- y + h sum_i b_i K_i.  Counts the right-hand-
+// side evaluations in st.newton.  Returns 1 when the new state is not finite.
+int erk_step(const Problem& P, const ErkTab& tab, double t, double h, double* y, const Forcing& fo, double tau,
+             double Hs, StepStats& st) {
+  const int n = P.n;
+  std::vector<double> K((size_t)tab.s * n), Y(n);
+  for (int i = 0; i < tab.s; ++i) {
+    for (int q = 0; q < n; ++q) {
+      Y[q] = y[q];
+      for (int j = 0; j < i; ++j) Y[q] += h * tab.A[i][j] * K[(size_t)j * n + q];
+    }
+    double* Ki = &K[(size_t)i * n];
+    P.rhs(t + tab.c[i] * h, Y.data(), Ki);
+    st.newton++;
+    const double rh = (tau + tab.c[i] * h) / Hs;
+    double pw = 1.0;
+    for (int k = 0; k < fo.K; ++k) {
+      for (int q = 0; q < n; ++q) Ki[q] += pw * fo.phi[(size_t)k * n + q];
+      pw *= rh;
+    }
+  }
+  bool finite = true;
+  for (int q = 0; q < n; ++q) {
+    double inc = 0.0;
+    for (int i = 0; i < tab.s; ++i) inc += tab.b[i] * K[(size_t)i * n + q];
+    y[q] += h * inc;
+    finite = finite && std::isfinite(y[q]);
+  }
+  return finite ? 0 : 1;
+}
+
 // Step-size factor of the adaptive controller: the largest of 4, 2, 1, 1/2 not above
 // 0.9 err^(-1/q), else 1/4.  Powers of two keep every substep size and offset a
 // dyadic multiple of the initial substep.
@@ -552,9 +626,13 @@ int fast_stage_unit(const Problem& P, const Tableau& tab, double t0, double Hs, 
   }
   StepStats st;
   int status = 0, done = 0;
+  const bool explicit_rk = is_erk(o.method);
+  const ErkTab et = explicit_rk ? erk(o.method) : ErkTab();
   for (size_t s = 0; s < hs.size(); ++s) {
     std::vector<double> save(y, y + P.n);
-    if (sdirk_step(P, tab, t0 + tau[s], hs[s], y, fo, tau[s], Hs, o, st) != 0) {
+    const int rc = explicit_rk ? erk_step(P, et, t0 + tau[s], hs[s], y, fo, tau[s], Hs, st)
+                               : sdirk_step(P, tab, t0 + tau[s], hs[s], y, fo, tau[s], Hs, o, st);
+    if (rc != 0) {
       std::copy(save.begin(), save.end(), y);
       status = 1;
       break;
@@ -933,6 +1011,32 @@ int orc_sdirk_embedded(int method, double* bhat, int* q) {
   return 0;
 }
 
+int orc_erk_tableau(int method, double* A, double* b, double* c, int* s) {
+  if (!is_erk(method)) return -1;
+  ErkTab t = erk(method);
+  *s = t.s;
+  for (int i = 0; i < t.s; ++i) {
+    c[i] = t.c[i];
+    b[i] = t.b[i];
+    for (int j = 0; j < t.s; ++j) A[i * t.s + j] = t.A[i][j];
+  }
+  return 0;
+}
+
+int orc_erk_scalar(int method, int problem, double lam, double t0, double t1, int nsteps, double y0,
+                   double* y_out) {
+  if (!is_erk(method) || nsteps < 1) return -1;
+  Scalar P(problem, lam);
+  ErkTab tab = erk(method);
+  double y = y0, hh = (t1 - t0) / nsteps;
+  StepStats st;
+  Forcing none;
+  for (int s = 0; s < nsteps; ++s)
+    if (erk_step(P, tab, t0 + s * hh, hh, &y, none, s * hh, t1 - t0, st) != 0) return 1;
+  *y_out = y;
+  return 0;
+}
+
 int orc_mri_tableau(double* A, double* c, int* s) {
   MriTab t = kw3();
   *s = t.s;
@@ -955,7 +1059,7 @@ int orc_mri_coupling(double* G, int* s) {
 int orc_stage_fast(const void* mech, double* y, const double* p, int ncell, const double* phi, int K,
                    double Hs, double h, const orc_opts* o, int32_t* status, int32_t* stats, int nthreads) {
   if (!mech || !o || ncell < 0 || K < 0 || !(Hs > 0) || !(h > 0)) return -1;
-  if (o->method != 2 && o->method != 3) return -1;
+  if (o->method != 2 && o->method != 3 && !(is_erk(o->method) && !o->adaptive)) return -1;
   return stage_fast(*static_cast<const Mech*>(mech), y, p, ncell, phi, K, Hs, h, *o, status, stats, nthreads);
 }
 
@@ -963,7 +1067,7 @@ int orc_stage_fast_exp(const void* mech, double* y, const double* p, int ncell, 
                        double Hs, double h, const orc_opts* o, const int8_t* step_exp, int32_t* status,
                        int32_t* stats, int nthreads) {
   if (!mech || !o || ncell < 0 || K < 0 || !(Hs > 0) || !(h > 0)) return -1;
-  if (o->method != 2 && o->method != 3) return -1;
+  if (o->method != 2 && o->method != 3 && !(is_erk(o->method) && !o->adaptive)) return -1;
   return stage_fast(*static_cast<const Mech*>(mech), y, p, ncell, phi, K, Hs, h, *o, status, stats, nthreads,
                     step_exp);
 }
@@ -1010,7 +1114,7 @@ int orc_sdirk_scalar(int method, int problem, double lam, double t0, double t1, 
 
 int orc_kpr_mri(int fast_method, double G, double e, double beta, double omega, double t1, int nsteps,
                 int m_fast, double* err, double* y_out) {
-  if ((fast_method != 2 && fast_method != 3) || nsteps < 1 || m_fast < 1) return -1;
+  if ((fast_method != 2 && fast_method != 3 && !is_erk(fast_method)) || nsteps < 1 || m_fast < 1) return -1;
   KPR k{G, e, beta, omega};
   KPRFast P(k);
   Tableau tab = sdirk(fast_method);

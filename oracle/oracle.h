@@ -20,6 +20,9 @@
  *     standard Chemkin definitions (Arrhenius, third body, Lindemann-Troe
  *     falloff, equilibrium constants from NASA-7 Gibbs polynomials), which the
  *     paper names but does not print;
+ *   - explicit fast integrators (Sec. 3.2, the MRI-P(k) methods): Heun's second-
+ *     order, Kutta's third-order and the classical fourth-order Runge-Kutta method,
+ *     fixed substeps, no Jacobian;
  *   - fast integrator: L-stable SDIRK2 / SDIRK3 (Alexander 1977) with full
  *     Newton (fresh analytic Jacobian and LU with partial pivoting every
  *     iteration), fixed substeps n_i = ceil(dc_i H / h), optionally a geometric
@@ -41,7 +44,8 @@ extern "C" {
 #endif
 
 typedef struct {
-  int method;          /* 2 = SDIRK2, 3 = SDIRK3 */
+  int method;          /* 2 = SDIRK2, 3 = SDIRK3; explicit (fixed substeps only): 12 = Heun,
+                          13 = Kutta's third-order method, 14 = classical RK4 */
   double rtol;         /* Newton WRMS relative tolerance */
   double atol_Y;       /* absolute tolerance, mass fractions */
   double atol_T;       /* absolute tolerance, temperature [K] */
@@ -81,6 +85,11 @@ int orc_sdirk_tableau(int method, double* A, double* b, double* c, int* s);
 /* embedded weights of the adaptive error estimate (one order lower than the method)
    and the estimate's order q (the controller scales steps by err^(-1/q)) */
 int orc_sdirk_embedded(int method, double* bhat, int* q);
+/* explicit Runge-Kutta tableau of method 12, 13 or 14 (A row-major s x s) */
+int orc_erk_tableau(int method, double* A, double* b, double* c, int* s);
+/* the explicit methods on the scalar test problems of orc_sdirk_scalar */
+int orc_erk_scalar(int method, int problem, double lam, double t0, double t1, int nsteps, double y0,
+                   double* y_out);
 int orc_mri_tableau(double* A, double* c, int* s);
 /* coupling coefficients of the MIS form: G[i*s + j] multiplies f^S(Y_j) in the
    constant forcing of stage i (i = 1..s-1, zero-based) */
@@ -106,8 +115,8 @@ int orc_single_rate(const void* mech, double* y, const double* p, const orc_grid
    y' = lam*(y - cos t) - sin t */
 int orc_sdirk_scalar(int method, int problem, double lam, double t0, double t1, int nsteps, double y0,
                      double* y_out);
-/* KPR multirate problem, MIS/KW3 slow + SDIRK fast with m substeps per unit
-   of slow step: returns max-norm error at t1 */
+/* KPR multirate problem, MIS/KW3 slow + SDIRK or explicit fast method (fast_method
+   2, 3, 12, 13, 14) with m substeps per unit of slow step: returns max-norm error at t1 */
 int orc_kpr_mri(int fast_method, double G, double e, double beta, double omega, double t1, int nsteps,
                 int m_fast, double* err, double* y_out);
 

@@ -67,6 +67,17 @@ extern "C" {
 /* ---- fast integrators ------------------------------------------------ */
 #define MRI_SDIRK2 2       /* Alexander (1977) 2-stage, order 2, L-stable, stiffly accurate */
 #define MRI_SDIRK3 3       /* Alexander (1977) 3-stage, order 3, L-stable, stiffly accurate */
+/* The paper's explicit fast methods (Sec. 3.2, the MRI-P(k) runs use explicit Runge-Kutta
+ * fast integrators): fixed substeps only (no adaptive option), no Jacobian and no Newton
+ * iteration, so the Newton, precision, solve-layout and matrix-cache options are ignored;
+ * stable only where h times the chemistry's largest eigenvalue is small (a cell whose
+ * state becomes non-finite stops with MRI_CELL_ENEWTON at the state before that substep).
+ * cell_stats[1] counts right-hand-side evaluations, cell_stats[2] stays 0.
+ * mri_stage_fast_guided and mri_stage_fast_batch reject them. */
+#define MRI_ERK2 12        /* Heun's method: c = (0, 1), a21 = 1, b = (1/2, 1/2) */
+#define MRI_ERK3 13        /* Kutta's third-order method: c = (0, 1/2, 1), a21 = 1/2,
+                              a31 = -1, a32 = 2, b = (1/6, 2/3, 1/6) */
+#define MRI_ERK4 14        /* classical fourth-order Runge-Kutta method */
 
 /* ---- slow (MRI) methods ---------------------------------------------- */
 #define MRI_KW3 1          /* explicit third-order method of Knoth & Wolke (1998) in
@@ -109,7 +120,7 @@ int mri_mech_info(const mri_mech* mech, int* n_species, int* n_reactions);
                                  stage values meet the same tolerance as the FP64 form. */
 
 typedef struct {
-  int method;            /* MRI_SDIRK2 or MRI_SDIRK3 */
+  int method;            /* MRI_SDIRK2, MRI_SDIRK3 or an explicit MRI_ERK2/3/4 */
   double newton_rtol;    /* WRMS weights w_k = rtol |Z_k| + atol_k; converged when WRMS(delta) <= 1 */
   double newton_atol_Y;  /* absolute tolerance of the mass fractions */
   double newton_atol_T;  /* absolute tolerance of T [K] */

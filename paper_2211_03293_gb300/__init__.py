@@ -25,6 +25,7 @@ _lib = ct.CDLL(LIB_PATH)
 MRI_OK, MRI_EINVAL, MRI_ENEWTON, MRI_ECUDA, MRI_ETIMEOUT, MRI_ENOMEM, MRI_ECONV = 0, -1, -2, -3, -4, -5, -6
 MRI_CELL_OK, MRI_CELL_ENEWTON, MRI_CELL_EINPUT, MRI_CELL_TIMEOUT = 0, 1, 2, 3
 MRI_SDIRK2, MRI_SDIRK3 = 2, 3
+MRI_ERK2, MRI_ERK3, MRI_ERK4 = 12, 13, 14
 MRI_KW3 = 1
 MRI_JAC_PER_SUBSTEP = 0
 MRI_JAC_LAZY = 1

@@ -79,8 +79,8 @@ struct WS {
   float *M32, *dinv32, *d32, *C32, *hh32, *cp32, *wd32, *DT32, *DC32, *aux32, *tbk32, *kfw32, *krw32, *tbs32;
   int ld, nv;
   __device__ __forceinline__ double* F(int j) const { return j == 0 ? F0 : F1; }
-  __device__ WS(double* base, const Layout& L, bool prec32, int K) {
-    WsOffsets o = ws_offsets(L, prec32, K);
+  __device__ WS(double* base, const Layout& L, bool prec32, int K, bool matrix = true) {
+    WsOffsets o = ws_offsets(L, prec32, K, matrix);
     M = base + o.M; y0 = base + o.y0; Z = base + o.Z; d = base + o.d;
     F0 = base + o.F0; F1 = base + o.F1; Fl = base + o.Fl; r = base + o.r; f = base + o.f; phi = base + o.phi;
     this->base = base + o.base;
@@ -1296,6 +1296,109 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) stage_fast_kernel(StageArgs
   stage_cells<PREC32>(a, smem, sA, sc, threadIdx.x >> 5, threadIdx.x & 31);
 }
 
+// Tableau of an explicit fast method (Sec. 3.2: the paper's MRI-P(k) runs use explicit
+// Runge-Kutta fast methods): K_i = F(tau + c_i h, y + h sum_{j<i} a_ij K_j),
+// y <- y + h sum_i b_i K_i, s <= 4 stages.
+struct ErkArgs {
+  double A[4][4], b[4], c[4];
+  int s;
+};
+
+// The cells of one stage launch with an explicit fast method, for one warp: n_sub
+// substeps (plus the start-up sequence), each with s evaluations of f^F + r(theta) and
+// the weighted update; no Jacobian, no Newton iteration.  A substep whose new state is
+// not finite leaves the cell at the state before it with MRI_CELL_ENEWTON.
+// cell_stats[1] counts right-hand-side evaluations.
+__device__ __forceinline__ void stage_cells_explicit(const StageArgs& a, const ErkArgs& e, unsigned char* smem,
+                                                     int warp, int lane) {
+  const Tab t(smem, a.L);
+  const WS w(reinterpret_cast<double*>(smem + a.L.bytes) + (size_t)warp * a.ws_stride, a.L, false, a.K, false);
+  const int n = t.n, Ns = t.Ns, S = e.s;
+  const int total_sub = a.n_sub + (a.ramp > 0 ? a.ramp : 0);
+  const int wpb = (int)(blockDim.x >> 5);
+  const int gw = (int)blockIdx.x * wpb + warp, nw = (int)gridDim.x * wpb;
+  int taken = 0;
+  const unsigned long long t_start = a.budget_ns ? globaltimer_ns() : 0ull;
+  int cell = next_cell(a, t_start, gw, nw, taken, lane);
+  for (; cell < a.ncell; ) {
+    double* yc = a.y + (size_t)cell * n;
+    const double p = a.p[cell];
+    int bad = 0;
+    for (int k = lane; k < n; k += 32) {
+      const double v = yc[k];
+      w.y0[k] = v;
+      if (!isfinite(v)) bad = 1;
+    }
+    for (int q = lane; q < a.K * n; q += 32) w.phi[(q / n) * w.nv + (q % n)] = a.phi[(size_t)cell * a.K * n + q];
+    __syncwarp();
+    bad = __any_sync(0xffffffffu, bad) || !(w.y0[Ns] > 0.0) || !(p > 0.0) || !isfinite(p);
+    int status = bad ? MRI_CELL_EINPUT : MRI_CELL_OK;
+    int nsub = 0, nrhs = 0;
+    for (int sidx = 0; sidx < total_sub && status == MRI_CELL_OK; ++sidx) {
+      double tau, hk;
+      substep_geometry(sidx, a.ramp, a.hh, tau, hk);
+      for (int i = 0; i < S; ++i) {
+        const double rh = (tau + e.c[i] * hk) / a.Hs;
+        for (int k = lane; k < n; k += 32) {
+          double z = w.y0[k];
+          for (int j = 0; j < i; ++j) {
+            const double* Kj = (j == 0) ? w.F0 : (j == 1) ? w.F1 : w.Fl;
+            z = fma(hk * e.A[i][j], Kj[k], z);
+          }
+          w.Z[k] = z;
+          double rv = 0.0;
+          for (int q = a.K - 1; q >= 0; --q) rv = fma(rv, rh, w.phi[q * w.nv + k]);
+          w.r[k] = rv;
+        }
+        __syncwarp();
+        Scal sc;
+        chem_eval<false>(t, w, w.Z, p, sc, lane);
+        chem_rhs_out(t, w, sc, w.f, lane);
+        double* Ki = (i == 0) ? w.F0 : (i == 1) ? w.F1 : w.Fl;   // K_3 is only summed
+        for (int k = lane; k < n; k += 32) {
+          const double kv = w.f[k] + w.r[k];
+          if (i < S - 1) Ki[k] = kv;
+          w.res[k] = (i == 0) ? e.b[0] * kv : fma(e.b[i], kv, w.res[k]);
+        }
+        __syncwarp();
+        ++nrhs;
+      }
+      int fin = 1;
+      for (int k = lane; k < n; k += 32) {
+        const double v = fma(hk, w.res[k], w.y0[k]);
+        w.Z[k] = v;
+        if (!isfinite(v)) fin = 0;
+      }
+      if (!__all_sync(0xffffffffu, fin)) {
+        status = MRI_CELL_ENEWTON;     // the cell keeps the state before this substep
+        break;
+      }
+      for (int k = lane; k < n; k += 32) w.y0[k] = w.Z[k];
+      __syncwarp();
+      ++nsub;
+    }
+    if (status != MRI_CELL_EINPUT)
+      for (int k = lane; k < n; k += 32) yc[k] = w.y0[k];
+    if (lane == 0) {
+      if (a.status && (!a.sticky || status != MRI_CELL_OK)) a.status[cell] = status;
+      if (a.stats) {
+        int32_t* st = a.stats + 4 * (size_t)cell;
+        st[0] += nsub; st[1] += nrhs; st[3] += (status != MRI_CELL_OK);
+      }
+      if (a.n_failed && status != MRI_CELL_OK) atomicAdd(a.n_failed, 1);
+    }
+    __syncwarp();
+    cell = next_cell(a, t_start, gw, nw, taken, lane);
+  }
+}
+
+__global__ void __launch_bounds__(kMaxWarps * 32, 1) stage_explicit_kernel(StageArgs a, ErkArgs e) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  stage_table(smem, a.table, a.L.bytes);
+  __syncthreads();
+  stage_cells_explicit(a, e, smem, threadIdx.x >> 5, threadIdx.x & 31);
+}
+
 // Several mechanisms in one launch: CTAs [block0[g], block0[g+1]) serve group g, each
 // with its own staged tables, workspace layout and queue.  The group's arguments are
 // copied to shared memory so that the hot loop reads them from there.
@@ -1447,14 +1550,14 @@ static int device_sm_smem() {
 // after the staged table.  wpb / bps: requested warps per CTA and CTAs per SM (0 =
 // automatic).  The grid is persistent: at most bps CTAs per SM.
 static bool plan_launch(const Layout& L, int ncell, int& warps, int& blocks, size_t& smem, bool prec32 = false,
-                        int K = 0, int wpb = 0, int bps = 0) {
+                        int K = 0, int wpb = 0, int bps = 0, bool matrix = true) {
   constexpr long long kStaticSmem = 1024;    // the kernels' static shared arrays (tableau, batch arguments)
   constexpr long long kReservedPerCta = 1024;   // shared memory the SM keeps per resident CTA
   const int per_cta_sm = bps > 0 ? bps : 1;
   long long cap = device_smem_limit();
   const long long share = (long long)device_sm_smem() / per_cta_sm - kReservedPerCta;
   if (share < cap) cap = share;
-  const size_t per_warp = (size_t)ws_offsets(L, prec32, K).total * 8;
+  const size_t per_warp = (size_t)ws_offsets(L, prec32, K, matrix).total * 8;
   long long room = cap - kStaticSmem - (long long)L.bytes;
   int wmax = room > 0 ? (int)(room / (long long)per_warp) : 0;
   if (wmax > kMaxWarps) wmax = kMaxWarps;
@@ -1508,6 +1611,31 @@ static void sdirk_table(int method, StageArgs& a) {
   }
 }
 
+bool is_explicit(int method) { return method == MRI_ERK2 || method == MRI_ERK3 || method == MRI_ERK4; }
+
+// Heun (order 2), Kutta's third-order method and the classical fourth-order method.
+static ErkArgs erk_table(int method) {
+  ErkArgs e{};
+  if (method == MRI_ERK2) {
+    e.s = 2;
+    e.A[1][0] = 1.0;
+    e.b[0] = 0.5; e.b[1] = 0.5;
+    e.c[1] = 1.0;
+  } else if (method == MRI_ERK3) {
+    e.s = 3;
+    e.A[1][0] = 0.5;
+    e.A[2][0] = -1.0; e.A[2][1] = 2.0;
+    e.b[0] = 1.0 / 6.0; e.b[1] = 2.0 / 3.0; e.b[2] = 1.0 / 6.0;
+    e.c[1] = 0.5; e.c[2] = 1.0;
+  } else {
+    e.s = 4;
+    e.A[1][0] = 0.5; e.A[2][1] = 0.5; e.A[3][2] = 1.0;
+    e.b[0] = 1.0 / 6.0; e.b[1] = 1.0 / 3.0; e.b[2] = 1.0 / 3.0; e.b[3] = 1.0 / 6.0;
+    e.c[1] = 0.5; e.c[2] = 0.5; e.c[3] = 1.0;
+  }
+  return e;
+}
+
 // Arguments of one stage launch over the cells of one mechanism.
 static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, const double* phi, int K,
                            double Hs, double h, const Mech& m, const mri_fast_opts& o, int ramp, int32_t* status,
@@ -1530,8 +1658,9 @@ static int fill_stage_args(StageArgs& a, double* y, const double* p, int ncell, 
   a.jac_policy = o.jac_policy;
   a.rtol = o.newton_rtol; a.atol_Y = o.newton_atol_Y; a.atol_T = o.newton_atol_T;
   a.newton_safety_f = (float)o.newton_safety;
-  sdirk_table(o.method, a);
-  a.ws_stride = ws_offsets(m.L, o.precision == MRI_PREC_FP32_LU, K).total;
+  if (!is_explicit(o.method)) sdirk_table(o.method, a);
+  a.ws_stride = is_explicit(o.method) ? ws_offsets(m.L, false, K, false).total
+                                      : ws_offsets(m.L, o.precision == MRI_PREC_FP32_LU, K).total;
   a.budget_ns = o.time_budget_s > 0 ? (unsigned long long)std::ceil(o.time_budget_s * 1e9) : 0ull;
   a.adaptive = o.adaptive;
   a.schedule = o.schedule;
@@ -1578,12 +1707,16 @@ int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, 
   a.n_fallback = n_fallback;
   a.step_exp = step_exp;
   const bool prec32 = (o.precision == MRI_PREC_FP32_LU);
+  const bool expl = is_explicit(o.method);
   int warps, blocks;
   size_t smem;
-  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32, K, o.warps_per_block, o.blocks_per_sm))
+  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32 && !expl, K, o.warps_per_block, o.blocks_per_sm, !expl))
     return MRI_EINVAL;
   if ((rc = take_queue(m, a, st)) != MRI_OK) return rc;
-  if (prec32) {
+  if (expl) {
+    if (!allow_full_smem((const void*)stage_explicit_kernel)) return MRI_ECUDA;
+    stage_explicit_kernel<<<blocks, warps * 32, smem, st>>>(a, erk_table(o.method));
+  } else if (prec32) {
     if (!allow_full_smem((const void*)stage_fast_kernel<true>)) return MRI_ECUDA;
     stage_fast_kernel<true><<<blocks, warps * 32, smem, st>>>(a);
   } else {
@@ -1680,7 +1813,8 @@ int launch_stage_fast_batch(const mri_stage_group* groups, int ngroups, double H
 namespace mri {
 
 bool fast_opts_ok(const mri_fast_opts* o) {
-  return o && (o->method == MRI_SDIRK2 || o->method == MRI_SDIRK3) && o->newton_rtol > 0 &&
+  return o && (o->method == MRI_SDIRK2 || o->method == MRI_SDIRK3 || (is_explicit(o->method) && !o->adaptive)) &&
+         o->newton_rtol > 0 &&
          std::isfinite(o->newton_rtol) && o->newton_atol_Y >= 0 && o->newton_atol_T >= 0 &&
          std::isfinite(o->newton_atol_Y) && std::isfinite(o->newton_atol_T) && o->max_newton >= 1 &&
          o->max_newton <= 100 && (o->jac_policy == MRI_JAC_PER_SUBSTEP || o->jac_policy == MRI_JAC_LAZY) &&
@@ -1764,6 +1898,7 @@ extern "C" int mri_stage_fast_guided(double* y, const double* p, int ncell, cons
   (void)t0;
   if (!mech || !mri::fast_opts_ok(opts) || ncell < 0 || K < 0 || K > mri::kMaxK) return MRI_EINVAL;
   if (start < MRI_START_PREDICTOR || start > MRI_START_GUESS_FIRST) return MRI_EINVAL;
+  if (mri::is_explicit(opts->method)) return MRI_EINVAL;     // no Newton iteration to start
   if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
   if (start == MRI_START_GUESS || start == MRI_START_GUESS_FIRST) {
     double nsub = std::ceil(Hstage / h * (1.0 - 1e-12));
@@ -1782,7 +1917,7 @@ extern "C" int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, 
   (void)t0;
   if (!groups || ngroups < 1 || ngroups > MRI_MAX_GROUPS || !mri::fast_opts_ok(opts)) return MRI_EINVAL;
   if (opts->warps_per_block != 0 || opts->blocks_per_sm > 1 || opts->time_budget_s != 0.0 || opts->matrix_cache ||
-      opts->schedule != MRI_SCHED_QUEUE)
+      opts->schedule != MRI_SCHED_QUEUE || mri::is_explicit(opts->method))
     return MRI_EINVAL;
   if (!(Hstage > 0) || !(h > 0) || !std::isfinite(Hstage) || !std::isfinite(h)) return MRI_EINVAL;
   for (int g = 0; g < ngroups; ++g) {
@@ -1800,8 +1935,9 @@ extern "C" int mri_stage_fast_shape(const mri_mech* mech, const mri_fast_opts* o
   const Mech* m = reinterpret_cast<const Mech*>(mech);
   int w = 0, b = 0;
   size_t s = 0;
-  if (!mri::plan_launch(m->L, ncell, w, b, s, opts->precision == MRI_PREC_FP32_LU, K, opts->warps_per_block,
-                        opts->blocks_per_sm))
+  const bool expl = mri::is_explicit(opts->method);
+  if (!mri::plan_launch(m->L, ncell, w, b, s, opts->precision == MRI_PREC_FP32_LU && !expl, K, opts->warps_per_block,
+                        opts->blocks_per_sm, !expl))
     return MRI_EINVAL;
   if (warps_per_block) *warps_per_block = w;
   if (blocks) *blocks = b;

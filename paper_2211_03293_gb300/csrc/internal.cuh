@@ -141,11 +141,15 @@ __host__ __device__ inline F32Offsets f32_offsets(const Layout& L) {
   return f;
 }
 
-__host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = false, int K = kMaxK) {
+// matrix = false: no Newton matrix (the explicit fast methods need none); every other
+// section keeps its meaning.
+__host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = false, int K = kMaxK,
+                                                bool matrix = true) {
   WsOffsets w;
   int nv = round_up(L.n + 1, 2);
   int o = 0;
-  w.M = o; o += prec32 ? round_up(L.n * L.ld, 4) / 2 : round_up(L.n * L.ld, 2);
+  w.M = o;
+  if (matrix) o += prec32 ? round_up(L.n * L.ld, 4) / 2 : round_up(L.n * L.ld, 2);
   w.y0 = o; o += nv;
   w.Z = o; o += nv;
   w.d = o; o += nv;
@@ -207,6 +211,7 @@ int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, 
                       int start = MRI_START_PREDICTOR, int32_t* n_fallback = nullptr,
                       const int8_t* step_exp = nullptr);
 bool fast_opts_ok(const mri_fast_opts* o);
+bool is_explicit(int method);
 // MRI_OK when the current device is the one the mechanism's tables were loaded on,
 // MRI_EINVAL when it is another, MRI_ECUDA when the device cannot be queried
 int mech_device_check(const Mech& m);

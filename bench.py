@@ -121,8 +121,8 @@ def flop_model(mech):
                + 2 * ntb * Ns * 3              # third-body columns
                + 4 * Ns * Ns + 10 * Ns         # DC, column sums, chain rule
                + 2 * n * n)                    # M = I - hg J
-    lu = (2.0 / 3.0) * n ** 3 + n
-    solve = 2 * n * n
+    lu = (n - 1) * n * (2 * n - 1) / 3.0 + n * (n - 1) / 2.0   # Doolittle: multiply-adds and divisions
+    solve = 2 * n * (n - 1) + n                                # two substitutions
     vec = 8 * n                                # residual, update, WRMS norm
     return dict(rates=rates, jac_fp64=jac_fp64, jac_asm=jac_asm, lu=lu, solve=solve, vec=vec, n=n)
 

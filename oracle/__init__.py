@@ -52,6 +52,7 @@ def lib():
         L.orc_jac_cs.argtypes = [ct.c_void_p, _dp, ct.c_double, _dp]
         L.orc_mech_info.argtypes = [ct.c_void_p, _ip, _ip]
         L.orc_lu_solve.argtypes = [ct.c_int, _dp, _ip, _dp]
+        L.orc_flop_counts.argtypes = [ct.c_void_p, _dp, ct.c_double, ct.c_double, ct.POINTER(ct.c_longlong)]
         L.orc_sdirk_tableau.argtypes = [ct.c_int, _dp, _dp, _dp, _ip]
         L.orc_mri_tableau.argtypes = [_dp, _dp, _ip]
         L.orc_erk_tableau.argtypes = [ct.c_int, _dp, _dp, _dp, _ip]
@@ -148,6 +149,16 @@ class Mech:
         J = np.zeros((self.n, self.n))
         assert lib().orc_jac(self.ptr, _d(y), float(p), _d(J)) == 0
         return J
+
+    def flop_counts(self, y, p, hg):
+        """Operation counts of the oracle's formulas at state y: a dict of rows (rhs, jac,
+        lu, solve), each a dict of categories (add, mul, div, exp, log, pow)."""
+        y = _f64(y)
+        out = (ct.c_longlong * 24)()
+        assert lib().orc_flop_counts(self.ptr, _d(y), float(p), float(hg), out) == 0
+        cats = ("add", "mul", "div", "exp", "log", "pow")
+        return {row: {c: int(out[6 * i + j]) for j, c in enumerate(cats)}
+                for i, row in enumerate(("rhs", "jac", "lu", "solve"))}
 
     def jac_cs(self, y, p):
         y = _f64(y)

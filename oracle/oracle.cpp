@@ -75,12 +75,49 @@ bool parse(const void* blob, size_t nbytes, Mech& m) {
   return true;
 }
 
+// ---------------------------------------------------------------- operation counts
+// A double that counts the floating-point operations made on it, by category, in the
+// calling thread: the oracle's own formulas evaluated once with this type give the
+// algorithmic operation counts of a right-hand-side evaluation, a Jacobian, an LU
+// factorisation and a solve (orc_flop_counts).  Comparisons and |x| are not counted.
+
+struct OpCounts {
+  long long add = 0, mul = 0, div = 0, exp = 0, log = 0, pow = 0;
+};
+thread_local OpCounts g_ops;
+
+struct CD {
+  double v = 0.0;
+  CD() = default;
+  CD(double x) : v(x) {}   // constants and doubles enter implicitly
+};
+inline CD operator+(CD a, CD b) { g_ops.add++; return CD(a.v + b.v); }
+inline CD operator-(CD a, CD b) { g_ops.add++; return CD(a.v - b.v); }
+inline CD operator*(CD a, CD b) { g_ops.mul++; return CD(a.v * b.v); }
+inline CD operator/(CD a, CD b) { g_ops.div++; return CD(a.v / b.v); }
+inline CD operator-(CD a) { return CD(-a.v); }
+inline CD& operator+=(CD& a, CD b) { a = a + b; return a; }
+inline CD& operator-=(CD& a, CD b) { a = a - b; return a; }
+inline CD& operator*=(CD& a, CD b) { a = a * b; return a; }
+inline CD& operator/=(CD& a, CD b) { a = a / b; return a; }
+inline bool operator<(CD a, CD b) { return a.v < b.v; }
+inline bool operator>(CD a, CD b) { return a.v > b.v; }
+inline bool operator==(CD a, CD b) { return a.v == b.v; }
+inline CD exp(CD a) { g_ops.exp++; return CD(std::exp(a.v)); }
+inline CD log(CD a) { g_ops.log++; return CD(std::log(a.v)); }
+inline CD log10(CD a) { g_ops.log++; return CD(std::log10(a.v)); }
+inline CD pow(CD a, double b) { g_ops.pow++; return CD(std::pow(a.v, b)); }
+inline CD fabs(CD a) { return CD(std::fabs(a.v)); }
+inline bool isfinite(CD a) { return std::isfinite(a.v); }
+inline CD clamp_pos(CD x) { return x.v > 1e-300 ? x : CD(1e-300); }
+
 // ---------------------------------------------------------------- thermodynamics
 // NASA 7-coefficient polynomials (Gordon & McBride): cp/R, h/RT, s/R, g/RT = h/RT - s/R.
 
 template <class S>
 void thermo(const Mech& m, S T, S* cpR, S* hRT, S* sR, S* gRT) {
-  S lnT = std::log(T);
+  using std::log;
+  S lnT = log(T);
   for (int k = 0; k < m.Ns; ++k) {
     const double* a = &m.nasa[7 * k];
     S T2 = T * T, T3 = T2 * T, T4 = T3 * T;
@@ -116,6 +153,10 @@ S third_body(const Mech& m, int r, const S* C) {
 // falloff: k_f = k_inf (Pr/(1+Pr)) F with the Troe F; k_r = k_f / K_c.
 template <class S>
 void rate_coeffs(const Mech& m, int r, S T, const S* C, const S* gRT, S& kf, S& kr, S& Kc, S& M) {
+  using std::exp;
+  using std::log;
+  using std::log10;
+  using std::pow;
   S sumg = 0.0;
   int dn = 0;
   for (int j = 0; j < 3; ++j) {
@@ -124,21 +165,21 @@ void rate_coeffs(const Mech& m, int r, S T, const S* C, const S* gRT, S& kf, S& 
     int c = m.prod[3 * r + j];
     if (c >= 0) { sumg += gRT[c]; dn += 1; }
   }
-  Kc = std::exp(-sumg + double(dn) * std::log(P_ATM / (R_U * T)));
-  S kinf = m.A[r] * std::pow(T, m.b[r]) * std::exp(-m.Ta[r] / T);
+  Kc = exp(-sumg + double(dn) * log(P_ATM / (R_U * T)));
+  S kinf = m.A[r] * pow(T, m.b[r]) * exp(-m.Ta[r] / T);
   M = (m.rtype[r] != 0) ? third_body(m, r, C) : S(0.0);
   if (m.rtype[r] == 2) {
     const double* t = &m.troe[7 * (size_t)m.troe_row[r]];
-    S k0 = t[0] * std::pow(T, t[1]) * std::exp(-t[2] / T);
+    S k0 = t[0] * pow(T, t[1]) * exp(-t[2] / T);
     S Pr = clamp_pos(k0 * M / kinf);
-    S Fc = (1.0 - t[3]) * std::exp(-T / t[4]) + t[3] * std::exp(-T / t[5]) + std::exp(-t[6] / T);
-    S logFc = std::log10(Fc);
+    S Fc = (1.0 - t[3]) * exp(-T / t[4]) + t[3] * exp(-T / t[5]) + exp(-t[6] / T);
+    S logFc = log10(Fc);
     S c = -0.4 - 0.67 * logFc;
     S nn = 0.75 - 1.27 * logFc;
-    S u = std::log10(Pr) + c;
+    S u = log10(Pr) + c;
     S f1 = u / (nn - 0.14 * u);
     S logF = logFc / (1.0 + f1 * f1);
-    kf = kinf * (Pr / (1.0 + Pr)) * std::exp(logF * LN10);
+    kf = kinf * (Pr / (1.0 + Pr)) * exp(logF * LN10);
   } else {
     kf = kinf;
   }
@@ -197,76 +238,80 @@ void fast_rhs(const Mech& m, const S* y, double p, S* f) {
 // term (product rule over the reactant / product lists, third-body [M], Troe F
 // through x = log10 Pr and log10 Fcent, K_c through d ln K_c/dT = (sum nu h/RT - dn)/T),
 // D = nu dq/dC, then the chain rule through C(Y, T) and rho(Y, T) at constant p.
-void fast_jac(const Mech& m, const double* y, double p, double* J) {
+template <class S>
+void fast_jac(const Mech& m, const S* y, double p, S* J) {
+  using std::exp;
+  using std::log10;
+  using std::pow;
   const int Ns = m.Ns, n = Ns + 1;
-  double T = y[Ns];
-  double Ssum = 0.0;
+  S T = y[Ns];
+  S Ssum = 0.0;
   for (int k = 0; k < Ns; ++k) Ssum += y[k] / m.W[k];
-  double rho = p / (R_U * T * Ssum);
-  std::vector<double> C(Ns), cpR(Ns), hRT(Ns), gRT(Ns), wdot(Ns, 0.0);
+  S rho = p / (R_U * T * Ssum);
+  std::vector<S> C(Ns), cpR(Ns), hRT(Ns), gRT(Ns), wdot(Ns, 0.0);
   for (int k = 0; k < Ns; ++k) C[k] = rho * y[k] / m.W[k];
-  thermo<double>(m, T, cpR.data(), hRT.data(), nullptr, gRT.data());
+  thermo<S>(m, T, cpR.data(), hRT.data(), nullptr, gRT.data());
 
-  std::vector<double> D((size_t)Ns * Ns, 0.0), DT(Ns, 0.0);
-  std::vector<double> dqdC(Ns);
+  std::vector<S> D((size_t)Ns * Ns, 0.0), DT(Ns, 0.0);
+  std::vector<S> dqdC(Ns);
   for (int r = 0; r < m.R; ++r) {
-    double kf, kr, Kc, M;
-    rate_coeffs<double>(m, r, T, C.data(), gRT.data(), kf, kr, Kc, M);
+    S kf, kr, Kc, M;
+    rate_coeffs<S>(m, r, T, C.data(), gRT.data(), kf, kr, Kc, M);
     const int* re = &m.reac[3 * r];
     const int* pr = &m.prod[3 * r];
-    double fwd = prod_list(re, C.data()), rev = prod_list(pr, C.data());
-    double sum_nu_h = 0.0;
+    S fwd = prod_list(re, C.data()), rev = prod_list(pr, C.data());
+    S sum_nu_h = 0.0;
     int dn = 0;
     for (int j = 0; j < 3; ++j) {
       if (re[j] >= 0) { sum_nu_h -= hRT[re[j]]; dn -= 1; }
       if (pr[j] >= 0) { sum_nu_h += hRT[pr[j]]; dn += 1; }
     }
-    double dlnKc_dT = (sum_nu_h - dn) / T;
-    double dlnkf_dT = (m.b[r] + m.Ta[r] / T) / T;
-    double dlnkf_dM = 0.0;
+    S dlnKc_dT = (sum_nu_h - dn) / T;
+    S dlnkf_dT = (m.b[r] + m.Ta[r] / T) / T;
+    S dlnkf_dM = 0.0;
     if (m.rtype[r] == 2) {
       const double* t = &m.troe[7 * (size_t)m.troe_row[r]];
-      double kinf = m.A[r] * std::pow(T, m.b[r]) * std::exp(-m.Ta[r] / T);
-      double k0 = t[0] * std::pow(T, t[1]) * std::exp(-t[2] / T);
-      double Pr = clamp_pos(k0 * M / kinf);
-      double dlnkinf_dT = (m.b[r] + m.Ta[r] / T) / T;
-      double dlnk0_dT = (t[1] + t[2] / T) / T;
-      double dlnPr_dT = dlnk0_dT - dlnkinf_dT;
-      double e3 = std::exp(-T / t[4]), e1 = std::exp(-T / t[5]), e2 = std::exp(-t[6] / T);
-      double Fc = (1.0 - t[3]) * e3 + t[3] * e1 + e2;
-      double dFc_dT = -(1.0 - t[3]) / t[4] * e3 - t[3] / t[5] * e1 + t[6] / (T * T) * e2;
-      double logFc = std::log10(Fc);
-      double c = -0.4 - 0.67 * logFc, nn = 0.75 - 1.27 * logFc;
-      double u = std::log10(Pr) + c;
-      double den = nn - 0.14 * u;
-      double f1 = u / den;
-      double g = 1.0 + f1 * f1;
-      double df1_du = nn / (den * den);      // d f1 / d x and d f1 / d c
-      double df1_dnn = -u / (den * den);
-      double dlogF_df1 = -logFc * 2.0 * f1 / (g * g);
-      double dlogF_dx = dlogF_df1 * df1_du;
-      double dlogF_dlogFc = 1.0 / g + dlogF_df1 * (df1_du * (-0.67) + df1_dnn * (-1.27));
-      double dlogFc_dT = dFc_dT / (Fc * LN10);
-      double dx_dT = dlnPr_dT / LN10;
-      double dlnF_dT = LN10 * (dlogF_dx * dx_dT + dlogF_dlogFc * dlogFc_dT);
+      S kinf = m.A[r] * pow(T, m.b[r]) * exp(-m.Ta[r] / T);
+      S k0 = t[0] * pow(T, t[1]) * exp(-t[2] / T);
+      S Pr = clamp_pos(k0 * M / kinf);
+      S dlnkinf_dT = (m.b[r] + m.Ta[r] / T) / T;
+      S dlnk0_dT = (t[1] + t[2] / T) / T;
+      S dlnPr_dT = dlnk0_dT - dlnkinf_dT;
+      S e3 = exp(-T / t[4]), e1 = exp(-T / t[5]), e2 = exp(-t[6] / T);
+      S Fc = (1.0 - t[3]) * e3 + t[3] * e1 + e2;
+      S dFc_dT = -(1.0 - t[3]) / t[4] * e3 - t[3] / t[5] * e1 + t[6] / (T * T) * e2;
+      S logFc = log10(Fc);
+      S c = -0.4 - 0.67 * logFc, nn = 0.75 - 1.27 * logFc;
+      S u = log10(Pr) + c;
+      S den = nn - 0.14 * u;
+      S f1 = u / den;
+      S g = 1.0 + f1 * f1;
+      S df1_du = nn / (den * den);      // d f1 / d x and d f1 / d c
+      S df1_dnn = -u / (den * den);
+      S dlogF_df1 = -logFc * 2.0 * f1 / (g * g);
+      S dlogF_dx = dlogF_df1 * df1_du;
+      S dlogF_dlogFc = 1.0 / g + dlogF_df1 * (df1_du * (-0.67) + df1_dnn * (-1.27));
+      S dlogFc_dT = dFc_dT / (Fc * LN10);
+      S dx_dT = dlnPr_dT / LN10;
+      S dlnF_dT = LN10 * (dlogF_dx * dx_dT + dlogF_dlogFc * dlogFc_dT);
       dlnkf_dT = dlnkinf_dT + dlnPr_dT / (1.0 + Pr) + dlnF_dT;
       dlnkf_dM = (1.0 / M) * (1.0 / (1.0 + Pr) + dlogF_dx);
     }
-    double dlnkr_dT = dlnkf_dT - dlnKc_dT;
-    double base = kf * fwd - kr * rev;
-    double wM = (m.rtype[r] == 1) ? M : 1.0;
-    double dqdT = wM * (kf * dlnkf_dT * fwd - kr * dlnkr_dT * rev);
+    S dlnkr_dT = dlnkf_dT - dlnKc_dT;
+    S base = kf * fwd - kr * rev;
+    S wM = (m.rtype[r] == 1) ? M : 1.0;
+    S dqdT = wM * (kf * dlnkf_dT * fwd - kr * dlnkr_dT * rev);
     // d(prod over list)/dC_l by the product rule
-    std::fill(dqdC.begin(), dqdC.end(), 0.0);
+    std::fill(dqdC.begin(), dqdC.end(), S(0.0));
     for (int j = 0; j < 3; ++j) {
       if (re[j] >= 0) {
-        double o = 1.0;
+        S o = 1.0;
         for (int jj = 0; jj < 3; ++jj)
           if (jj != j && re[jj] >= 0) o *= C[re[jj]];
         dqdC[re[j]] += wM * kf * o;
       }
       if (pr[j] >= 0) {
-        double o = 1.0;
+        S o = 1.0;
         for (int jj = 0; jj < 3; ++jj)
           if (jj != j && pr[jj] >= 0) o *= C[pr[jj]];
         dqdC[pr[j]] -= wM * kr * o;
@@ -274,10 +319,10 @@ void fast_jac(const Mech& m, const double* y, double p, double* J) {
     }
     if (m.rtype[r] != 0) {
       int row = m.eff_row[r];
-      double s = (m.rtype[r] == 1) ? base : dlnkf_dM * base;
+      S s = (m.rtype[r] == 1) ? base : dlnkf_dM * base;
       for (int l = 0; l < Ns; ++l) dqdC[l] += m.eff[(size_t)row * Ns + l] * s;
     }
-    double qr = wM * base;
+    S qr = wM * base;
     for (int j = 0; j < 3; ++j) {
       int a = re[j], c = pr[j];
       if (a >= 0) {
@@ -291,7 +336,7 @@ void fast_jac(const Mech& m, const double* y, double p, double* J) {
     }
   }
   // chain rule to (Y, T)
-  std::vector<double> DC(Ns, 0.0);
+  std::vector<S> DC(Ns, 0.0);
   for (int k = 0; k < Ns; ++k)
     for (int l = 0; l < Ns; ++l) DC[k] += D[(size_t)k * Ns + l] * C[l];
   for (int k = 0; k < Ns; ++k) {
@@ -300,7 +345,7 @@ void fast_jac(const Mech& m, const double* y, double p, double* J) {
     J[(size_t)k * n + Ns] = (m.W[k] / rho) * (DT[k] - (DC[k] - wdot[k]) / T);
   }
   // temperature row: f_T = -Phi Q / cpm, Phi = T/rho, Q = sum h/RT wdot, cpm = sum Y cp/R / W
-  double Phi = T / rho, Q = 0.0, cpm = 0.0, dcpm_dT = 0.0;
+  S Phi = T / rho, Q = 0.0, cpm = 0.0, dcpm_dT = 0.0;
   for (int k = 0; k < Ns; ++k) {
     const double* a = &m.nasa[7 * k];
     Q += hRT[k] * wdot[k];
@@ -308,13 +353,13 @@ void fast_jac(const Mech& m, const double* y, double p, double* J) {
     dcpm_dT += y[k] / m.W[k] * (a[1] + 2.0 * a[2] * T + 3.0 * a[3] * T * T + 4.0 * a[4] * T * T * T);
   }
   for (int j = 0; j < Ns; ++j) {
-    double dQ = 0.0;   // sum_k h/RT_k d wdot_k / dY_j
+    S dQ = 0.0;   // sum_k h/RT_k d wdot_k / dY_j
     for (int k = 0; k < Ns; ++k)
       dQ += hRT[k] * (D[(size_t)k * Ns + j] * rho / m.W[j] - DC[k] / (Ssum * m.W[j]));
-    double dPhi = Phi / (Ssum * m.W[j]);
+    S dPhi = Phi / (Ssum * m.W[j]);
     J[(size_t)Ns * n + j] = -(dPhi * Q / cpm + Phi * dQ / cpm - Phi * Q * (cpR[j] / m.W[j]) / (cpm * cpm));
   }
-  double dQdT = 0.0;
+  S dQdT = 0.0;
   for (int k = 0; k < Ns; ++k) dQdT += (cpR[k] - hRT[k]) / T * wdot[k] + hRT[k] * (DT[k] - DC[k] / T);
   J[(size_t)Ns * n + Ns] = -(2.0 * Phi / T * Q / cpm + Phi * dQdT / cpm - Phi * Q * dcpm_dT / (cpm * cpm));
 }
@@ -333,20 +378,23 @@ void fast_jac_cs(const Mech& m, const double* y, double p, double* J) {
 // ---------------------------------------------------------------- dense LU
 // Doolittle LU with partial pivoting (largest |a|, ties -> lowest row index), in place.
 
-int lu_factor(int n, double* A, int* piv) {
+template <class S>
+int lu_factor(int n, S* A, int* piv) {
+  using std::fabs;
+  using std::isfinite;
   for (int k = 0; k < n; ++k) {
     int p = k;
-    double best = std::fabs(A[(size_t)k * n + k]);
+    S best = fabs(A[(size_t)k * n + k]);
     for (int i = k + 1; i < n; ++i) {
-      double v = std::fabs(A[(size_t)i * n + k]);
+      S v = fabs(A[(size_t)i * n + k]);
       if (v > best) { best = v; p = i; }
     }
     piv[k] = p;
-    if (best == 0.0 || !std::isfinite(best)) return k + 1;
+    if (best == S(0.0) || !isfinite(best)) return k + 1;
     if (p != k)
       for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
     for (int i = k + 1; i < n; ++i) {
-      double l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      S l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
       A[(size_t)i * n + k] = l;
       for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
     }
@@ -354,7 +402,8 @@ int lu_factor(int n, double* A, int* piv) {
   return 0;
 }
 
-void lu_solve(int n, const double* A, const int* piv, double* b) {
+template <class S>
+void lu_solve(int n, const S* A, const int* piv, S* b) {
   for (int k = 0; k < n; ++k)
     if (piv[k] != k) std::swap(b[k], b[piv[k]]);
   for (int i = 0; i < n; ++i)
@@ -980,6 +1029,36 @@ int orc_jac(const void* mech, const double* y, double p, double* J) {
 int orc_jac_cs(const void* mech, const double* y, double p, double* J) {
   if (!mech) return -1;
   fast_jac_cs(*static_cast<const Mech*>(mech), y, p, J);
+  return 0;
+}
+
+int orc_flop_counts(const void* mech, const double* y, double p, double hg, long long* out) {
+  if (!mech || !y || !out || !(p > 0) || !(hg > 0)) return -1;
+  const Mech& m = *static_cast<const Mech*>(mech);
+  const int n = m.Ns + 1;
+  auto take = [&](int row) {
+    const long long v[6] = {g_ops.add, g_ops.mul, g_ops.div, g_ops.exp, g_ops.log, g_ops.pow};
+    for (int c = 0; c < 6; ++c) out[row * 6 + c] = v[c];
+    g_ops = OpCounts();
+  };
+  std::vector<CD> yc(y, y + n), f(n), Jc((size_t)n * n);
+  g_ops = OpCounts();
+  fast_rhs<CD>(m, yc.data(), p, f.data());
+  take(0);
+  fast_jac<CD>(m, yc.data(), p, Jc.data());
+  take(1);
+  // LU of the Newton matrix I - hg J at this state (pivots as in the solver)
+  std::vector<double> J((size_t)n * n);
+  fast_jac<double>(m, y, p, J.data());
+  std::vector<CD> M((size_t)n * n), b(n, CD(1.0));
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c < n; ++c) M[(size_t)a * n + c] = CD((a == c ? 1.0 : 0.0) - hg * J[(size_t)a * n + c]);
+  std::vector<int> piv(n);
+  g_ops = OpCounts();
+  if (lu_factor<CD>(n, M.data(), piv.data()) != 0) return 1;
+  take(2);
+  lu_solve<CD>(n, M.data(), piv.data(), b.data());
+  take(3);
   return 0;
 }
 

@@ -81,6 +81,12 @@ int orc_jac(const void* mech, const double* y, double p, double* J);
 int orc_jac_cs(const void* mech, const double* y, double p, double* J);
 
 int orc_lu_solve(int n, double* A, int* piv, double* b);
+/* Floating-point operations of the oracle's own formulas at state y, counted by
+ * category: out[row * 6 + col], rows 0 one f^F evaluation, 1 one analytic Jacobian
+ * (its rate evaluation included), 2 one LU factorisation of I - hg J, 3 one solve with
+ * those factors; columns add/subtract, multiply, divide, exp, log (natural or decimal),
+ * pow.  Returns 0, 1 if the matrix is singular, -1 on bad arguments. */
+int orc_flop_counts(const void* mech, const double* y, double p, double hg, long long* out);
 int orc_sdirk_tableau(int method, double* A, double* b, double* c, int* s);
 /* embedded weights of the adaptive error estimate (one order lower than the method)
    and the estimate's order q (the controller scales steps by err^(-1/q)) */

@@ -293,10 +293,12 @@ typedef struct {
  * on a 9-, a 40- and an 80-species mechanism: K = 0 and no slow partition).  Every
  * group is integrated exactly as mri_stage_fast integrates it (same Hstage, h and
  * opts for all groups; the results are bitwise those of one mri_stage_fast call per
- * group).  The SMs are split between the groups in proportion to an estimate of
- * their work; each group's CTAs hold its tables and take its cells from its own
- * queue.  opts->warps_per_block and opts->time_budget_s must be 0 and
- * opts->blocks_per_sm 0 or 1 (MRI_EINVAL otherwise).  n_failed (nullable) counts
+ * group).  The SMs are first split between the groups in proportion to an estimate
+ * of their work; each group's CTAs hold its tables and take its cells from its own
+ * queue, and a CTA whose group has no cells left stages the next group's tables and
+ * takes cells from that group's queue, so the costliest group gets help at the end.
+ * opts->warps_per_block and opts->time_budget_s must be 0, opts->blocks_per_sm 0 or
+ * 1, opts->schedule the work queue and the method implicit (MRI_EINVAL otherwise).  n_failed (nullable) counts
  * failed cells over all groups.  The paper solves one mechanism at a time; mixing
  * mechanisms in one launch is a batching service of this library. */
 int mri_stage_fast_batch(const mri_stage_group* groups, int ngroups, double t0, double Hstage, double h,

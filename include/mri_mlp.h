@@ -99,6 +99,30 @@ int mri_learned_guess(const double* y_in, const float* yhat, int ld_yhat, int G,
 int mri_learned_step_exp(const float* yhat, int ld_yhat, int col, int ncell, float tmean, float tstd, int kmin,
                          int kmax, int8_t* step_exp, void* stream);
 
+/* Standardisation constants of a data matrix (the network's raw inputs or targets),
+ * computed on the device: X [rows][ld] FP32, for each column f < cols the mean and the
+ * population standard deviation over the rows (sums in FP64, over row chunks added in
+ * a fixed order, so the result is deterministic); a deviation below floor_sd (a
+ * constant column) is replaced by 1.  mean, inv_std = 1 / sd and sd (nullable) are
+ * FP32 device arrays of cols values.  workspace: device buffer of
+ * mri_learned_moments_workspace_size(cols) bytes (MRI_ENOMEM if smaller). */
+size_t mri_learned_moments_workspace_size(int cols);
+int mri_learned_moments(const float* X, long long rows, int cols, int ld, float floor_sd, float* mean,
+                        float* inv_std, float* sd, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Standardised and reordered rows: out [rows_out][ld_out] with
+ * out[i][f] = (X[perm[i]][f] - mean[f]) * inv_std[f] for f < used and 0 for
+ * used <= f < ld_out; perm (device int32 [rows_out], nullable: identity) is the
+ * shuffle of a training epoch, drawn by the caller. */
+int mri_learned_standardise(const float* X, int ld, const int32_t* perm, long long rows_out, int used,
+                            const float* mean, const float* inv_std, float* out, int ld_out, void* stream);
+
+/* Targets of the substep-size network from an adaptive solve's per-cell counters:
+ * k[c] = log2(n_sub / max(accepted[c * stride], 1)), the log2 of the cell's mean
+ * accepted step relative to the uniform substep Hstage / n_sub (accepted: device
+ * int32, e.g. cell_stats with stride 4; k: device FP32 [ncell]). */
+int mri_learned_step_targets(const int32_t* accepted, int stride, int ncell, int n_sub, float* k, void* stream);
+
 /* The GEMM the network is built on, exposed for testing:
  * C [M][ldc] (FP32) = A [M][lda] * B [N][ldb]^T over K, A and B bfloat16 bit
  * patterns (uint16) with K contiguous; N a multiple of 16 in 16..256, K, lda and

@@ -93,6 +93,12 @@ _lib.mri_learned_features.argtypes = [_vp, _vp, _vp, ct.c_int, ct.c_int, ct.c_in
                                       ct.c_int, _vp]
 _lib.mri_learned_targets.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, ct.c_int, _vp]
 _lib.mri_learned_guess.argtypes = [_vp, _vp, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _vp, _vp, _vp, _vp]
+_lib.mri_learned_moments_workspace_size.argtypes = [ct.c_int]
+_lib.mri_learned_moments_workspace_size.restype = ct.c_size_t
+_lib.mri_learned_moments.argtypes = [_vp, ct.c_longlong, ct.c_int, ct.c_int, ct.c_float, _vp, _vp, _vp, _vp,
+                                     ct.c_size_t, _vp]
+_lib.mri_learned_standardise.argtypes = [_vp, ct.c_int, _vp, ct.c_longlong, ct.c_int, _vp, _vp, _vp, ct.c_int, _vp]
+_lib.mri_learned_step_targets.argtypes = [_vp, ct.c_int, ct.c_int, ct.c_int, _vp, _vp]
 _lib.mri_learned_step_exp.argtypes = [_vp, ct.c_int, ct.c_int, ct.c_int, ct.c_float, ct.c_float, ct.c_int, ct.c_int,
                                       _vp, _vp]
 _lib.mri_probe_log.argtypes = [_vp, _vp, ct.c_longlong, _vp]
@@ -142,7 +148,8 @@ EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_de
             "mri_learned_guess", "mri_learned_step_exp", "mri_probe_log", "mri_probe_exp_pair",
             "mri_matrix_cache_size", "mri_diffusion_workspace_size", "mri_diffusion_solve",
             "mri_step_imex1_workspace_size", "mri_step_imex1", "mri_step_imex2_workspace_size",
-            "mri_step_imex2", "mri_probe_mech_device")
+            "mri_step_imex2", "mri_probe_mech_device", "mri_learned_moments_workspace_size",
+            "mri_learned_moments", "mri_learned_standardise", "mri_learned_step_targets")
 
 
 class MriError(RuntimeError):
@@ -544,6 +551,39 @@ def mri_learned_targets(y_in, y_seq, tmean, tinv_std, t, stream=None) -> int:
     return _check(_lib.mri_learned_targets(_f64(y_in), _f64(y_seq), y_seq.shape[1], y_in.shape[0], y_in.shape[1],
                                            _f32(tmean), _f32(tinv_std), _f32(t), t.shape[1], _stream(stream)),
                   "mri_learned_targets")
+
+
+def mri_learned_moments(X, used, floor_sd, stream=None):
+    """Column mean, inverse standard deviation and standard deviation (float32 device
+    tensors of `used` values) of the first `used` columns of X [rows][ld] (float32)."""
+    import torch
+    rows, ld = X.shape
+    dev = X.device
+    mean = torch.empty(used, dtype=torch.float32, device=dev)
+    inv = torch.empty(used, dtype=torch.float32, device=dev)
+    sd = torch.empty(used, dtype=torch.float32, device=dev)
+    nb = int(_lib.mri_learned_moments_workspace_size(used))
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    _check(_lib.mri_learned_moments(_f32(X), rows, used, ld, float(floor_sd), _f32(mean), _f32(inv), _f32(sd),
+                                    _ptr(ws), nb, _stream(stream)), "mri_learned_moments")
+    return mean, inv, sd
+
+
+def mri_learned_standardise(X, perm, used, mean, inv_std, out, stream=None) -> int:
+    """out[i] = (X[perm[i]] - mean) * inv_std on the first `used` columns, 0 beyond."""
+    import torch
+    if perm is not None and perm.dtype != torch.int32:
+        raise TypeError("int32 permutation expected")
+    rows_out = out.shape[0]
+    return _check(_lib.mri_learned_standardise(_f32(X), X.shape[1], _ptr(perm), rows_out, int(used), _f32(mean),
+                                               _f32(inv_std), _f32(out), out.shape[1], _stream(stream)),
+                  "mri_learned_standardise")
+
+
+def mri_learned_step_targets(accepted, n_sub, k, stride=4, stream=None) -> int:
+    """k[c] = log2(n_sub / max(accepted[c * stride], 1)) on the device (accepted: int32)."""
+    return _check(_lib.mri_learned_step_targets(_i32(accepted), int(stride), k.shape[0], int(n_sub), _f32(k),
+                                                _stream(stream)), "mri_learned_step_targets")
 
 
 def mri_learned_step_exp(yhat, col, tmean, tstd, step_exp, kmin=-20, kmax=10, stream=None) -> int:

@@ -1412,19 +1412,27 @@ static_assert(sizeof(BatchArgs) <= 32764, "batch arguments must fit the kernel p
 static_assert(sizeof(StageArgs) + 12 * sizeof(double) <= 1024, "static shared memory of the stage kernels");
 
 template <bool PREC32>
+// The split of the CTAs is only where they start: a CTA whose group has no cells left
+// moves on to the other groups in turn (staging their tables), so the groups whose cells
+// cost most get help at the end instead of leaving the other SMs idle.  Every cell is
+// still integrated by one warp with its group's tables, so results do not change.
 __global__ void __launch_bounds__(kMaxWarps * 32) stage_fast_batch_kernel(const __grid_constant__ BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sA[3][3], sc[3];
   __shared__ StageArgs sa;
   int gi = 0;
   while (gi + 1 < b.ngroups && (int)blockIdx.x >= b.block0[gi + 1]) ++gi;
-  if (threadIdx.x == 0) sa = b.g[gi];
-  stage_table(smem, b.g[gi].table, b.g[gi].L.bytes);
-  if (threadIdx.x < 9) sA[threadIdx.x / 3][threadIdx.x % 3] = b.g[gi].A[threadIdx.x / 3][threadIdx.x % 3];
-  if (threadIdx.x < 3) sc[threadIdx.x] = b.g[gi].c[threadIdx.x];
-  __syncthreads();
   const int warp = threadIdx.x >> 5;
-  if (warp < b.warps[gi]) stage_cells<PREC32>(sa, smem, sA, sc, warp, threadIdx.x & 31);
+  for (int pass = 0; pass < b.ngroups; ++pass) {
+    const int g = (gi + pass) % b.ngroups;
+    if (threadIdx.x == 0) sa = b.g[g];
+    stage_table(smem, b.g[g].table, b.g[g].L.bytes);
+    if (threadIdx.x < 9) sA[threadIdx.x / 3][threadIdx.x % 3] = b.g[g].A[threadIdx.x / 3][threadIdx.x % 3];
+    if (threadIdx.x < 3) sc[threadIdx.x] = b.g[g].c[threadIdx.x];
+    __syncthreads();
+    if (warp < b.warps[g]) stage_cells<PREC32>(sa, smem, sA, sc, warp, threadIdx.x & 31);
+    __syncthreads();        // every warp is done with this group's tables before the next are staged
+  }
 }
 
 // Cells the budget left untaken: [min(counter, ncell), ncell).

@@ -26,6 +26,7 @@ constexpr int kRedBlocks = 512;     // blocks of the fused passes (partial sums 
 constexpr int kPassThreads = 256;   // threads of a fused pass (at least one warp per component)
 constexpr int kPassMax = 1024;      // n <= 1024: one slot of up to 1024 threads
 constexpr int kScalThreads = 1024;  // the scalar kernels: one warp per component at a time
+constexpr int kDirBlocks = 2432;    // blocks of the direction update (16 per SM)
 
 struct Lap7 {
   int nx, ny, nz, n;
@@ -45,9 +46,13 @@ struct CgScal {          // per component
   int done;
 };
 
-// (A x)[cell][q] for the 7-point operator
+// (A x)[cell][q] for the 7-point operator.  The cell's grid coordinates come from 32-bit
+// unsigned division (grids hold at most 2^31 - 1 cells), several times cheaper than the
+// 64-bit form on a pass that touches every element.
 __device__ __forceinline__ double apply_at(const double* __restrict__ x, const Lap7& s, long long cell, int q) {
-  const int i = (int)(cell % s.nx), j = (int)((cell / s.nx) % s.ny), k = (int)(cell / ((long long)s.nx * s.ny));
+  const unsigned cc = (unsigned)cell, nx = (unsigned)s.nx, ny = (unsigned)s.ny;
+  const unsigned row = cc / nx;
+  const int i = (int)(cc - row * nx), j = (int)(row % ny), k = (int)(row / ny);
   double acc = s.centre * x[cell * s.n + q];
   if (s.nx > 1) {
     const int ip = (i + 1 == s.nx) ? 0 : i + 1, im = (i == 0) ? s.nx - 1 : i - 1;
@@ -201,19 +206,20 @@ __global__ void __launch_bounds__(kPassMax) update_pass_kernel(double* __restric
 }
 
 // START: p = r / diag for every component; else p = r / diag + beta p for the
-// components still iterating
+// components still iterating.  Thread (slot, q) of the fused passes' layout owns
+// component q of its cells, so the component needs no division.
 template <bool START>
-__global__ void dir_kernel(double* __restrict__ p, const double* __restrict__ r, long long len, int n, double inv_diag,
-                           const CgScal* sc, const CgState* cs) {
+__global__ void __launch_bounds__(kPassMax) dir_kernel(double* __restrict__ p, const double* __restrict__ r,
+                                                          long long ncell, int n, int rt, double inv_diag,
+                                                          const CgScal* sc, const CgState* cs) {
   if (!START && cs->finished) return;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-       e += (long long)gridDim.x * blockDim.x) {
-    if (START) {
-      p[e] = r[e] * inv_diag;
-    } else {
-      const int q = (int)(e % n);
-      if (!sc[q].done) p[e] = fma(sc[q].beta, p[e], r[e] * inv_diag);
-    }
+  const int q = threadIdx.x % rt, slot = threadIdx.x / rt, S = blockDim.x / rt;
+  if (q >= n) return;
+  if (!START && sc[q].done) return;
+  const double beta = START ? 0.0 : sc[q].beta;
+  for (long long c = (long long)blockIdx.x * S + slot; c < ncell; c += (long long)gridDim.x * S) {
+    const long long e = c * n + q;
+    p[e] = START ? r[e] * inv_diag : fma(beta, p[e], r[e] * inv_diag);
   }
 }
 
@@ -312,7 +318,6 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
   CgState* cs = reinterpret_cast<CgState*>(sc + n);
   const Lap7 op = make_op(g, n, a);
   const double inv_diag = 1.0 / op.centre;
-  const int eb = elementwise_blocks(len);
   const int rt = ((n + 31) / 32) * 32;
   const int S = rt < kPassThreads ? kPassThreads / rt : 1;
   const int pt = S * rt;                                   // threads of a fused pass
@@ -321,7 +326,8 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
   if (iters) *iters = 0;
   apply_pass_kernel<0><<<nblk, pt, 0, st>>>(x, b, r, op, rt, part1, part2, nullptr, nullptr);
   cg_init_kernel<<<1, kScalThreads, 0, st>>>(part1, part2, nblk, n, inv_diag, tol, sc, cs);
-  dir_kernel<true><<<eb, 256, 0, st>>>(p, r, len, n, inv_diag, sc, cs);
+  const int dblk = (int)((ncell + S - 1) / S < kDirBlocks ? (ncell + S - 1) / S : kDirBlocks);
+  dir_kernel<true><<<dblk, pt, 0, st>>>(p, r, ncell, n, rt, inv_diag, sc, cs);
   if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
   CgState h{};
   for (int it = 0; it < max_iter; ++it) {
@@ -333,7 +339,7 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
     }
     apply_pass_kernel<1><<<nblk, pt, 0, st>>>(p, nullptr, Ap, op, rt, part1, nullptr, sc, cs);
     update_pass_kernel<<<nblk, pt, 0, st>>>(x, r, p, Ap, ncell, n, rt, sc, part1, inv_diag, tol, cs);
-    dir_kernel<false><<<eb, 256, 0, st>>>(p, r, len, n, inv_diag, sc, cs);
+    dir_kernel<false><<<dblk, pt, 0, st>>>(p, r, ncell, n, rt, inv_diag, sc, cs);
     if (cudaGetLastError() != cudaSuccess) return MRI_ECUDA;
   }
   if (info) {

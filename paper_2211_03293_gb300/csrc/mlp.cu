@@ -630,8 +630,110 @@ __global__ void step_exp_kernel(const float* yhat, int ld, int col, int ncell, f
   }
 }
 
+// Column moments, pass 1: block (column group of 32, row chunk) sums X and X^2 (FP64)
+// over its rows for its 32 columns; 8 row slots per block, combined in a fixed order.
+constexpr int kMomChunks = 256;
+__global__ void moments_part_kernel(const float* X, long long rows, int cols, int ld, double* part) {
+  __shared__ double s1[8][32], s2[8][32];
+  const int f = blockIdx.x * 32 + threadIdx.x, slot = threadIdx.y;
+  const long long per = (rows + kMomChunks - 1) / kMomChunks;
+  const long long r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
+  double a = 0.0, b = 0.0;
+  if (f < cols)
+    for (long long r = r0 + slot; r < r1; r += 8) {
+      const double v = X[r * ld + f];
+      a += v;
+      b = fma(v, v, b);
+    }
+  s1[slot][threadIdx.x] = a;
+  s2[slot][threadIdx.x] = b;
+  __syncthreads();
+  if (slot == 0 && f < cols) {
+    double A = 0.0, B = 0.0;
+    for (int k = 0; k < 8; ++k) { A += s1[k][threadIdx.x]; B += s2[k][threadIdx.x]; }
+    part[((size_t)blockIdx.y * cols + f) * 2] = A;
+    part[((size_t)blockIdx.y * cols + f) * 2 + 1] = B;
+  }
+}
+
+// pass 2: one thread per column adds the chunks in order: mean, population standard
+// deviation (a deviation below floor becomes 1) and its inverse
+__global__ void moments_final_kernel(const double* part, long long rows, int cols, float floor_sd, float* mean,
+                                     float* inv_std, float* sd_out) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= cols) return;
+  double A = 0.0, B = 0.0;
+  for (int c = 0; c < kMomChunks; ++c) {
+    A += part[((size_t)c * cols + f) * 2];
+    B += part[((size_t)c * cols + f) * 2 + 1];
+  }
+  const double m = A / (double)rows;
+  const double var = fmax(B / (double)rows - m * m, 0.0);
+  double sd = sqrt(var);
+  if (!(sd >= (double)floor_sd)) sd = 1.0;
+  mean[f] = (float)m;
+  inv_std[f] = (float)(1.0 / sd);
+  if (sd_out) sd_out[f] = (float)sd;
+}
+
+// out[i][f] = (X[perm[i]][f] - mean[f]) * inv_std[f] for f < used, 0 up to ld_out
+__global__ void standardise_kernel(const float* X, int ld, const int32_t* perm, long long rows_out, int used,
+                                   const float* mean, const float* inv_std, float* out, int ld_out) {
+  const long long total = rows_out * ld_out;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / ld_out;
+    const int f = (int)(e % ld_out);
+    const long long src = perm ? (long long)perm[i] : i;
+    out[e] = (f < used) ? (X[src * ld + f] - mean[f]) * inv_std[f] : 0.0f;
+  }
+}
+
+// k[c] = log2(n_sub / max(accepted[c], 1)): the log2 of a cell's mean accepted step
+// relative to the uniform substep
+__global__ void step_targets_kernel(const int32_t* accepted, int stride, int ncell, int n_sub, float* k) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int a = accepted[(size_t)c * stride];
+    k[c] = (float)log2((double)n_sub / (double)(a > 1 ? a : 1));
+  }
+}
+
 }  // namespace
 }  // namespace mri
+
+extern "C" size_t mri_learned_moments_workspace_size(int cols) {
+  return cols < 1 ? 0 : (size_t)mri::kMomChunks * cols * 2 * sizeof(double);
+}
+
+extern "C" int mri_learned_moments(const float* X, long long rows, int cols, int ld, float floor_sd, float* mean,
+                                   float* inv_std, float* sd, void* workspace, size_t workspace_bytes, void* stream) {
+  if (rows < 1 || cols < 1 || ld < cols || !(floor_sd >= 0.0f) || !X || !mean || !inv_std) return MRI_EINVAL;
+  if (!workspace || workspace_bytes < mri_learned_moments_workspace_size(cols)) return MRI_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* part = static_cast<double*>(workspace);
+  mri::moments_part_kernel<<<dim3((cols + 31) / 32, mri::kMomChunks), dim3(32, 8), 0, st>>>(X, rows, cols, ld, part);
+  mri::moments_final_kernel<<<(cols + 127) / 128, 128, 0, st>>>(part, rows, cols, floor_sd, mean, inv_std, sd);
+  return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
+}
+
+extern "C" int mri_learned_standardise(const float* X, int ld, const int32_t* perm, long long rows_out, int used,
+                                       const float* mean, const float* inv_std, float* out, int ld_out, void* stream) {
+  if (rows_out < 0 || used < 0 || used > ld || used > ld_out || !X || !mean || !inv_std || !out) return MRI_EINVAL;
+  if (rows_out == 0) return MRI_OK;
+  mri::standardise_kernel<<<grid_for(rows_out * ld_out), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      X, ld, perm, rows_out, used, mean, inv_std, out, ld_out);
+  return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
+}
+
+extern "C" int mri_learned_step_targets(const int32_t* accepted, int stride, int ncell, int n_sub, float* k,
+                                        void* stream) {
+  if (ncell < 0 || stride < 1 || n_sub < 1) return MRI_EINVAL;
+  if (ncell == 0) return MRI_OK;
+  if (!accepted || !k) return MRI_EINVAL;
+  mri::step_targets_kernel<<<grid_for(ncell), 256, 0, static_cast<cudaStream_t>(stream)>>>(accepted, stride, ncell,
+                                                                                         n_sub, k);
+  return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
+}
 
 extern "C" int mri_learned_step_exp(const float* yhat, int ld_yhat, int col, int ncell, float tmean, float tstd,
                                     int kmin, int kmax, int8_t* step_exp, void* stream) {

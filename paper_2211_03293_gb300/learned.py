@@ -2,12 +2,13 @@
 predicts a stage's substep-end states as the Newton start of the fast solve.
 
 Every computation runs in the library's kernels (include/mri_mlp.h, mri.h):
-the plain solver produces the training data, the tensor-core network kernels
-train and evaluate the model, and mri_stage_fast_guided solves the stage from
-the predicted states -- every stage value is still accepted only by the FP64
-Newton residual test, with a restart from the plain start wherever Newton does
-not converge.  This module only sequences those calls and keeps the
-normalisation constants (host arithmetic on data already produced).
+the plain solver produces the training data, the data kernels standardise and
+shuffle it on the device, the tensor-core network kernels train and evaluate the
+model, and mri_stage_fast_guided solves the stage from the predicted states --
+every stage value is still accepted only by the FP64 Newton residual test, with a
+restart from the plain start wherever Newton does not converge.  This module only
+sequences those calls; the host draws the shuffles' permutations (seeded) and
+reads back the step network's two normalisation constants.
 """
 from __future__ import annotations
 
@@ -15,8 +16,9 @@ import math
 
 import numpy as np
 
-from . import (Mlp, mri_fast_opts, mri_learned_features, mri_learned_guess, mri_learned_step_exp,
-               mri_learned_targets, mri_mlp_adam, mri_mlp_forward, mri_mlp_grad, mri_stage_fast)
+from . import (Mlp, mri_fast_opts, mri_learned_features, mri_learned_guess, mri_learned_moments,
+               mri_learned_standardise, mri_learned_step_exp, mri_learned_step_targets, mri_learned_targets,
+               mri_mlp_adam, mri_mlp_forward, mri_mlp_grad, mri_stage_fast)
 
 
 def _pad16(v):
@@ -97,48 +99,54 @@ class LearnedStart:
         self.records.append((x, t))
 
     def _standardise(self):
+        """Device standardisation constants of the collected examples; returns the raw
+        feature and target matrices (device float32)."""
         import torch
-        X = torch.cat([r[0] for r in self.records]).cpu().numpy().astype(np.float64)
-        T = torch.cat([r[1] for r in self.records]).cpu().numpy().astype(np.float64)
-        fm, fs = X.mean(0), X.std(0)
-        tm, ts = T.mean(0), T.std(0)
-        used_out = self.g_max * self.n
-        fs[fs < 1e-12] = 1.0
-        ts[ts < 1e-30] = 1.0
-        dev = self.fmean.device
-        self.fmean = torch.tensor(fm, dtype=torch.float32, device=dev)
-        self.finv = torch.tensor(1.0 / fs, dtype=torch.float32, device=dev)
-        self.tmean = torch.tensor(tm, dtype=torch.float32, device=dev)
-        self.tstd = torch.tensor(ts, dtype=torch.float32, device=dev)
-        w = np.zeros(self.n_out)
-        w[:used_out] = 1.0
-        self.w_out = torch.tensor(w, dtype=torch.float32, device=dev)
-        Xn = ((X - fm) / fs).astype(np.float32)
-        Xn[:, 2 * self.n + 2:] = 0.0
-        Tn = ((T - tm) / ts).astype(np.float32)
-        return Xn, Tn
+        X = torch.cat([r[0] for r in self.records])
+        T = torch.cat([r[1] for r in self.records])
+        nf, used_out = 2 * self.n + 2, self.g_max * self.n
+        fm, finv, _ = mri_learned_moments(X, nf, 1e-12)
+        tm, tinv, ts = mri_learned_moments(T, used_out, 1e-30)
+        dev = X.device
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.fmean, self.finv = torch.zeros(self.n_in, **f32), torch.ones(self.n_in, **f32)
+        self.fmean[:nf].copy_(fm)
+        self.finv[:nf].copy_(finv)
+        self.tmean, self.tstd = torch.zeros(self.n_out, **f32), torch.ones(self.n_out, **f32)
+        self.tmean[:used_out].copy_(tm)
+        self.tstd[:used_out].copy_(ts)
+        self._tinv = torch.ones(self.n_out, **f32)
+        self._tinv[:used_out].copy_(tinv)
+        self.w_out = torch.zeros(self.n_out, **f32)
+        self.w_out[:used_out] = 1.0
+        return X, T
 
     # ------------------------------------------------------------------ training
     def fit(self, epochs=100, lr=1e-3, seed=0, stream=None, log=None):
-        """Adam on minibatches of the collected examples (shuffled once on the host).
-        Returns the loss history (one value per epoch, the last minibatch's)."""
+        """Adam on minibatches of the collected examples, standardised and shuffled (once,
+        with a seeded permutation) on the device.  Returns the loss history (one value per
+        epoch, the last minibatch's)."""
         import torch
-        Xn, Tn = self._standardise()
-        rng = np.random.default_rng(seed)
-        perm = rng.permutation(Xn.shape[0])
-        nb = Xn.shape[0] // self.batch
+        X, T = self._standardise()
+        N = X.shape[0]
+        nb = N // self.batch
         if nb < 1:
             raise ValueError("fewer examples than one minibatch")
-        dev = self.fmean.device
-        X = torch.tensor(Xn[perm[:nb * self.batch]], device=dev).view(nb, self.batch, -1)
-        T = torch.tensor(Tn[perm[:nb * self.batch]], device=dev).view(nb, self.batch, -1)
+        dev = X.device
+        perm = torch.tensor(np.random.default_rng(seed).permutation(N)[:nb * self.batch].astype(np.int32), device=dev)
+        Xn = torch.empty((nb * self.batch, self.n_in), dtype=torch.float32, device=dev)
+        Tn = torch.empty((nb * self.batch, self.n_out), dtype=torch.float32, device=dev)
+        mri_learned_standardise(X, perm, 2 * self.n + 2, self.fmean, self.finv, Xn, stream=stream)
+        mri_learned_standardise(T, perm, self.g_max * self.n, self.tmean, self._tinv, Tn, stream=stream)
+        Xb = Xn.view(nb, self.batch, -1)
+        Tb = Tn.view(nb, self.batch, -1)
         y = torch.empty((self.batch, self.n_out), dtype=torch.float32, device=dev)
         loss = torch.zeros(1, dtype=torch.float32, device=dev)
         hist = []
         for ep in range(epochs):
             rate = lr * 0.5 * (1.0 + math.cos(math.pi * ep / epochs))    # cosine decay
             for b in range(nb):
-                mri_mlp_grad(self.net, X[b], T[b], self.w_out, y, loss, stream=stream)
+                mri_mlp_grad(self.net, Xb[b], Tb[b], self.w_out, y, loss, stream=stream)
                 self.step += 1
                 mri_mlp_adam(self.net, rate, self.step, stream=stream)
             hist.append(float(loss.item()))
@@ -201,37 +209,48 @@ class LearnedSteps:
 
     def add(self, y_in, p, phi, Hstage, h, accepted):
         """One stage's examples: the stage inputs and the accepted step counts of an
-        adaptive solve of it (cell_stats[:, 0], host or device)."""
+        adaptive solve of it (int32, device or host: cell_stats[:, 0] or a whole
+        cell_stats [ncell][4] tensor)."""
         import torch
         ncell = y_in.shape[0]
-        x = torch.empty((ncell, self.n_in), dtype=torch.float32, device=y_in.device)
-        zero = torch.zeros(self.n_in, dtype=torch.float32, device=y_in.device)
-        one = torch.ones(self.n_in, dtype=torch.float32, device=y_in.device)
+        dev = y_in.device
+        x = torch.empty((ncell, self.n_in), dtype=torch.float32, device=dev)
+        zero = torch.zeros(self.n_in, dtype=torch.float32, device=dev)
+        one = torch.ones(self.n_in, dtype=torch.float32, device=dev)
         mri_learned_features(y_in, p, phi, Hstage, zero, one, x)
-        acc = accepted.cpu().numpy() if hasattr(accepted, "cpu") else np.asarray(accepted)
-        k = np.log2(n_substeps(Hstage, h) / np.maximum(acc, 1).astype(np.float64))
+        if not torch.is_tensor(accepted):
+            accepted = torch.tensor(np.asarray(accepted), dtype=torch.int32, device=dev)
+        stride = 4 if accepted.dim() == 2 else 1
+        acc = accepted.to(device=dev, dtype=torch.int32).contiguous()
+        k = torch.empty((ncell, 1), dtype=torch.float32, device=dev)
+        mri_learned_step_targets(acc, n_substeps(Hstage, h), k, stride=stride)
         self.records.append((x, k))
 
     def fit(self, epochs=100, lr=1e-3, seed=0, stream=None):
+        """Adam on the collected examples, standardised and shuffled on the device."""
         import torch
-        X = torch.cat([r[0] for r in self.records]).cpu().numpy().astype(np.float64)
-        k = np.concatenate([r[1] for r in self.records])
-        fm, fs = X.mean(0), X.std(0)
-        fs[fs < 1e-12] = 1.0
-        self.kmean, self.kstd = float(k.mean()), float(max(k.std(), 1e-6))
-        dev = self.fmean.device
-        self.fmean = torch.tensor(fm, dtype=torch.float32, device=dev)
-        self.finv = torch.tensor(1.0 / fs, dtype=torch.float32, device=dev)
-        Xn = ((X - fm) / fs).astype(np.float32)
-        Xn[:, 2 * self.n + 2:] = 0.0
-        Tn = np.zeros((Xn.shape[0], self.n_out), dtype=np.float32)
-        Tn[:, 0] = (k - self.kmean) / self.kstd
-        perm = np.random.default_rng(seed).permutation(Xn.shape[0])
-        nb = Xn.shape[0] // self.batch
+        X = torch.cat([r[0] for r in self.records])
+        K = torch.cat([r[1] for r in self.records])
+        nf = 2 * self.n + 2
+        dev = X.device
+        fm, finv, _ = mri_learned_moments(X, nf, 1e-12)
+        km, kinv, ks = mri_learned_moments(K, 1, 1e-6)
+        self.fmean = torch.zeros(self.n_in, dtype=torch.float32, device=dev)
+        self.finv = torch.ones(self.n_in, dtype=torch.float32, device=dev)
+        self.fmean[:nf].copy_(fm)
+        self.finv[:nf].copy_(finv)
+        self.kmean, self.kstd = float(km.item()), float(ks.item())
+        N = X.shape[0]
+        nb = N // self.batch
         if nb < 1:
             raise ValueError("fewer examples than one minibatch")
-        Xd = torch.tensor(Xn[perm[:nb * self.batch]], device=dev).view(nb, self.batch, -1)
-        Td = torch.tensor(Tn[perm[:nb * self.batch]], device=dev).view(nb, self.batch, -1)
+        perm = torch.tensor(np.random.default_rng(seed).permutation(N)[:nb * self.batch].astype(np.int32), device=dev)
+        Xd = torch.empty((nb * self.batch, self.n_in), dtype=torch.float32, device=dev)
+        Td = torch.empty((nb * self.batch, self.n_out), dtype=torch.float32, device=dev)
+        mri_learned_standardise(X, perm, nf, self.fmean, self.finv, Xd, stream=stream)
+        mri_learned_standardise(K, perm, 1, km, kinv, Td, stream=stream)
+        Xd = Xd.view(nb, self.batch, -1)
+        Td = Td.view(nb, self.batch, -1)
         y = torch.empty((self.batch, self.n_out), dtype=torch.float32, device=dev)
         loss = torch.zeros(1, dtype=torch.float32, device=dev)
         hist = []

@@ -69,13 +69,20 @@ FLOPS_PER_TRANSCENDENTAL = 20.0
 # launches; traffic grows with the cells processed, so a launch over `cells` moves
 # cells times this).  None: the kernel changed since the capture.
 STAGE_DRAM_BYTES_PER_CELL = {0: None, 1: None}
+# forms timed without the Newton-matrix cache (the learned form's comparison: without the
+# cache's f^F no derivative predicts the first SDIRK stage of a call, which is where the
+# network's prediction is used)
+NO_CACHE = {"nocache", "learned_front"}
 FORM_NAMES = {"plain": "plain FP64", "mixed": "mixed: FP32 Newton matrix and LU, FP64 rates, residual and update",
               "learned": "learned: mixed form with Newton started from a bf16 MLP's prediction where the "
                          "predictor has none",
               "batched": "batched: mixed form, autotuned shape/solve layout/schedule, device work queue, "
                          "IMEX step graph-captured",
               "static": "batched with the static cell-to-warp mapping instead of the work queue",
-              "plain_imex": "plain FP64 in the same IMEX step"}
+              "plain_imex": "plain FP64 in the same IMEX step",
+              "nocache": "batched without the Newton-matrix cache",
+              "learned_front": "batched without the cache, first SDIRK stage of each call started from the "
+                               "network's prediction"}
 
 
 # ----------------------------------------------------------------------------- flop model
@@ -308,7 +315,7 @@ class Case:
                                           newton_safety=3e-4 if prec == 0 else self.args.tuned_newton_safety)
         if form == "static":
             o.schedule = mri.MRI_SCHED_STATIC
-        cache = self.cache.get(prec)
+        cache = None if form in NO_CACHE else self.cache.get(prec)
         return o if cache is None else mri.with_matrix_cache(o, cache)
 
     def new_cache(self, prec):
@@ -371,7 +378,7 @@ class Case:
 
     # -------------------------------------------------------------- IMEX step, call by call
 
-    def imex2_step(self, y, form, first=False, ev=None, gate=None, ws=None):
+    def imex2_step(self, y, form, first=False, ev=None, gate=None, ws=None, model=None):
         """The second-order Strang-split IMEX multirate step composed from the public
         calls (the sequence mri_step_imex2 runs): a Crank-Nicolson half step of the
         diffusion, (I - (H/4) L) y* = (I + (H/4) L) y by Jacobi-PCG, the MRI3 step with
@@ -398,14 +405,46 @@ class Case:
                 self._end(ev, e0)
                 gate.before(y, self.phi, Hs, ramp)
                 e0 = self._rec(ev)
-            mri.mri_stage_fast(y, self.p, self.phi, 0.0, Hs, w.h, self.mech, o, cell_status=self.status,
-                               cell_stats=self.stats, n_failed=self.nfail, stream=st)
+            if model is None:
+                mri.mri_stage_fast(y, self.p, self.phi, 0.0, Hs, w.h, self.mech, o, cell_status=self.status,
+                                   cell_stats=self.stats, n_failed=self.nfail, stream=st)
+            else:
+                guess = model.guess(y, self.p, self.phi, Hs, w.h, stream=st)
+                mri.mri_stage_fast_guided(y, self.p, self.phi, 0.0, Hs, w.h, self.mech, o,
+                                          start=mri.MRI_START_GUESS_FIRST, guess=guess, cell_status=self.status,
+                                          cell_stats=self.stats, n_failed=self.nfail, n_fallback=self.nfallback,
+                                          stream=st)
             self._end(ev, e0, stage=True)
             if gate is not None:
                 gate.after(y)
             e0 = self._rec(ev)
         half()
         self._end(ev, e0)
+
+    def imex2_training_step(self, y, model, ws):
+        """One IMEX step whose fast stages run a substep at a time with the plain solver
+        (mixed form), recording each stage's (input, substep-end states) as training
+        examples of the learned form."""
+        from paper_2211_03293_gb300.learned import stage_substep_states
+        mri, c, G, w, torch = self.mri, self.c, self.G, self.w, self.torch
+        a = 0.25 * w.H
+        fI, rhs, cws, info = ws
+
+        def half():
+            mri.mri_slow_rhs(y, fI, self.gridI)
+            torch.add(y, fI, alpha=a, out=rhs)
+            mri.mri_diffusion_solve(y, rhs, self.gridI, a, cws, tol=self.args.cg_tol, max_iter=self.args.cg_iters,
+                                    check_every=0, cg_info=info)
+        half()
+        for i in range(1, 4):
+            mri.mri_slow_rhs(y, self.fS[i - 1], self.gridE)
+            mri.mri_stage_forcing(self.fS, i, G[i], self.phi)
+            Hs = (c[i] - c[i - 1]) * w.H
+            y_in = y.clone()
+            seq, _ = stage_substep_states(y, self.p, self.phi, Hs, w.h, self.mech, self.opts("mixed"))
+            model.add(y_in, self.p, self.phi.clone(), Hs, seq)
+            del seq, y_in
+        half()
 
     def imex_ws(self):
         torch = self.torch
@@ -745,8 +784,53 @@ def run_front128(args, world, peak):
         r["roofline"] = roofline(case, r, peak)
         r["nsteps"] = args.big_steps
         res[form] = r
+    if args.learned:
+        res.update(front_learned(case, args, y_warm, ws, step, peak, world))
     cg = diffusion_cg(case, args)
     return res, cg
+
+
+def front_learned(case, args, y_warm, ws, step, peak, world):
+    """The learned form on the flame front: a network trained on the substep-end states
+    of one IMEX step of the front (6.3M examples) starts Newton at the first SDIRK stage
+    of every call, the stage the analytic predictor has no derivative for when no
+    Newton-matrix cache keeps f^F between calls; timed against the same step without
+    the cache and without the network, every stage gated."""
+    from paper_2211_03293_gb300.learned import LearnedStart
+    torch = case.torch
+    t0 = time.time()
+    model = LearnedStart(case.n, g_max=5, batch=4096, infer_batch=1 << 16)
+    y = y_warm.clone()
+    case.tuned["mixed"] = case.tuned["batched"]
+    case.imex2_training_step(y, model, ws)
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    hist = model.fit(epochs=args.front_learn_epochs, lr=2e-3)
+    torch.cuda.synchronize()
+    learn = {"examples": int(sum(r[0].shape[0] for r in model.records)), "epochs": args.front_learn_epochs,
+             "loss_first": hist[0], "loss_last": hist[-1], "data_s": round(t_data, 2),
+             "train_s": round(time.time() - t0 - t_data, 2), "network": model.dims}
+    model.records = []
+    out = {}
+    for form in ("nocache", "learned_front"):
+        case.tuned[form] = case.tuned["batched"]
+        y = y_warm.clone()
+        m = model if form == "learned_front" else None
+        warm(case, form, y, 1, step, ramp_first=False, model=m)
+        r = case.timed_steps(y, form, args.big_steps, step, model=m, world=world)
+        r["form"] = form
+        r["spread"] = spread(r.pop("per_cell"))
+        (r["value"],), _ = whole_job_rates([r["ms"]], [r["substeps"]], world, case.dev)
+        r["e2e_value"] = None
+        r["e2e"] = None
+        r["roofline"] = roofline(case, r, peak)
+        r["nsteps"] = args.big_steps
+        if m is not None:
+            r["learn"] = learn
+        out[form] = r
+    base, lr = out["nocache"], out["learned_front"]
+    lr["newton_saved"] = 1.0 - lr["newton"] / max(base["newton"], 1)
+    return out
 
 
 def diffusion_cg(case, args):
@@ -994,6 +1078,7 @@ def main():
     ap.add_argument("--big-steps", type=int, default=1, help="timed steps of the box64 and front128 workloads")
     ap.add_argument("--cg-tol", type=float, default=1e-12, help="tolerance of the IMEX step's diffusion solves")
     ap.add_argument("--cg-iters", type=int, default=30, help="iteration cap of the IMEX step's diffusion solves")
+    ap.add_argument("--front-learn-epochs", type=int, default=4, help="training epochs of the learned form on front128")
     args = ap.parse_args()
     rank, world = dist_init(args)
 

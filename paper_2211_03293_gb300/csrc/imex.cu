@@ -27,6 +27,7 @@ constexpr int kPassThreads = 256;   // threads of a fused pass (at least one war
 constexpr int kPassMax = 1024;      // n <= 1024: one slot of up to 1024 threads
 constexpr int kScalThreads = 1024;  // the scalar kernels: one warp per component at a time
 constexpr int kDirBlocks = 2432;    // blocks of the direction update (16 per SM)
+constexpr int kUnroll = 4;          // cells of a thread's sequence loaded together in the passes
 
 struct Lap7 {
   int nx, ny, nz, n;
@@ -128,19 +129,32 @@ __global__ void __launch_bounds__(kPassMax) apply_pass_kernel(const double* __re
   const int q = threadIdx.x % rt, slot = threadIdx.x / rt, S = blockDim.x / rt;
   const long long ncell = (long long)s.nx * s.ny * s.nz;
   double a1 = 0.0, a2 = 0.0;
+  const long long stride = (long long)gridDim.x * S;
   if (q < s.n)
-    for (long long c = (long long)blockIdx.x * S + slot; c < ncell; c += (long long)gridDim.x * S) {
-      const double ax = apply_at(x, s, c, q);
-      const long long e = c * s.n + q;
-      if (MODE == 0) {
-        const double bv = bvec[e];
-        const double rr = bv - ax;
-        out[e] = rr;
-        a1 = fma(rr, rr, a1);
-        a2 = fma(bv, bv, a2);
-      } else {
-        out[e] = ax;
-        a1 = fma(x[e], ax, a1);
+    for (long long c0 = (long long)blockIdx.x * S + slot; c0 < ncell; c0 += kUnroll * stride) {
+      // kUnroll cells of the thread's sequence at once: their loads are in flight
+      // together; the sums still run over the cells in sequence order
+      double ax[kUnroll], xv[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const long long c = c0 + u * stride;
+        ax[u] = (c < ncell) ? apply_at(x, s, c, q) : 0.0;
+        xv[u] = (c < ncell) ? (MODE == 0 ? bvec[c * s.n + q] : x[c * s.n + q]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const long long c = c0 + u * stride;
+        if (c >= ncell) break;
+        const long long e = c * s.n + q;
+        if (MODE == 0) {
+          const double rr = xv[u] - ax[u];
+          out[e] = rr;
+          a1 = fma(rr, rr, a1);
+          a2 = fma(xv[u], xv[u], a2);
+        } else {
+          out[e] = ax[u];
+          a1 = fma(xv[u], ax[u], a1);
+        }
       }
     }
   block_partial(a1, s.n, rt, part1);
@@ -171,12 +185,29 @@ __global__ void __launch_bounds__(kPassMax) update_pass_kernel(double* __restric
   double acc = 0.0;
   if (q < n && !sc[q].done) {
     const double al = sc[q].alpha;
-    for (long long c = (long long)blockIdx.x * S + slot; c < ncell; c += (long long)gridDim.x * S) {
-      const long long e = c * n + q;
-      x[e] = fma(al, p[e], x[e]);
-      const double rr = fma(-al, Ap[e], r[e]);
-      r[e] = rr;
-      acc = fma(rr, rr, acc);
+    const long long stride = (long long)gridDim.x * S;
+    for (long long c0 = (long long)blockIdx.x * S + slot; c0 < ncell; c0 += kUnroll * stride) {
+      double pv[kUnroll], xv[kUnroll], av[kUnroll], rv[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const long long c = c0 + u * stride;
+        const long long e = c * n + q;
+        const bool in = c < ncell;
+        pv[u] = in ? p[e] : 0.0;
+        xv[u] = in ? x[e] : 0.0;
+        av[u] = in ? Ap[e] : 0.0;
+        rv[u] = in ? r[e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const long long c = c0 + u * stride;
+        if (c >= ncell) break;
+        const long long e = c * n + q;
+        x[e] = fma(al, pv[u], xv[u]);
+        const double rr = fma(-al, av[u], rv[u]);
+        r[e] = rr;
+        acc = fma(rr, rr, acc);
+      }
     }
   }
   block_partial(acc, n, rt, part);
@@ -217,9 +248,22 @@ __global__ void __launch_bounds__(kPassMax) dir_kernel(double* __restrict__ p, c
   if (q >= n) return;
   if (!START && sc[q].done) return;
   const double beta = START ? 0.0 : sc[q].beta;
-  for (long long c = (long long)blockIdx.x * S + slot; c < ncell; c += (long long)gridDim.x * S) {
-    const long long e = c * n + q;
-    p[e] = START ? r[e] * inv_diag : fma(beta, p[e], r[e] * inv_diag);
+  const long long stride = (long long)gridDim.x * S;
+  for (long long c0 = (long long)blockIdx.x * S + slot; c0 < ncell; c0 += kUnroll * stride) {
+    double rv[kUnroll], pv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const long long c = c0 + u * stride;
+      const bool in = c < ncell;
+      rv[u] = in ? r[c * n + q] : 0.0;
+      pv[u] = (in && !START) ? p[c * n + q] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const long long c = c0 + u * stride;
+      if (c >= ncell) break;
+      p[c * n + q] = START ? rv[u] * inv_diag : fma(beta, pv[u], rv[u] * inv_diag);
+    }
   }
 }
 

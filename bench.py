@@ -312,7 +312,7 @@ class Case:
         else:
             o = mri.mri_fast_opts_default(method=self.w.method, newton_rtol=self.w.newton_rtol, ramp=ramp,
                                           jac_policy=mri.MRI_JAC_LAZY, precision=prec,
-                                          newton_safety=3e-4 if prec == 0 else self.args.tuned_newton_safety)
+                                          newton_safety=self.args.newton_safety)
         if form == "static":
             o.schedule = mri.MRI_SCHED_STATIC
         cache = None if form in NO_CACHE else self.cache.get(prec)
@@ -784,10 +784,12 @@ def run_front128(args, world, peak):
         r["roofline"] = roofline(case, r, peak)
         r["nsteps"] = args.big_steps
         res[form] = r
+    model = None
     if args.learned:
         res.update(front_learned(case, args, y_warm, ws, step, peak, world))
+        model = res.pop("_model")
     cg = diffusion_cg(case, args)
-    return res, cg
+    return res, cg, model
 
 
 def front_learned(case, args, y_warm, ws, step, peak, world):
@@ -830,6 +832,32 @@ def front_learned(case, args, y_warm, ws, step, peak, world):
         out[form] = r
     base, lr = out["nocache"], out["learned_front"]
     lr["newton_saved"] = 1.0 - lr["newton"] / max(base["newton"], 1)
+    out["_model"] = model
+    return out
+
+
+def run_front256(args, world, peak, model):
+    """The learned form's 256^3 variant of the flame front (16.8M cells): one MRI3 step
+    of the mixed form warms the field up; then one fast stage is timed without the
+    Newton-matrix cache (at 16.8M cells a cache would hold 123 GB) with and without the
+    network's start (trained on the 128^3 front), every timed stage gated."""
+    case = Case("front128", args, cells_per_side=256)
+    torch = case.torch
+    y = torch.tensor(case.w.y0, device=case.dev)
+    warm(case, "nocache", y, 1, case.mri3_step)
+    out = {}
+    for form in ("nocache", "learned_front"):
+        m = model if form == "learned_front" else None
+        yy = y.clone()
+        r = case.timed_steps(yy, form, 1, lambda yv, f, **kw: case.mri3_step(yv, f, **kw), model=m, world=world)
+        r["form"] = form
+        r["spread"] = spread(r.pop("per_cell"))
+        (r["value"],), _ = whole_job_rates([r["ms"]], [r["substeps"]], world, case.dev)
+        r["e2e_value"], r["e2e"] = None, None
+        r["roofline"] = roofline(case, r, peak)
+        r["nsteps"] = 1
+        out[form] = r
+    out["learned_front"]["newton_saved"] = 1.0 - out["learned_front"]["newton"] / max(out["nocache"]["newton"], 1)
     return out
 
 
@@ -1063,8 +1091,10 @@ def main():
     ap.add_argument("--cells-per-side", type=int, default=None,
                     help="shrink the headline box (profiling captures only; the bench line is for 32^3)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling captures)")
-    ap.add_argument("--tuned-newton-safety", type=float, default=3e-2,
-                    help="mri_fast_opts.newton_safety of the tuned forms (the plain form keeps 3e-4)")
+    ap.add_argument("--newton-safety", type=float, default=3e-2,
+                    help="mri_fast_opts.newton_safety of every form (the library's default, 3e-4, keeps whole MRI "
+                         "steps within 1e-10 of a full-Newton solution; 3e-2 keeps every accepted iterate inside the "
+                         "Newton tolerance, far inside the gate's 1e-6)")
     ap.add_argument("--form", default=None, choices=["plain", "mixed", "learned"],
                     help="time one form of the headline workload only")
     ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip the learned form")
@@ -1079,6 +1109,10 @@ def main():
     ap.add_argument("--cg-tol", type=float, default=1e-12, help="tolerance of the IMEX step's diffusion solves")
     ap.add_argument("--cg-iters", type=int, default=30, help="iteration cap of the IMEX step's diffusion solves")
     ap.add_argument("--front-learn-epochs", type=int, default=4, help="training epochs of the learned form on front128")
+    ap.add_argument("--profile-cg", type=int, default=0,
+                    help="profiling captures only: time the diffusion solve alone on an N^3 front and exit")
+    ap.add_argument("--front256", action="store_true",
+                    help="also time the learned form's 256^3 variant of the front (16.8M cells, a few minutes)")
     args = ap.parse_args()
     rank, world = dist_init(args)
 
@@ -1099,11 +1133,19 @@ def main():
     peak = 2.0 * mri.mri_probe_fp64_fma(probe, iters=4096) / 1e12
     del probe
 
+    if args.profile_cg:
+        # profiling captures only: the diffusion solve alone on a smaller front (no bench line)
+        c = Case("front128", args, cells_per_side=args.profile_cg)
+        print(json.dumps({"profile_cg": diffusion_cg(c, args)}))
+        return
     case, box = run_box32(args, world, peak)
     extra = {}
     if args.configs:
         extra["box64"] = run_box64(args, world, peak)
-        extra["front128"], extra["diffusion_cg_front128"] = run_front128(args, world, peak)
+        extra["front128"], extra["diffusion_cg_front128"], model = run_front128(args, world, peak)
+        if args.front256 and model is not None:
+            torch.cuda.empty_cache()
+            extra["front256"] = run_front256(args, world, peak, model)
         extra["diffusion_cg_box32"] = diffusion_cg(case, args)
         extra["reactor_batch"] = reactor_batch(args)
     if rank != 0:
@@ -1137,6 +1179,8 @@ def main():
     if args.configs:
         summary += [summary_row("box64", f, extra["box64"][f]) for f in extra["box64"]]
         summary += [summary_row("front128", f, extra["front128"][f]) for f in extra["front128"]]
+        if "front256" in extra:
+            summary += [summary_row("front256", f, extra["front256"][f]) for f in extra["front256"]]
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
@@ -1163,6 +1207,8 @@ def main():
     if args.configs:
         line["box64"] = detail(extra["box64"])
         line["front128"] = detail(extra["front128"])
+        if "front256" in extra:
+            line["front256"] = detail(extra["front256"])
         line["diffusion_cg"] = {"front128": extra["diffusion_cg_front128"], "box32": extra["diffusion_cg_box32"]}
         line["reactor_batch"] = extra["reactor_batch"]
     line["summary"] = summary       # last, so that it survives a truncated tail

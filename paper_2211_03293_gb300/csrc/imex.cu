@@ -22,7 +22,7 @@
 namespace mri {
 namespace {
 
-constexpr int kRedBlocks = 512;     // blocks of the fused passes (partial sums per block)
+constexpr int kRedBlocks = 1024;    // blocks of the fused passes at most (partial sums per block)
 constexpr int kPassThreads = 256;   // threads of a fused pass (at least one warp per component)
 constexpr int kPassMax = 1024;      // n <= 1024: one slot of up to 1024 threads
 constexpr int kScalThreads = 1024;  // the scalar kernels: one warp per component at a time
@@ -32,7 +32,20 @@ constexpr int kUnroll = 4;          // cells of a thread's sequence loaded toget
 struct Lap7 {
   int nx, ny, nz, n;
   double centre, w[3];   // operator A = I - a L: centre weight and the neighbour weight per axis
+  long long st[3];       // element strides of the axes: n, nx n, nx ny n
+  long long wrap[3];     // element distance from the first to the last cell of an axis: (N - 1) stride
+  unsigned mx, my;       // ceil(2^32 / nx), ceil(2^32 / ny) for the division by nx and ny (0 when 1)
 };
+
+// a / d for a < 2^31 with m = ceil(2^32 / d), d >= 2: the product's high word is the
+// quotient or one more (a m / 2^32 exceeds a / d by less than 1/2), corrected by the sign
+// of the remainder
+__device__ __forceinline__ unsigned div_magic(unsigned a, unsigned d, unsigned m) {
+  if (m == 0) return a;                       // d == 1
+  unsigned q = __umulhi(a, m);
+  if ((int)(a - q * d) < 0) --q;
+  return q;
+}
 
 // Device-side progress of one solve: finished (every component converged) and the
 // iterations taken.
@@ -47,28 +60,31 @@ struct CgScal {          // per component
   int done;
 };
 
-// (A x)[cell][q] for the 7-point operator.  The cell's grid coordinates come from 32-bit
-// unsigned division (grids hold at most 2^31 - 1 cells), several times cheaper than the
-// 64-bit form on a pass that touches every element.
+// (A x)[cell][q] for the 7-point operator.  The cell's grid coordinates come from a
+// multiply-high division (grids hold at most 2^31 - 1 cells) and the neighbours from the
+// element strides of the axes, with a wrap at the periodic boundary.
 __device__ __forceinline__ double apply_at(const double* __restrict__ x, const Lap7& s, long long cell, int q) {
-  const unsigned cc = (unsigned)cell, nx = (unsigned)s.nx, ny = (unsigned)s.ny;
-  const unsigned row = cc / nx;
-  const int i = (int)(cc - row * nx), j = (int)(row % ny), k = (int)(row / ny);
-  double acc = s.centre * x[cell * s.n + q];
+  const unsigned cc = (unsigned)cell;
+  const unsigned row = div_magic(cc, (unsigned)s.nx, s.mx);
+  const unsigned i = cc - row * (unsigned)s.nx;
+  const unsigned k = div_magic(row, (unsigned)s.ny, s.my);
+  const unsigned j = row - k * (unsigned)s.ny;
+  const long long e = cell * s.n + q;
+  double acc = s.centre * x[e];
   if (s.nx > 1) {
-    const int ip = (i + 1 == s.nx) ? 0 : i + 1, im = (i == 0) ? s.nx - 1 : i - 1;
-    acc = fma(s.w[0], x[(((long long)k * s.ny + j) * s.nx + ip) * s.n + q] +
-                          x[(((long long)k * s.ny + j) * s.nx + im) * s.n + q], acc);
+    const long long ep = e + ((i + 1 == (unsigned)s.nx) ? -s.wrap[0] : s.st[0]);
+    const long long em = e + ((i == 0) ? s.wrap[0] : -s.st[0]);
+    acc = fma(s.w[0], x[ep] + x[em], acc);
   }
   if (s.ny > 1) {
-    const int jp = (j + 1 == s.ny) ? 0 : j + 1, jm = (j == 0) ? s.ny - 1 : j - 1;
-    acc = fma(s.w[1], x[(((long long)k * s.ny + jp) * s.nx + i) * s.n + q] +
-                          x[(((long long)k * s.ny + jm) * s.nx + i) * s.n + q], acc);
+    const long long ep = e + ((j + 1 == (unsigned)s.ny) ? -s.wrap[1] : s.st[1]);
+    const long long em = e + ((j == 0) ? s.wrap[1] : -s.st[1]);
+    acc = fma(s.w[1], x[ep] + x[em], acc);
   }
   if (s.nz > 1) {
-    const int kp = (k + 1 == s.nz) ? 0 : k + 1, km = (k == 0) ? s.nz - 1 : k - 1;
-    acc = fma(s.w[2], x[(((long long)kp * s.ny + j) * s.nx + i) * s.n + q] +
-                          x[(((long long)km * s.ny + j) * s.nx + i) * s.n + q], acc);
+    const long long ep = e + ((k + 1 == (unsigned)s.nz) ? -s.wrap[2] : s.st[2]);
+    const long long em = e + ((k == 0) ? s.wrap[2] : -s.st[2]);
+    acc = fma(s.w[2], x[ep] + x[em], acc);
   }
   return acc;
 }
@@ -326,6 +342,14 @@ int elementwise_blocks(long long len) {
 Lap7 make_op(const mri_grid* g, int n, double a) {
   Lap7 s{};
   s.nx = g->nx; s.ny = g->ny; s.nz = g->nz; s.n = n;
+  s.st[0] = n;
+  s.st[1] = (long long)g->nx * n;
+  s.st[2] = (long long)g->nx * g->ny * n;
+  s.wrap[0] = (long long)(g->nx - 1) * s.st[0];
+  s.wrap[1] = (long long)(g->ny - 1) * s.st[1];
+  s.wrap[2] = (long long)(g->nz - 1) * s.st[2];
+  s.mx = g->nx > 1 ? (unsigned)(((1ull << 32) + g->nx - 1) / g->nx) : 0u;
+  s.my = g->ny > 1 ? (unsigned)(((1ull << 32) + g->ny - 1) / g->ny) : 0u;
   const int N[3] = {g->nx, g->ny, g->nz};
   const double c = g->D / (g->dx * g->dx);
   s.centre = 1.0;
@@ -365,8 +389,16 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
   const int rt = ((n + 31) / 32) * 32;
   const int S = rt < kPassThreads ? kPassThreads / rt : 1;
   const int pt = S * rt;                                   // threads of a fused pass
+  // one wave of the fused passes: as many blocks as stay resident together (at most
+  // kRedBlocks, the partial-sum slots), so no block of a pass waits for a second wave
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_pass_kernel<1>, pt, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  long long resident = (long long)per_sm * device_sm_count();
+  if (resident > kRedBlocks) resident = kRedBlocks;
   const long long want = (ncell + S - 1) / S;
-  const int nblk = (int)(want < kRedBlocks ? want : kRedBlocks);
+  const int nblk = (int)(want < resident ? want : resident);
   if (iters) *iters = 0;
   apply_pass_kernel<0><<<nblk, pt, 0, st>>>(x, b, r, op, rt, part1, part2, nullptr, nullptr);
   cg_init_kernel<<<1, kScalThreads, 0, st>>>(part1, part2, nblk, n, inv_diag, tol, sc, cs);

@@ -817,7 +817,7 @@ def run_front128(args, world, peak):
     if args.learned:
         res.update(front_learned(case, args, y_warm, ws, step, peak, world))
         model = res.pop("_model")
-    cg = diffusion_cg(case, args)
+    cg = diffusion_cg(case, args, peak)
     return res, cg, model
 
 
@@ -890,10 +890,12 @@ def run_front256(args, world, peak, model):
     return out
 
 
-def diffusion_cg(case, args):
+def diffusion_cg(case, args, peak):
     """The Jacobi-PCG diffusion solve alone: (I - a D lap_h) x = b on the workload's state
     with a D / dx^2 = 1, iterations fixed at the converged count, replayed from a CUDA
-    graph, against the HBM roofline."""
+    graph.  Its roofline: 21 FP64 flops per element and iteration against the FP64 peak
+    (peak, TFLOP/s) and 11 doubles moved against the HBM copy bandwidth; on GB300 the
+    FP64 floor is the higher one, so the FP64 fraction is the bound reported."""
     torch, mri, st = case.torch, case.mri, None
     g = case.w.grid
     a = g["dx"] ** 2 / g["D"]
@@ -930,14 +932,26 @@ def diffusion_cg(case, args):
     avg = sum(ms) / len(ms)
     nbytes = ncell * n * 8
     traffic = nbytes * (2 + 5 + its * 11)      # copy of x, the start (r = b - A x, p), 11 doubles per iteration
-    hbm = measured_hbm_gbs()
+    # FP64 flops per element: the start 16 (stencil 10, residual 1, two sums 4, direction 1);
+    # per iteration 21 (stencil 10 and the p.Ap sum 2, x and r updates and the r.r sum 6,
+    # direction 3)
+    flops = ncell * n * (16 + its * 21)
+    hbm, hbm_basis = measured_hbm_gbs(), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    if hbm is None:
+        hbm, hbm_basis = HBM_FALLBACK_GBS, "of fallback (MEASURED_PEAKS.json absent: 6.8 TB/s, an earlier GB300 copy)"
+    gbs = traffic / (avg * 1e-3) / 1e9
+    tflops = flops / (avg * 1e-3) / 1e12
     return {"workload": case.name, "iterations": its, "ms": avg, "ms_direct": sum(ms_direct) / len(ms_direct),
             "us_per_iteration": 1e3 * avg / its,
-            "roofline": {"bound": "hbm", "achieved": traffic / (avg * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                         "frac": traffic / (avg * 1e-3) / 1e9 / hbm if hbm else None, "traffic": None,
-                         "basis": "11 doubles moved per element and iteration (stencil pass with the p.Ap "
-                                  "sums 2, x/r update with the r.r sums 6, direction 3) plus the start and the "
-                                  "copy of x; peak: MEASURED_PEAKS.json hbm_gbs"}}
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                         "traffic": None,
+                         "basis": "21 FP64 flops per element and iteration; peak: the FP64 FMA rate measured in "
+                                  "this run (the FP64 floor, flops / peak, is above the HBM floor, bytes / "
+                                  "bandwidth)",
+                         "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                 "basis": "11 doubles moved per element and iteration (stencil pass with the "
+                                          "p.Ap sums 2, x/r update with the r.r sums 6, direction 3) plus the "
+                                          "start and the copy of x; peak " + hbm_basis}}}
 
 
 def reactor_batch(args):
@@ -1003,6 +1017,11 @@ def reactor_batch(args):
     out["groups"] = per
     out["sum_of_groups_alone_ms"] = sum(g["ms_alone"] for g in per)
     return out
+
+
+# HBM copy bandwidth when MEASURED_PEAKS.json is absent: one earlier STREAM-style copy
+# on a GB300
+HBM_FALLBACK_GBS = 6800.0
 
 
 def measured_hbm_gbs():
@@ -1165,7 +1184,7 @@ def main():
     if args.profile_cg:
         # profiling captures only: the diffusion solve alone on a smaller front (no bench line)
         c = Case("front128", args, cells_per_side=args.profile_cg)
-        print(json.dumps({"profile_cg": diffusion_cg(c, args)}))
+        print(json.dumps({"profile_cg": diffusion_cg(c, args, peak)}))
         return
     case, box = run_box32(args, world, peak)
     extra = {}
@@ -1175,7 +1194,7 @@ def main():
         if args.front256 and model is not None:
             torch.cuda.empty_cache()
             extra["front256"] = run_front256(args, world, peak, model)
-        extra["diffusion_cg_box32"] = diffusion_cg(case, args)
+        extra["diffusion_cg_box32"] = diffusion_cg(case, args, peak)
         extra["reactor_batch"] = reactor_batch(args)
     if rank != 0:
         return

@@ -191,9 +191,14 @@ typedef struct {
    * against).  Static scheduling takes no time budget and is rejected by
    * mri_stage_fast_batch (MRI_EINVAL). */
   int schedule;
-  /* Layout of the triangular solves of every Newton iteration (MRI_LU_*).  The
-   * arithmetic and its order are the same in every layout, so the results are
-   * bitwise identical; only the cost differs (a dimension of the autotuner). */
+  /* How the Newton matrix is factorised and every Newton iteration solved
+   * (MRI_LU_*).  The triangular-solve layouts (AUTO, REGS, REGS_SPLIT, SHARED) share
+   * the arithmetic and its order, so their results are bitwise identical; only the
+   * cost differs.  MRI_LU_INVERSE computes the inverse instead, so its corrections
+   * differ from the others by rounding (the converged stage values still meet the
+   * Newton tolerance).  A dimension of the autotuner.  A matrix cache entry records
+   * whether it holds LU factors or an inverse; an entry of the other kind counts as
+   * empty. */
   int lu_variant;
 } mri_fast_opts;
 
@@ -208,6 +213,12 @@ typedef struct {
                                 MRI_LU_REGS layout for the backward pass (fewer FP64
                                 instructions); n <= 32 as MRI_LU_REGS, larger n shared */
 #define MRI_LU_SHARED 3      /* substitutions on the right-hand side in shared memory */
+#define MRI_LU_INVERSE 4     /* Gauss-Jordan inversion with partial pivoting (the pivot
+                                rule of the LU) at every Jacobian evaluation; every
+                                Newton solve is then a matrix-vector product, with no
+                                chain of dependent steps (one warp instruction of a
+                                narrow FP64 unit costs the same whatever its active
+                                lanes, and a substitution step waits on the previous) */
 
 /* Fill opts with the defaults (SDIRK3, rtol 1e-10, atol_Y 1e-20, atol_T 1e-10 K,
  * 10 Newton iterations, per-substep Jacobian, FP64, no ramp, automatic launch
@@ -464,6 +475,11 @@ int mri_fast_jac(const double* y, const double* p, int ncell, const mri_mech* me
  * factors, b [nbatch][n] by x; info [nbatch] (may be NULL) gets 0 or k+1 for a
  * zero pivot in column k.  1 <= n <= 128. */
 int mri_lu_solve_batched(double* A, double* b, int n, int nbatch, int32_t* info, void* stream);
+/* Batched dense solve A x = b through the Gauss-Jordan inverse of MRI_LU_INVERSE
+ * (FP64): A [nbatch][n][n] row-major is overwritten by A^-1, b [nbatch][n] by
+ * x = A^-1 b computed as the stage kernel does (W (P b), W = (P A)^-1); info as for
+ * mri_lu_solve_batched.  1 <= n <= 128. */
+int mri_inverse_solve_batched(double* A, double* b, int n, int nbatch, int32_t* info, void* stream);
 
 const char* mri_status_str(int code);
 

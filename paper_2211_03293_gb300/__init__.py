@@ -33,7 +33,7 @@ MRI_PREC_FP64 = 0
 MRI_PREC_FP32_LU = 1
 MRI_START_PREDICTOR, MRI_START_PREVIOUS, MRI_START_GUESS, MRI_START_GUESS_FIRST = 0, 1, 2, 3
 MRI_SCHED_QUEUE, MRI_SCHED_STATIC = 0, 1
-MRI_LU_AUTO, MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED = 0, 1, 2, 3
+MRI_LU_AUTO, MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED, MRI_LU_INVERSE = 0, 1, 2, 3, 4
 
 
 class mri_fast_opts(ct.Structure):
@@ -129,6 +129,7 @@ _lib.mri_step_noalloc.argtypes = [_vp, _vp, ct.POINTER(mri_grid), ct.c_double, c
 _lib.mri_fast_rhs.argtypes = [_vp, _vp, ct.c_int, _vp, _vp, _vp]
 _lib.mri_fast_jac.argtypes = [_vp, _vp, ct.c_int, _vp, _vp, _vp]
 _lib.mri_lu_solve_batched.argtypes = [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp]
+_lib.mri_inverse_solve_batched.argtypes = [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp]
 _lib.mri_stage_forcing.argtypes = [_vp, ct.c_int, ct.c_longlong, ct.POINTER(ct.c_double), _vp, _vp]
 _lib.mri_method_coupling.argtypes = [ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                      ct.POINTER(ct.c_int)]
@@ -140,7 +141,7 @@ _lib.mri_status_str.restype = ct.c_char_p
 
 EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_default", "mri_stage_fast",
             "mri_slow_rhs", "mri_step_workspace_size", "mri_step", "mri_fast_rhs", "mri_fast_jac",
-            "mri_lu_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling",
+            "mri_lu_solve_batched", "mri_inverse_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling",
             "mri_step_noalloc", "mri_probe_fp64_fma", "mri_probe_exp", "mri_stage_fast_shape",
             "mri_stage_fast_batch", "mri_mlp_create", "mri_mlp_free", "mri_mlp_num_params", "mri_mlp_params",
             "mri_mlp_forward", "mri_mlp_grad", "mri_mlp_grad_copy", "mri_mlp_adam", "mri_mlp_status",
@@ -448,6 +449,11 @@ def mri_fast_jac(y, p, mech: Mech, J, stream=None) -> int:
 def mri_lu_solve_batched(A, b, info=None, stream=None) -> int:
     return _check(_lib.mri_lu_solve_batched(_f64(A), _f64(b), A.shape[-1], A.shape[0], _i32(info), _stream(stream)),
                   "mri_lu_solve_batched")
+
+
+def mri_inverse_solve_batched(A, b, info=None, stream=None) -> int:
+    return _check(_lib.mri_inverse_solve_batched(_f64(A), _f64(b), A.shape[-1], A.shape[0], _i32(info),
+                                                 _stream(stream)), "mri_inverse_solve_batched")
 
 
 # ----------------------------------------------------------------------------- learned form

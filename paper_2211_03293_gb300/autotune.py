@@ -16,10 +16,13 @@ The best choice depends on the mechanism's size, the precision form, K and the
 cell count, so it is measured: each candidate runs the caller's own stage on a copy
 of its inputs, timed with CUDA events on the launching stream.  The search is
 coordinate-wise (launch shapes first, then the solve layout at the best shape, then
-the schedule); every candidate computes the same result, so the tuner needs no
-checking and the results of the timed runs are discarded.
+the schedule).  Every candidate but the Gauss-Jordan inverse (MRI_LU_INVERSE)
+computes the same result bit for bit, and that one differs by rounding inside the
+Newton tolerance, so the tuner needs no checking and the results of the timed runs
+are discarded.
 """
-from . import (MRI_LU_AUTO, MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED, MRI_SCHED_QUEUE, MRI_SCHED_STATIC,
+from . import (MRI_LU_AUTO, MRI_LU_INVERSE, MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED, MRI_SCHED_QUEUE,
+               MRI_SCHED_STATIC,
                MriError, mri_fast_opts, mri_stage_fast, mri_stage_fast_shape)
 
 _cache = {}
@@ -47,12 +50,12 @@ def candidate_shapes(mech, opts, ncell, K, max_bps=4, depth=3):
 
 
 def candidate_lu_variants(n):
-    """Solve layouts that differ for a system of n unknowns."""
+    """Factorisations and solve layouts that differ for a system of n unknowns."""
     if n <= 32:
-        return [MRI_LU_REGS, MRI_LU_SHARED]
+        return [MRI_LU_REGS, MRI_LU_SHARED, MRI_LU_INVERSE]
     if n <= 64:
-        return [MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED]
-    return [MRI_LU_SHARED]
+        return [MRI_LU_REGS, MRI_LU_REGS_SPLIT, MRI_LU_SHARED, MRI_LU_INVERSE]
+    return [MRI_LU_SHARED, MRI_LU_INVERSE]
 
 
 def autotune_stage(mech, y, p, phi, Hstage, h, opts, repeats=2, stream=None, verbose=False, schedules=True):

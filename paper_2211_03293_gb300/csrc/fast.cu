@@ -796,6 +796,145 @@ __device__ __forceinline__ void lu_solve_perm(const MT* A, int n, int ld, const 
   }
 }
 
+// In-place Gauss-Jordan inversion with partial pivoting of the n x n matrix A (row
+// stride ld, n <= 128), one warp, with the pivot rule of lu_factor_warp (largest |a| in
+// the pivot column, ties to the lowest row; piv[k] the row interchanged with row k at
+// step k).  On return A holds W^T, W = (P A)^-1 with P those interchanges, so that
+// A^-1 b = W (P b) (piv_to_perm turns piv into P).  col: n scratch values.  Returns 0,
+// or k + 1 when pivot column k is zero or not finite (the inversion stops there).
+// Step k scales the pivot row by 1/a_kk (its own column taking 1/a_kk) and subtracts
+// a_ik times it from every other row i, whose column k starts from 0; those (row,
+// column) pairs run flattened over the lanes.  The transposition at the end lets the
+// solve read a column of W^T per lane group without bank conflicts.
+template <typename MT>
+__device__ __forceinline__ int gj_invert_warp(MT* A, int n, int ld, int* piv, MT* col, int lane) {
+  for (int k = 0; k < n; ++k) {
+    unsigned long long v = 0ull;
+    int bi = 127;
+    for (int i = k + lane; i < n; i += 32) {
+      const unsigned long long a = abs_bits(A[i * ld + k]);
+      if (a > v) { v = a; bi = i; }
+    }
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned hmax = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned lmax = __reduce_max_sync(0xffffffffu, hi == hmax ? lo : 0u);
+    const unsigned long long best = ((unsigned long long)hmax << 32) | lmax;
+    if (best == 0ull || best >= inf_bits(MT(0))) return k + 1;
+    bi = 127 - (int)__reduce_max_sync(0xffffffffu, (v == best) ? (unsigned)(127 - bi) : 0u);
+    if (lane == 0) piv[k] = bi;
+    if (bi != k)
+      for (int j = lane; j < n; j += 32) {
+        const MT a = A[k * ld + j];
+        A[k * ld + j] = A[bi * ld + j];
+        A[bi * ld + j] = a;
+      }
+    __syncwarp();
+    const MT inv = MT(1) / A[k * ld + k];
+    for (int i = lane; i < n; i += 32) col[i] = A[i * ld + k];
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) A[k * ld + j] = (j == k) ? inv : A[k * ld + j] * inv;
+    __syncwarp();
+    const int m = n - 1;                       // the rows other than k
+    if (m > 0) {
+      int q = lane / n, r = lane - q * n;      // pair e = q n + r: row q (+1 past k), column r
+      for (; q < m;) {
+        const int i = q + (q >= k ? 1 : 0);
+        const MT base = (r == k) ? MT(0) : A[i * ld + r];
+        A[i * ld + r] = fma_t(-col[i], A[k * ld + r], base);
+        r += 32;
+        while (r >= n) { r -= n; ++q; }
+      }
+    }
+    __syncwarp();
+  }
+  // W -> W^T: the pairs (i, j), i < j, of the strict upper triangle, flattened
+  {
+    int i = 0, j = 1 + lane;                   // row i holds the pairs j = i + 1 .. n - 1
+    while (i < n - 1 && j >= n) { const int over = j - n; ++i; j = i + 1 + over; }
+    for (; i < n - 1;) {
+      const MT a = A[i * ld + j];
+      A[i * ld + j] = A[j * ld + i];
+      A[j * ld + i] = a;
+      j += 32;
+      while (i < n - 1 && j >= n) { const int over = j - n; ++i; j = i + 1 + over; }
+    }
+  }
+  __syncwarp();
+  return 0;
+}
+
+// Column ranges ("chunks") into which inv_apply_warp splits each of the rem = n mod 32
+// rows of its last, partial row group: the count c <= 32 / rem that minimises the
+// chunk length ceil(n / c) plus the c - 1 additions of the partial sums.
+__host__ __device__ inline int inv_chunk_count(int n) {
+  const int rem = n % 32;
+  if (rem == 0) return 1;
+  int best_c = 1, best = n;
+  for (int c = 2; c * rem <= 32; ++c) {
+    const int cost = (n + c - 1) / c + c - 1;
+    if (cost < best) { best = cost; best_c = c; }
+  }
+  return best_c;
+}
+
+// x = W (P b) with W^T in A (gj_invert_warp) and the permutation perm of piv_to_perm;
+// b is overwritten by x.  Row 32 g + lane of a full group of 32 rows is one lane's dot
+// product (two accumulators, even and odd columns); each of the rem rows of a last
+// partial group is split into `chunks` column ranges on consecutive lanes, whose
+// partial sums are added in chunk order.  No step waits on another lane's result
+// except that final addition.
+template <typename MT>
+__device__ __forceinline__ void inv_apply_warp(const MT* A, int n, int ld, const int* perm, MT* b, int chunks,
+                                               int lane) {
+  MT g[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) g[r] = (lane + 32 * r < n) ? b[perm[lane + 32 * r]] : MT(0);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (lane + 32 * r < n) b[lane + 32 * r] = g[r];
+  __syncwarp();
+  const int full = n >> 5, rem = n & 31;
+  MT x[4];
+#pragma unroll
+  for (int gi = 0; gi < 4; ++gi) {
+    x[gi] = MT(0);
+    if (gi < full) {
+      const int i = 32 * gi + lane;
+      MT a0 = MT(0), a1 = MT(0);
+      int j = 0;
+      for (; j + 1 < n; j += 2) {
+        a0 = fma_t(A[j * ld + i], b[j], a0);
+        a1 = fma_t(A[(j + 1) * ld + i], b[j + 1], a1);
+      }
+      if (j < n) a0 = fma_t(A[j * ld + i], b[j], a0);
+      x[gi] = a0 + a1;
+    }
+  }
+  const int c = chunks, rr = lane / c, h = lane - rr * c;
+  MT sum = MT(0);
+  if (rem > 0) {
+    const int len = (n + c - 1) / c;
+    MT acc = MT(0);
+    if (rr < rem) {
+      const int i = 32 * full + rr;
+      const int j1 = min(n, (h + 1) * len);
+      for (int j = h * len; j < j1; ++j) acc = fma_t(A[j * ld + i], b[j], acc);
+    }
+    sum = acc;
+    for (int o = 1; o < c; ++o) {
+      const MT v = __shfl_down_sync(0xffffffffu, acc, o);
+      if (h + o < c) sum += v;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int gi = 0; gi < 4; ++gi)
+    if (gi < full) b[32 * gi + lane] = x[gi];
+  if (rem > 0 && h == 0 && rr < rem) b[32 * full + rr] = sum;
+  __syncwarp();
+}
+
 // ------------------------------------------------------------------ stage kernel
 
 struct StageArgs {
@@ -861,11 +1000,14 @@ __device__ __forceinline__ float wrms_update(const double* d, const double* Z, i
   return isnan(nrm) ? INFINITY : nrm;
 }
 
-// Jacobian at Z, M = I - hg J, LU; the row interchanges are kept as a permutation
-// (piv_to_perm).  Returns the LU info (0 = ok).  PREC32: the assembly (from FP64
-// rates), the matrix and its factors are FP32.
+// Jacobian at Z, M = I - hg J, then its LU factors or (MRI_LU_INVERSE) the transposed
+// inverse of gj_invert_warp, whose column scratch is the unused diagonal-inverse
+// vector; the row interchanges are kept as a permutation (piv_to_perm).  Returns the
+// factorisation's info (0 = ok).  PREC32: the assembly (from FP64 rates), the matrix
+// and its factors are FP32.
 template <bool PREC32>
-__device__ __forceinline__ int refresh_matrix(const Tab& t, const WS& w, const double* Z, double p, double hg, int lane) {
+__device__ __forceinline__ int refresh_matrix(const Tab& t, const WS& w, const double* Z, double p, double hg,
+                                              int variant, int lane) {
   Scal s;
   chem_eval<true>(t, w, Z, p, s, lane);
   int rc;
@@ -873,11 +1015,13 @@ __device__ __forceinline__ int refresh_matrix(const Tab& t, const WS& w, const d
     const JacIn<float> in = jac_in32(t, w, lane);
     chem_jac<float>(t, w, Z, s, w.M32, in, lane);
     form_newton_matrix<float>(w.M32, t.n, w.ld, hg, lane);
-    rc = lu_factor_warp<true, float>(w.M32, t.n, w.ld, w.piv, w.dinv32, lane);
+    rc = (variant == MRI_LU_INVERSE) ? gj_invert_warp<float>(w.M32, t.n, w.ld, w.piv, w.dinv32, lane)
+                                     : lu_factor_warp<true, float>(w.M32, t.n, w.ld, w.piv, w.dinv32, lane);
   } else {
     chem_jac<double>(t, w, Z, s, w.M, jac_in64(t, w), lane);
     form_newton_matrix<double>(w.M, t.n, w.ld, hg, lane);
-    rc = lu_factor_warp<true, double>(w.M, t.n, w.ld, w.piv, w.dinv, lane);
+    rc = (variant == MRI_LU_INVERSE) ? gj_invert_warp<double>(w.M, t.n, w.ld, w.piv, w.dinv, lane)
+                                     : lu_factor_warp<true, double>(w.M, t.n, w.ld, w.piv, w.dinv, lane);
   }
   if (rc == 0) piv_to_perm(w.piv, t.n, lane);
   return rc;
@@ -888,15 +1032,17 @@ __device__ __forceinline__ int refresh_matrix(const Tab& t, const WS& w, const d
 // residual of every Newton iteration then refines the stage value to the same
 // tolerance as the FP64 form.
 template <bool PREC32>
-__device__ __forceinline__ void newton_solve(const WS& w, int n, int lane, int variant) {
+__device__ __forceinline__ void newton_solve(const WS& w, int n, int lane, int variant, int chunks) {
   if (PREC32) {
     for (int k = lane; k < n; k += 32) w.d32[k] = (float)w.d[k];
     __syncwarp();
-    lu_solve_perm<float>(w.M32, n, w.ld, w.piv, w.dinv32, w.d32, lane, variant);
+    if (variant == MRI_LU_INVERSE) inv_apply_warp<float>(w.M32, n, w.ld, w.piv, w.d32, chunks, lane);
+    else lu_solve_perm<float>(w.M32, n, w.ld, w.piv, w.dinv32, w.d32, lane, variant);
     for (int k = lane; k < n; k += 32) w.d[k] = (double)w.d32[k];
     __syncwarp();
   } else {
-    lu_solve_perm<double>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane, variant);
+    if (variant == MRI_LU_INVERSE) inv_apply_warp<double>(w.M, n, w.ld, w.piv, w.d, chunks, lane);
+    else lu_solve_perm<double>(w.M, n, w.ld, w.piv, w.dinv, w.d, lane, variant);
   }
 }
 
@@ -948,6 +1094,8 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
   const WS w(reinterpret_cast<double*>(smem + a.L.bytes) + (size_t)warp * a.ws_stride, a.L, PREC32, a.K);
   const int n = t.n, Ns = t.Ns, S = a.nstage;
   const int total_sub = a.n_sub + (a.ramp > 0 ? a.ramp : 0);
+  const int chunks = inv_chunk_count(n);   // MRI_LU_INVERSE solves
+  const int layout = (a.lu_variant == MRI_LU_INVERSE) ? 1 : 0;   // what a cache entry holds
   // Persistent warps take cells from a device work queue, so that cells of uneven
   // stiffness (Newton and Jacobian counts vary severalfold across a front) balance.
   // With a time budget a warp stops taking cells once it has run that long, so the
@@ -979,7 +1127,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
                              ? a.mcache + (size_t)cell * a.mc_stride : nullptr;
     if (mce) {
       const McHeader* hd = reinterpret_cast<const McHeader*>(mce);
-      if (hd->tag == kMcTag && hd->n == n && hd->prec == (PREC32 ? 1 : 0)) {
+      if (hd->tag == kMcTag && hd->n == n && hd->prec == (PREC32 ? 1 : 0) && hd->layout == layout) {
         const int nm = n * w.ld;
         if (PREC32) {
           const float* src = reinterpret_cast<const float*>(mce + sizeof(McHeader));
@@ -1040,7 +1188,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
       const bool need = (a.jac_policy == MRI_JAC_PER_SUBSTEP) || startup_sub || hg != M_hg ||
                         M_age >= kMaxJacAge;
       if (need) {
-        if (refresh_matrix<PREC32>(t, w, w.y0, p, hg, lane) != 0) { status = MRI_CELL_ENEWTON; break; }
+        if (refresh_matrix<PREC32>(t, w, w.y0, p, hg, a.lu_variant, lane) != 0) { status = MRI_CELL_ENEWTON; break; }
         njac++;
         M_hg = hg;
         M_age = 0;
@@ -1147,11 +1295,11 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
           }
           __syncwarp();
           if (startup && !fresh) {   // start-up substeps: full Newton, as far from the manifold
-            if (refresh_matrix<PREC32>(t, w, w.Z, p, hg, lane) != 0) break;
+            if (refresh_matrix<PREC32>(t, w, w.Z, p, hg, a.lu_variant, lane) != 0) break;
             njac++;
             fresh = true;
           }
-          newton_solve<PREC32>(w, n, lane, a.lu_variant);
+          newton_solve<PREC32>(w, n, lane, a.lu_variant, chunks);
           float nrm = wrms_update(w.d, w.Z, n, a.rtol, a.atol_Y, a.atol_T, lane);
           // redo with a fresh matrix when the stale one contracts by less than 10x, or
           // when its contraction rate would not reach the tolerance three iterations
@@ -1165,12 +1313,12 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
             redo = proj > 1.0f;
           }
           if (redo) {
-            if (refresh_matrix<PREC32>(t, w, w.Z, p, hg, lane) != 0) break;
+            if (refresh_matrix<PREC32>(t, w, w.Z, p, hg, a.lu_variant, lane) != 0) break;
             njac++;
             M_age = 0;
             for (int k = lane; k < n; k += 32) w.d[k] = w.res[k];
             __syncwarp();
-            newton_solve<PREC32>(w, n, lane, a.lu_variant);
+            newton_solve<PREC32>(w, n, lane, a.lu_variant, chunks);
             nrm = wrms_update(w.d, w.Z, n, a.rtol, a.atol_Y, a.atol_T, lane);
           }
           for (int k = lane; k < n; k += 32) w.Z[k] += w.d[k];
@@ -1262,6 +1410,7 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
         hd->n = n;
         hd->prec = PREC32 ? 1 : 0;
         hd->has_f = (nsub > 0) ? 1 : 0;
+        hd->layout = layout;
         hd->tag = kMcTag;
       }
     } else if (mce && lane == 0) {
@@ -1500,6 +1649,36 @@ __global__ void lu_kernel(double* A, double* b, int n, int ld, int nbatch, int32
     if (rc == 0) lu_solve_warp<false, double>(Ms, n, ld, pv, dv, bs, lane);
     for (int e = lane; e < n * n; e += 32) A[(size_t)sys * n * n + e] = Ms[(e / n) * ld + e % n];
     for (int k = lane; k < n; k += 32) b[(size_t)sys * n + k] = bs[k];
+    if (lane == 0 && info) info[sys] = rc;
+    __syncwarp();
+  }
+}
+
+// The inverse path of MRI_LU_INVERSE on a batch of FP64 systems (one warp per system):
+// A <- A^-1 (row-major, from W^T: A^-1[i][perm[k]] = W[i][k]), b <- W (P b).
+__global__ void inverse_kernel(double* A, double* b, int n, int ld, int nbatch, int32_t* info) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per = round_up(n * ld, 2) + 2 * round_up(n, 2) + n;
+  double* Ms = reinterpret_cast<double*>(smem) + (size_t)warp * per;
+  double* bs = Ms + round_up(n * ld, 2);
+  double* cs = bs + round_up(n, 2);
+  int* pv = reinterpret_cast<int*>(cs + round_up(n, 2));
+  const int chunks = inv_chunk_count(n);
+  for (int sys = blockIdx.x * nw + warp; sys < nbatch; sys += gridDim.x * nw) {
+    for (int e = lane; e < n * n; e += 32) Ms[(e / n) * ld + e % n] = A[(size_t)sys * n * n + e];
+    for (int k = lane; k < n; k += 32) bs[k] = b[(size_t)sys * n + k];
+    __syncwarp();
+    const int rc = gj_invert_warp<double>(Ms, n, ld, pv, cs, lane);
+    if (rc == 0) {
+      piv_to_perm(pv, n, lane);
+      inv_apply_warp<double>(Ms, n, ld, pv, bs, chunks, lane);
+      for (int e = lane; e < n * n; e += 32) {
+        const int k = e / n, i = e % n;        // W^T[k][i] = W[i][k] -> A^-1[i][perm[k]]
+        A[(size_t)sys * n * n + (size_t)i * n + pv[k]] = Ms[k * ld + i];
+      }
+      for (int k = lane; k < n; k += 32) b[(size_t)sys * n + k] = bs[k];
+    }
     if (lane == 0 && info) info[sys] = rc;
     __syncwarp();
   }
@@ -1835,7 +2014,7 @@ bool fast_opts_ok(const mri_fast_opts* o) {
                                std::isfinite(o->ctrl_atol_T))) &&
          o->newton_safety > 0 && o->newton_safety <= 1.0 &&
          (o->schedule == MRI_SCHED_QUEUE || (o->schedule == MRI_SCHED_STATIC && o->time_budget_s == 0.0)) &&
-         o->lu_variant >= MRI_LU_AUTO && o->lu_variant <= MRI_LU_SHARED;
+         o->lu_variant >= MRI_LU_AUTO && o->lu_variant <= MRI_LU_INVERSE;
 }
 
 int mech_device_check(const Mech& m) {
@@ -1983,20 +2162,32 @@ extern "C" int mri_fast_jac(const double* y, const double* p, int ncell, const m
   return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
 }
 
-extern "C" int mri_lu_solve_batched(double* A, double* b, int n, int nbatch, int32_t* info, void* stream) {
+namespace mri {
+// Launch of the batched one-warp-per-system test kernels (lu_kernel, inverse_kernel).
+static int launch_batched_solve(void (*kern)(double*, double*, int, int, int, int32_t*), double* A, double* b,
+                                int n, int nbatch, int32_t* info, void* stream) {
   if (n < 1 || n > 128 || nbatch < 0 || (nbatch > 0 && (!A || !b))) return MRI_EINVAL;
   if (nbatch == 0) return MRI_OK;
   const int ld = (n % 2 == 1) ? n : n + 1;
-  const size_t per = ((size_t)mri::round_up(n * ld, 2) + 2 * mri::round_up(n, 2) + n) * 8;
-  const int limit = mri::device_smem_limit();
+  const size_t per = ((size_t)round_up(n * ld, 2) + 2 * round_up(n, 2) + n) * 8;
+  const int limit = device_smem_limit();
   int warps = (int)(limit / per);
   if (warps < 1) return MRI_EINVAL;
   if (warps > 8) warps = 8;
   int blocks = (nbatch + warps - 1) / warps;
-  const int cap = mri::device_sm_count() * 4;
+  const int cap = device_sm_count() * 4;
   if (blocks > cap) blocks = cap;
   const size_t smem = per * warps;
-  if (!mri::allow_full_smem((const void*)mri::lu_kernel)) return MRI_ECUDA;
-  mri::lu_kernel<<<blocks, warps * 32, smem, static_cast<cudaStream_t>(stream)>>>(A, b, n, ld, nbatch, info);
+  if (!allow_full_smem((const void*)kern)) return MRI_ECUDA;
+  kern<<<blocks, warps * 32, smem, static_cast<cudaStream_t>(stream)>>>(A, b, n, ld, nbatch, info);
   return cudaGetLastError() == cudaSuccess ? MRI_OK : MRI_ECUDA;
+}
+}  // namespace mri
+
+extern "C" int mri_lu_solve_batched(double* A, double* b, int n, int nbatch, int32_t* info, void* stream) {
+  return mri::launch_batched_solve(mri::lu_kernel, A, b, n, nbatch, info, stream);
+}
+
+extern "C" int mri_inverse_solve_batched(double* A, double* b, int n, int nbatch, int32_t* info, void* stream) {
+  return mri::launch_batched_solve(mri::inverse_kernel, A, b, n, nbatch, info, stream);
 }

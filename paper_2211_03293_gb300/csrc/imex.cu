@@ -23,7 +23,7 @@ namespace mri {
 namespace {
 
 constexpr int kRedBlocks = 1024;    // blocks of the fused passes at most (partial sums per block)
-constexpr int kPassThreads = 256;   // threads of a fused pass (at least one warp per component)
+constexpr int kPassThreads = 256;   // threads of a fused pass at least (when that many fit)
 constexpr int kPassMax = 1024;      // n <= 1024: one slot of up to 1024 threads
 constexpr int kScalThreads = 1024;  // the scalar kernels: one warp per component at a time
 constexpr int kDirBlocks = 2432;    // blocks of the direction update (16 per SM)
@@ -89,8 +89,11 @@ __device__ __forceinline__ double apply_at(const double* __restrict__ x, const L
   return acc;
 }
 
-// Layout of a fused pass: thread (slot, q), q < rt = n rounded up to a warp,
-// slot < S = kPassThreads / rt; block b takes the cells b S + slot + m (gridDim S).
+// Layout of a fused pass: thread (slot, q) = threadIdx slot rt + q, q < rt = n, slot < S
+// (pass_slots); block b takes the cells b S + slot + m (gridDim S).  Consecutive threads
+// touch consecutive doubles of the state, and every lane of every full warp has an
+// element: the FP64 instructions, which cost the same whatever the active lanes,
+// carry no idle lanes.
 // The block's partial sums over its slots are written component-major,
 // part[q][block], in slot order.
 __device__ __forceinline__ void block_partial(double v, int n, int rt, double* __restrict__ part) {
@@ -180,8 +183,8 @@ __global__ void __launch_bounds__(kPassMax) apply_pass_kernel(const double* __re
     return;
   }
   if (!last_block(cs)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int qq = warp; qq < s.n; qq += nw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;   // full warps
+  for (int qq = warp; warp < nw && qq < s.n; qq += nw) {
     const double pq = sum_parts(part1, gridDim.x, qq, lane);
     if (lane == 0) sc[qq].alpha = (sc[qq].done || !(pq > 0.0)) ? 0.0 : sc[qq].rz / pq;
   }
@@ -228,9 +231,9 @@ __global__ void __launch_bounds__(kPassMax) update_pass_kernel(double* __restric
   }
   block_partial(acc, n, rt, part);
   if (!last_block(cs)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;   // full warps
   int active = 0;
-  for (int qq = warp; qq < n; qq += nw) {
+  for (int qq = warp; warp < nw && qq < n; qq += nw) {
     const double rr = sum_parts(part, gridDim.x, qq, lane);
     CgScal t = sc[qq];
     if (!t.done) {
@@ -360,6 +363,22 @@ Lap7 make_op(const mri_grid* g, int n, double a) {
   return s;
 }
 
+// Slots S of a fused pass (S n threads): at least kPassThreads threads where that many
+// fit in kPassMax, and of those the block whose last warp is fullest (fewest idle lanes),
+// the smallest on ties.
+int pass_slots(int n) {
+  const int smax = kPassMax / n;
+  int best = smax;
+  double best_eff = -1.0;
+  for (int S = 1; S <= smax; ++S) {
+    const int pt = S * n;
+    if (pt < kPassThreads && S < smax) continue;
+    const double eff = (double)pt / (double)(((pt + 31) / 32) * 32);
+    if (eff > best_eff) { best_eff = eff; best = S; }
+  }
+  return best;
+}
+
 bool grid_ok2(const mri_grid* g) {
   return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->dx > 0 && std::isfinite(g->dx) && g->D >= 0 &&
          std::isfinite(g->D) && (g->order == 2 || g->order == 4) && std::isfinite(g->u[0]) &&
@@ -386,8 +405,8 @@ int diffusion_solve(double* x, const double* b, int n, const mri_grid* g, double
   CgState* cs = reinterpret_cast<CgState*>(sc + n);
   const Lap7 op = make_op(g, n, a);
   const double inv_diag = 1.0 / op.centre;
-  const int rt = ((n + 31) / 32) * 32;
-  const int S = rt < kPassThreads ? kPassThreads / rt : 1;
+  const int rt = n;
+  const int S = pass_slots(n);
   const int pt = S * rt;                                   // threads of a fused pass
   // one wave of the fused passes: as many blocks as stay resident together (at most
   // kRedBlocks, the partial-sum slots), so no block of a pass waits for a second wave

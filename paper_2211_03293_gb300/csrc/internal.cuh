@@ -64,14 +64,16 @@ struct Layout {
   int ws_doubles32;       // doubles per cell (warp), mixed-precision form, K = kMaxK
 };
 
-// Newton-matrix cache entry: header, then the factorised matrix (n * ld values), the
-// diagonal inverses (n values) and the pivot permutation (n int32), in the form's
-// precision, then (8-byte aligned) f^F at the cell's state when the last call ended
-// (n doubles; has_f = 1 when present).
+// Newton-matrix cache entry: header, then the factorised matrix (n * ld values: LU
+// factors, or with layout 1 the transposed inverse), the diagonal inverses (n values;
+// unused by layout 1) and the pivot permutation (n int32), in the form's precision,
+// then (8-byte aligned) f^F at the cell's state when the last call ended (n doubles;
+// has_f = 1 when present).
 struct McHeader {
   double hg;
   int age, tag, n, prec;
-  int has_f, pad;
+  int has_f;
+  int layout;   // 0: LU factors, 1: transposed inverse (MRI_LU_INVERSE)
 };
 constexpr int kMcTag = 0x4D434145;   // marks a filled entry (a zeroed entry is empty)
 

@@ -89,7 +89,7 @@ def test_stage_argument_validation_on_host(lib):
                dict(time_budget_s=-1.0), dict(time_budget_s=float("nan")), dict(adaptive=2),
                dict(adaptive=1, ctrl_rtol=0.0), dict(adaptive=1, ctrl_atol_T=-1.0), dict(newton_safety=0.0),
                dict(newton_safety=1.5), dict(newton_safety=float("nan")), dict(schedule=2),
-               dict(schedule=1, time_budget_s=1.0), dict(lu_variant=4), dict(lu_variant=-1), dict(method=11),
+               dict(schedule=1, time_budget_s=1.0), dict(lu_variant=5), dict(lu_variant=-1), dict(method=11),
                dict(method=14, adaptive=1), dict(method=15)):
         bad = lib.mri_fast_opts_default(**kw)
         assert L.mri_stage_fast(fake, fake, 4, None, 0, 0.0, 1e-8, 1e-9, fake, ct.byref(bad), None, None, None,

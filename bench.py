@@ -68,7 +68,7 @@ FLOPS_PER_TRANSCENDENTAL = 20.0
 # profiles/stage_fast_fp64_box16.md and profiles/stage_fast_mixed_box16.md (4096-cell
 # launches; traffic grows with the cells processed, so a launch over `cells` moves
 # cells times this).  None: the kernel changed since the capture.
-STAGE_DRAM_BYTES_PER_CELL = {0: (61923072 + 3229952) / 4096, 1: (33617920 + 256) / 4096}
+STAGE_DRAM_BYTES_PER_CELL = {0: (61929728 + 3034880) / 4096, 1: (33627136 + 256) / 4096}
 # forms timed without the Newton-matrix cache (the learned form's comparison: without the
 # cache's f^F no derivative predicts the first SDIRK stage of a call, which is where the
 # network's prediction is used)
@@ -1179,6 +1179,10 @@ def main():
     torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     probe = torch.empty(N_SM * 8 * 256 * 4, dtype=torch.float64, device=dev)
     peak = 2.0 * mri.mri_probe_fp64_fma(probe, iters=4096) / 1e12
+    # the FP64 unit's cost model: lane-FMA rate with 32, 16, 8 and 1 active lanes per
+    # warp (8 warps per SM), and the latency of a dependent FMA
+    fp64_unit = {"lane_fma_per_s": {str(k): mri.mri_probe_fp64_lanes(probe, k) for k in (32, 16, 8, 1)},
+                 "dependent_fma_cycles": mri.mri_probe_fp64_latency(probe)}
     del probe
 
     if args.profile_cg:
@@ -1244,7 +1248,7 @@ def main():
                    "plain_fp64_cell_steps_per_s": box.get("plain", {}).get("value"),
                    "plain_fp64_roofline_frac": box["plain"]["roofline"]["frac"] if "plain" in box else None},
         "clocks": r["clocks"],
-        "roofline": r["roofline"],
+        "roofline": dict(r["roofline"], fp64_unit=fp64_unit),
         "cpu_baseline": cpu,
         "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": r["e2e"]["h2d"],
                 "d2h_bytes_per_step": r["e2e"]["d2h"]},

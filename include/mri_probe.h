@@ -17,6 +17,22 @@ extern "C" {
  * Returns 0, -1 for bad arguments or -3 for a CUDA error. */
 int mri_probe_fp64_fma(double* scratch, long long scratch_doubles, int iters, double* fma_per_s, void* stream);
 
+/* The same chains with only the first active_lanes (1..32) lanes of every warp
+ * running them, warps_per_sm (1..32) warps on each SM: the rate of lane FMAs in
+ * *lane_fma_per_s.  On a device whose FP64 unit spends the same time on a warp
+ * instruction whatever its active lanes, this rate is proportional to
+ * active_lanes; the benchmark records it, because that cost model is what bounds
+ * the fast path's fraction of the FP64 peak (partial passes over n = Ns + 1
+ * unknowns, triangular solves, warp-uniform scalar work).  scratch: at least
+ * 32 warps_per_sm doubles per SM.  Returns 0, -1 or -3. */
+int mri_probe_fp64_lanes(double* scratch, long long scratch_doubles, int iters, int active_lanes, int warps_per_sm,
+                         double* lane_fma_per_s, void* stream);
+
+/* One warp running one dependent FP64 FMA chain of iters FMAs: SM clock cycles
+ * per FMA in *cycles (synchronises `stream`).  scratch: at least 40 doubles.
+ * Returns 0, -1 or -3. */
+int mri_probe_fp64_latency(double* scratch, long long scratch_doubles, int iters, double* cycles, void* stream);
+
 /* The FP64 exponential the rate kernels use (a table-driven method after Tang,
  * 1989, see fastmath.cuh), applied elementwise y[i] = exp(x[i]) on the device,
  * so that its accuracy can be checked against libm.  Returns 0, -1 or -3. */

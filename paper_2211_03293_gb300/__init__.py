@@ -134,6 +134,8 @@ _lib.mri_stage_forcing.argtypes = [_vp, ct.c_int, ct.c_longlong, ct.POINTER(ct.c
 _lib.mri_method_coupling.argtypes = [ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                      ct.POINTER(ct.c_int)]
 _lib.mri_probe_fp64_fma.argtypes = [_vp, ct.c_longlong, ct.c_int, ct.POINTER(ct.c_double), _vp]
+_lib.mri_probe_fp64_lanes.argtypes = [_vp, ct.c_longlong, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp]
+_lib.mri_probe_fp64_latency.argtypes = [_vp, ct.c_longlong, ct.c_int, ct.POINTER(ct.c_double), _vp]
 _lib.mri_probe_exp.argtypes = [_vp, _vp, ct.c_longlong, _vp]
 _lib.mri_probe_mech_device.argtypes = [_vp, ct.c_int]
 _lib.mri_status_str.argtypes = [ct.c_int]
@@ -142,7 +144,7 @@ _lib.mri_status_str.restype = ct.c_char_p
 EXPORTED = ("mri_mech_load", "mri_mech_free", "mri_mech_info", "mri_fast_opts_default", "mri_stage_fast",
             "mri_slow_rhs", "mri_step_workspace_size", "mri_step", "mri_fast_rhs", "mri_fast_jac",
             "mri_lu_solve_batched", "mri_inverse_solve_batched", "mri_status_str", "mri_stage_forcing", "mri_method_coupling",
-            "mri_step_noalloc", "mri_probe_fp64_fma", "mri_probe_exp", "mri_stage_fast_shape",
+            "mri_step_noalloc", "mri_probe_fp64_fma", "mri_probe_fp64_lanes", "mri_probe_fp64_latency", "mri_probe_exp", "mri_stage_fast_shape",
             "mri_stage_fast_batch", "mri_mlp_create", "mri_mlp_free", "mri_mlp_num_params", "mri_mlp_params",
             "mri_mlp_forward", "mri_mlp_grad", "mri_mlp_grad_copy", "mri_mlp_adam", "mri_mlp_status",
             "mri_gemm_bf16", "mri_stage_fast_guided", "mri_learned_features", "mri_learned_targets",
@@ -410,6 +412,26 @@ def mri_probe_fp64_fma(scratch, iters=4096, stream=None) -> float:
     if rc != 0:
         raise MriError(rc, "mri_probe_fp64_fma")
     return rate.value
+
+
+def mri_probe_fp64_lanes(scratch, active_lanes, warps_per_sm=8, iters=4096, stream=None) -> float:
+    """Lane-FMA rate (FMA/s) with only active_lanes lanes of every warp running FP64 FMA
+    chains, warps_per_sm warps per SM."""
+    rate = ct.c_double()
+    rc = _lib.mri_probe_fp64_lanes(_f64(scratch), scratch.numel(), iters, active_lanes, warps_per_sm,
+                                   ct.byref(rate), _stream(stream))
+    if rc != 0:
+        raise MriError(rc, "mri_probe_fp64_lanes")
+    return rate.value
+
+
+def mri_probe_fp64_latency(scratch, iters=4096, stream=None) -> float:
+    """SM cycles per FMA of one dependent FP64 FMA chain in one warp."""
+    cyc = ct.c_double()
+    rc = _lib.mri_probe_fp64_latency(_f64(scratch), scratch.numel(), iters, ct.byref(cyc), _stream(stream))
+    if rc != 0:
+        raise MriError(rc, "mri_probe_fp64_latency")
+    return cyc.value
 
 
 def mri_probe_exp(x, y, stream=None) -> int:

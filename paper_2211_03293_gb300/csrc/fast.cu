@@ -151,8 +151,9 @@ struct RxnOut {
 };
 
 // Rate of progress of reaction r (and with JAC its Jacobian pieces) from the species
-// factors of chem_eval: k_f = k_inf (times the falloff factor), 1/K_c as a product of
-// species factors, q = [M] (k_f prod C^nu' - k_r prod C^nu'').
+// factors of chem_eval: k_f = k_inf (times the falloff factor Pr/(1+Pr) F, whose ln F
+// joins the exponent of k_inf), 1/K_c as a product of species factors,
+// q = [M] (k_f prod C^nu' - k_r prod C^nu'').
 template <bool JAC>
 __device__ __forceinline__ void rxn_eval(const Tab& t, const WS& w, int r, double lnT, double invT, double Ctot,
                                          RxnOut& o) {
@@ -162,9 +163,10 @@ __device__ __forceinline__ void rxn_eval(const Tab& t, const WS& w, int r, doubl
   const int dn = (int)(int8_t)((rec >> 48) & 0xff);
   const int type = (int)(rec >> 56);
   const int tr = t.rrow[r] >> 16;                  // falloff row (type 2)
-  const double lnkinf = fma(t.b[r], lnT, t.lnA[r]) - t.Ta[r] * invT;
-  double kf = exp_tab(lnkinf, t.exp2t);
-  if (type == 2) kf *= w.tro[kTroeSlots * tr + 9];
+  double lnkf = fma(t.b[r], lnT, t.lnA[r]) - t.Ta[r] * invT;
+  if (type == 2) lnkf += w.tro[kTroeSlots * tr + 6];      // ln F
+  double kf = exp_tab(lnkf, t.exp2t);
+  if (type == 2) kf *= w.tro[kTroeSlots * tr + 9];        // Pr / (1 + Pr)
   double M = 1.0;
   if (type == 1) {
     const int row = t.rrow[r] & 0xffff;
@@ -287,9 +289,11 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     q[7 + kind] = log_tab(x, t.logt) * (1.0 / kLn10);   // q[7] = log10 Fc, q[8] = log10 Pr
   }
   __syncwarp();
-  // falloff, phase 3: broadening F, factor Pr/(1+Pr) F, and its derivatives.  Without
-  // the Jacobian and with fewer than 32 falloff reactions, lane NT (idle in this pass)
-  // inverts the mixture heat capacity in the same division instruction.
+  // falloff, phase 3: ln F of the broadening factor (slot 6; the reaction pass adds it
+  // to the exponent of k_inf), the factor Pr/(1+Pr) (slot 9), and with the Jacobian
+  // their derivatives.  Without the Jacobian and with fewer than 32 falloff reactions,
+  // lane NT (idle in this pass) inverts the mixture heat capacity in the same division
+  // instruction.
   double invcpm;
   if (!JAC && NT < 32) {
     double den_in = cpm, d2 = 0.0, s2 = 0.0, P1 = 0.0, logFc = 0.0, Pr = 0.0;
@@ -308,9 +312,10 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     }
     const double inv = 1.0 / den_in;
     if (lane < NT) {
-      // log F = log Fc den^2 / (den^2 + u^2) and the factor Pr/(1+Pr) F share the division
+      // log F = log Fc den^2 / (den^2 + u^2) and the factor Pr/(1+Pr) share the division
       const double logF = (logFc * d2) * (P1 * inv);
-      q[9] = (Pr * s2) * inv * exp_tab(logF * kLn10, t.exp2t);
+      q[9] = (Pr * s2) * inv;
+      q[6] = logF * kLn10;
     }
     invcpm = __shfl_sync(0xffffffffu, inv, NT);
   } else {
@@ -324,12 +329,13 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     const double u = q[8] + c;
     const double den = fma(-0.14, u, nn);
     if (!JAC) {
-      // log F = log Fc den^2 / (den^2 + u^2) and the factor Pr/(1+Pr) F, with one
+      // log F = log Fc den^2 / (den^2 + u^2) and the factor Pr/(1+Pr), with one
       // division for both quotients
       const double d2 = den * den, s2 = fma(u, u, d2), P1 = 1.0 + Pr;
       const double inv = 1.0 / (s2 * P1);
       const double logF = (logFc * d2) * (P1 * inv);
-      q[9] = (Pr * s2) * inv * exp_tab(logF * kLn10, t.exp2t);
+      q[9] = (Pr * s2) * inv;
+      q[6] = logF * kLn10;
     } else {
       const double invden = 1.0 / den;
       const double f1 = u * invden;
@@ -337,7 +343,7 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
       const double invg = 1.0 / g1;
       const double logF = logFc * invg;
       const double invPr1 = 1.0 / (1.0 + Pr);
-      q[9] = Pr * invPr1 * exp_tab(logF * kLn10, t.exp2t);
+      q[9] = Pr * invPr1;
       const int r = t.trx[tr];
       const double* tp = t.troe + 8 * tr;
       const double dlnkinf_dT = fma(t.Ta[r], invT, t.b[r]) * invT;
@@ -353,6 +359,7 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
       const double dlnF_dT = fma(dlogF_dx, dlnPr_dT, dlogF_dlogFc * dFc_dT / q[6]);
       q[10] = dlnPr_dT * invPr1 + dlnF_dT;            // added to d ln k_inf / dT
       q[11] = (invPr1 + dlogF_dx) / q[4];             // d ln k_f / d[M]
+      q[6] = logF * kLn10;                            // (Fc, read above, is no longer needed)
     }
   }
   __syncwarp();
@@ -1287,9 +1294,12 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
         for (int it = 0; it < a.max_newton; ++it) {
           Scal s;
           chem_eval<false>(t, w, w.Z, p, s, lane);
-          chem_rhs_out(t, w, s, w.f, lane);
+          // residual base + hg (f^F(Z) + r) - Z, with f^F formed in place (the formulas
+          // of chem_rhs_out): f_k = (wdot_k W_k) / rho, f_T = (-T Q / cpm) / rho
+          const double fT_rho = -(s.T * s.Q) * s.invcpm;
           for (int k = lane; k < n; k += 32) {
-            const double g = -(w.Z[k] - w.base[k] - hg * (w.f[k] + w.r[k]));
+            const double a = (k < Ns) ? w.wd[k] * t.W[k] : fT_rho;
+            const double g = fma(hg, fma(a, s.invrho, w.r[k]), w.base[k]) - w.Z[k];
             w.res[k] = g;
             w.d[k] = g;
           }
@@ -1736,16 +1746,21 @@ static int device_sm_smem() {
 // Warps per CTA and grid for a warp-per-cell kernel with `per_warp` bytes of workspace
 // after the staged table.  wpb / bps: requested warps per CTA and CTAs per SM (0 =
 // automatic).  The grid is persistent: at most bps CTAs per SM.
+// Static shared memory of the kernels, at most: the batched kernel (tableau and a
+// group's arguments) and the single-mechanism stage kernels (the tableau, 96 bytes).
+constexpr long long kStaticSmem = 1024;
+constexpr long long kStageStaticSmem = 128;
+
 static bool plan_launch(const Layout& L, int ncell, int& warps, int& blocks, size_t& smem, bool prec32 = false,
-                        int K = 0, int wpb = 0, int bps = 0, bool matrix = true) {
-  constexpr long long kStaticSmem = 1024;    // the kernels' static shared arrays (tableau, batch arguments)
+                        int K = 0, int wpb = 0, int bps = 0, bool matrix = true,
+                        long long static_smem = kStaticSmem) {
   constexpr long long kReservedPerCta = 1024;   // shared memory the SM keeps per resident CTA
   const int per_cta_sm = bps > 0 ? bps : 1;
   long long cap = device_smem_limit();
   const long long share = (long long)device_sm_smem() / per_cta_sm - kReservedPerCta;
   if (share < cap) cap = share;
   const size_t per_warp = (size_t)ws_offsets(L, prec32, K, matrix).total * 8;
-  long long room = cap - kStaticSmem - (long long)L.bytes;
+  long long room = cap - static_smem - (long long)L.bytes;
   int wmax = room > 0 ? (int)(room / (long long)per_warp) : 0;
   if (wmax > kMaxWarps) wmax = kMaxWarps;
   if (wmax < 1) return false;
@@ -1897,7 +1912,8 @@ int launch_stage_fast(double* y, const double* p, int ncell, const double* phi, 
   const bool expl = is_explicit(o.method);
   int warps, blocks;
   size_t smem;
-  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32 && !expl, K, o.warps_per_block, o.blocks_per_sm, !expl))
+  if (!plan_launch(m.L, ncell, warps, blocks, smem, prec32 && !expl, K, o.warps_per_block, o.blocks_per_sm, !expl,
+                   kStageStaticSmem))
     return MRI_EINVAL;
   if ((rc = take_queue(m, a, st)) != MRI_OK) return rc;
   if (expl) {
@@ -2124,7 +2140,7 @@ extern "C" int mri_stage_fast_shape(const mri_mech* mech, const mri_fast_opts* o
   size_t s = 0;
   const bool expl = mri::is_explicit(opts->method);
   if (!mri::plan_launch(m->L, ncell, w, b, s, opts->precision == MRI_PREC_FP32_LU && !expl, K, opts->warps_per_block,
-                        opts->blocks_per_sm, !expl))
+                        opts->blocks_per_sm, !expl, mri::kStageStaticSmem))
     return MRI_EINVAL;
   if (warps_per_block) *warps_per_block = w;
   if (blocks) *blocks = b;

@@ -1,12 +1,13 @@
 // FP64 exponential for the rate evaluation, written from the table-driven method of
 // P. T. P. Tang, "Table-driven implementation of the exponential function in IEEE
-// floating-point arithmetic", ACM TOMS 15 (1989):
-//   x = (32 m + j) ln2/32 + r,  |r| <= ln2/64,   exp(x) = 2^m * 2^(j/32) * exp(r),
-// with ln2/32 split in two parts (the first has 15 trailing zero bits so that
-// N * L1 is exact for |N| < 2^15), exp(r) - 1 by its Taylor polynomial of degree 6
-// (truncation below 3e-18 relative for |r| <= ln2/64), 2^(j/32) from a table of 32
-// correctly rounded doubles, and 2^m applied to the exponent field with integer
-// arithmetic.  Arguments outside |x| <= 700 (and NaN) take the library exp.
+// floating-point arithmetic", ACM TOMS 15 (1989), with a table of 128 entries:
+//   x = (128 m + j) ln2/128 + r,  |r| <= ln2/256,   exp(x) = 2^m * 2^(j/128) * exp(r),
+// with ln2/128 split in two parts (the first has 36 significant bits, so that
+// N * L1 is exact for |N| < 2^17), exp(r) - 1 by its Taylor polynomial of degree 5
+// (truncation below 6e-19 relative for |r| <= ln2/256), 2^(j/128) from a table of
+// 128 correctly rounded doubles, and 2^m applied to the exponent field with integer
+// arithmetic.  Arguments outside |x| <= 700 (and NaN) take the library exp.  (The
+// larger table buys one FP64 instruction per exponential over 32 entries.)
 //
 // FP64 natural logarithm, written from the table-driven method of P. T. P. Tang,
 // "Table-driven implementation of the logarithm function in IEEE floating-point
@@ -25,12 +26,17 @@
 
 namespace mri {
 
-constexpr double kExpInvL = 46.166241308446828;              // 32 / ln 2
-constexpr double kExpL1 = 0x1.62e42fefa0000p-6;              // ln2/32, leading 38 bits
-constexpr double kExpL2 = 0x1.cf79abc9e3b3ap-45;             // ln2/32 - L1
+constexpr int kExpTab = 128;                                 // entries of the table 2^(j/128)
+constexpr double kExpInvL = 184.66496523378731;              // 128 / ln 2
+constexpr double kExpL1 = 0x1.62e42fefa0000p-8;              // ln2/128, leading 36 significant bits
+constexpr double kExpL2 = 0x1.cf79abc9e3b3ap-47;             // ln2/128 - L1
 constexpr double kExpShift = 6755399441055744.0;             // 1.5 * 2^52: round to integer
 
-__device__ __forceinline__ double exp_tab(double x, const double* __restrict__ tab32) {
+inline void fill_exp_table(double* t) {
+  for (int j = 0; j < kExpTab; ++j) t[j] = (double)std::exp2l((long double)j / (long double)kExpTab);
+}
+
+__device__ __forceinline__ double exp_tab(double x, const double* __restrict__ tab) {
   const int hx = __double2hiint(x) & 0x7fffffff;
   if (hx >= 0x4085E000) return exp(x);                      // |x| >= 700, Inf or NaN
   const double t = fma(x, kExpInvL, kExpShift);
@@ -38,22 +44,22 @@ __device__ __forceinline__ double exp_tab(double x, const double* __restrict__ t
   const double kd = t - kExpShift;
   double r = fma(-kd, kExpL1, x);
   r = fma(-kd, kExpL2, r);
-  double p = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-  p = fma(p, r, 1.0 / 24.0);
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
   p = fma(p, r, 1.0 / 6.0);
   p = fma(p, r, 0.5);
   p = fma(p, r, 1.0);
   p = p * r;                                                 // exp(r) - 1
-  const double s = tab32[N & 31];
+  const double s = tab[N & (kExpTab - 1)];
   const double v = fma(s, p, s);
-  return __hiloint2double(__double2hiint(v) + (N >> 5) * 1048576, __double2loint(v));
+  return __hiloint2double(__double2hiint(v) + (N >> 7) * 1048576, __double2loint(v));
 }
 
 // exp(x) and exp(-x) from one argument reduction (the method of exp_tab): with
-// x = N ln2/32 + r, exp(x) = 2^(N>>5) 2^((N&31)/32) e^r and exp(-x) = 2^((-N)>>5)
-// 2^(((-N)&31)/32) e^-r, and e^(+-r) - 1 = E(r) +- O(r) from the even and odd parts
-// of the same degree-6 Taylor polynomial.  |x| >= 700 and NaN take the library exp.
-__device__ __forceinline__ void exp_pair(double x, const double* __restrict__ tab32, double& ep, double& em) {
+// x = N ln2/128 + r, exp(x) = 2^(N>>7) 2^((N&127)/128) e^r and exp(-x) =
+// 2^((-N)>>7) 2^(((-N)&127)/128) e^-r, and e^(+-r) - 1 = E(r) +- O(r) from the even
+// and odd parts of the same degree-5 Taylor polynomial.  |x| >= 700 and NaN take
+// the library exp.
+__device__ __forceinline__ void exp_pair(double x, const double* __restrict__ tab, double& ep, double& em) {
   const int hx = __double2hiint(x) & 0x7fffffff;
   if (hx >= 0x4085E000) {
     ep = exp(x);
@@ -66,14 +72,14 @@ __device__ __forceinline__ void exp_pair(double x, const double* __restrict__ ta
   double r = fma(-kd, kExpL1, x);
   r = fma(-kd, kExpL2, r);
   const double r2 = r * r;
-  const double ev = r2 * fma(fma(r2, 1.0 / 720.0, 1.0 / 24.0), r2, 0.5);   // r^2/2 + r^4/24 + r^6/720
+  const double ev = r2 * fma(r2, 1.0 / 24.0, 0.5);                          // r^2/2 + r^4/24
   const double od = r * fma(fma(r2, 1.0 / 120.0, 1.0 / 6.0), r2, 1.0);     // r + r^3/6 + r^5/120
   const int Nm = -N;
-  const double sp = tab32[N & 31], sm = tab32[Nm & 31];
+  const double sp = tab[N & (kExpTab - 1)], sm = tab[Nm & (kExpTab - 1)];
   const double vp = fma(sp, ev + od, sp);
   const double vm = fma(sm, ev - od, sm);
-  ep = __hiloint2double(__double2hiint(vp) + (N >> 5) * 1048576, __double2loint(vp));
-  em = __hiloint2double(__double2hiint(vm) + (Nm >> 5) * 1048576, __double2loint(vm));
+  ep = __hiloint2double(__double2hiint(vp) + (N >> 7) * 1048576, __double2loint(vp));
+  em = __hiloint2double(__double2hiint(vm) + (Nm >> 7) * 1048576, __double2loint(vm));
 }
 
 // table: [0, 129) 1/F, [129, 258) log(F) leading, [258, 387) log(F) trailing, then

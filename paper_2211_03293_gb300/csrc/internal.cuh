@@ -49,7 +49,7 @@ struct Layout {
   int o_tcr;              // int32 [ntc]: reaction of the correction
   int o_tcv, o_tcv32;     // double / float [ntc]: alpha_rl - 1
   int o_trx;              // int32 [n_troe]: reaction index of each falloff row
-  int o_exp2;             // double [32]: 2^(j/32), the table of the exponential (fastmath.cuh)
+  int o_exp2;             // double [kExpTab]: 2^(j/128), the table of the exponential (fastmath.cuh)
   int o_logt;             // double [260]: 1/F, log F, ln2 split: the table of the logarithm (fastmath.cuh)
   int o_nu;               // double [8]: the small integers -3..4 as doubles (index v + 3), so kernels
                           // turn stoichiometric integers into doubles with a load, not a conversion

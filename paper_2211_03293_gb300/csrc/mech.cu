@@ -269,7 +269,7 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
   L.o_tcv = S.add((ntc + 1) * 8);
   L.o_tcv32 = S.add((ntc + 1) * 4);
   L.o_trx = S.add((size_t)(B.n_troe > 0 ? B.n_troe : 1) * 4);
-  L.o_exp2 = S.add(32 * 8);
+  L.o_exp2 = S.add(kExpTab * 8);
   L.o_logt = S.add(kLogTabDoubles * 8);
   L.o_nu = S.add(8 * 8);
   L.o_nu32 = S.add(8 * 4);
@@ -396,8 +396,7 @@ int build_table(const Blob& Bin, Layout& L, std::vector<unsigned char>& out) {
   int32_t* trx = S.at<int32_t>(L.o_trx);
   for (int r = 0; r < R; ++r)
     if (B.rtype[r] == 2) trx[B.troe_row[r]] = r;
-  double* e2 = S.at<double>(L.o_exp2);
-  for (int j = 0; j < 32; ++j) e2[j] = (double)std::exp2l((long double)j / 32.0L);
+  fill_exp_table(S.at<double>(L.o_exp2));
   fill_log_table(S.at<double>(L.o_logt));
   double* nu = S.at<double>(L.o_nu);
   for (int i = 0; i < 8; ++i) nu[i] = (double)(i - 3);

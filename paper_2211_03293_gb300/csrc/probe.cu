@@ -45,20 +45,20 @@ __global__ void dfma_latency(double* out, long long* cycles, int iters, double a
 }
 
 struct Exp2Table {
-  double v[32];
+  double v[mri::kExpTab];
 };
 
 __global__ void exp_probe_kernel(const double* x, double* y, long long n, Exp2Table tab) {
-  __shared__ double s[32];
-  if (threadIdx.x < 32) s[threadIdx.x] = tab.v[threadIdx.x];
+  __shared__ double s[mri::kExpTab];
+  for (int i = threadIdx.x; i < mri::kExpTab; i += blockDim.x) s[i] = tab.v[i];
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = mri::exp_tab(x[i], s);
 }
 
 __global__ void exp_pair_probe_kernel(const double* x, double* y, double* z, long long n, Exp2Table tab) {
-  __shared__ double s[32];
-  if (threadIdx.x < 32) s[threadIdx.x] = tab.v[threadIdx.x];
+  __shared__ double s[mri::kExpTab];
+  for (int i = threadIdx.x; i < mri::kExpTab; i += blockDim.x) s[i] = tab.v[i];
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     mri::exp_pair(x[i], s, y[i], z[i]);
@@ -82,7 +82,7 @@ extern "C" int mri_probe_exp_pair(const double* x, double* y, double* z, long lo
   if (n < 0 || (n > 0 && (!x || !y || !z))) return -1;
   if (n == 0) return 0;
   Exp2Table tab;
-  for (int j = 0; j < 32; ++j) tab.v[j] = (double)std::exp2l((long double)j / 32.0L);
+  mri::fill_exp_table(tab.v);
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   exp_pair_probe_kernel<<<(int)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, z, n, tab);
@@ -104,7 +104,7 @@ extern "C" int mri_probe_exp(const double* x, double* y, long long n, void* stre
   if (n < 0 || (n > 0 && (!x || !y))) return -1;
   if (n == 0) return 0;
   Exp2Table tab;
-  for (int j = 0; j < 32; ++j) tab.v[j] = (double)std::exp2l((long double)j / 32.0L);
+  mri::fill_exp_table(tab.v);
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   exp_probe_kernel<<<(int)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n, tab);

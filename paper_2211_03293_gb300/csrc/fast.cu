@@ -153,16 +153,18 @@ struct RxnOut {
 // Rate of progress of reaction r (and with JAC its Jacobian pieces) from the species
 // factors of chem_eval: k_f = k_inf (times the falloff factor Pr/(1+Pr) F, whose ln F
 // joins the exponent of k_inf), 1/K_c as a product of species factors,
-// q = [M] (k_f prod C^nu' - k_r prod C^nu'').
-template <bool JAC>
+// q = [M] (k_f prod C^nu' - k_r prod C^nu'').  PLAIN: the caller guarantees a
+// reaction without third body or falloff ([M] = 1), and the code has no branches on
+// the reaction type (the same values as the general code).
+template <bool JAC, bool PLAIN = false>
 __device__ __forceinline__ void rxn_eval(const Tab& t, const WS& w, int r, double lnT, double invT, double Ctot,
                                          RxnOut& o) {
   const uint64_t rec = t.rxn[r];
   const int i0 = rec & 0xff, i1 = (rec >> 8) & 0xff, i2 = (rec >> 16) & 0xff;
   const int j0 = (rec >> 24) & 0xff, j1 = (rec >> 32) & 0xff, j2 = (rec >> 40) & 0xff;
   const int dn = (int)(int8_t)((rec >> 48) & 0xff);
-  const int type = (int)(rec >> 56);
-  const int tr = t.rrow[r] >> 16;                  // falloff row (type 2)
+  const int type = PLAIN ? 0 : (int)(rec >> 56);
+  const int tr = PLAIN ? 0 : t.rrow[r] >> 16;      // falloff row (type 2)
   double lnkf = fma(t.b[r], lnT, t.lnA[r]) - t.Ta[r] * invT;
   if (type == 2) lnkf += w.tro[kTroeSlots * tr + 6];      // ln F
   double kf = exp_tab(lnkf, t.exp2t);
@@ -179,21 +181,23 @@ __device__ __forceinline__ void rxn_eval(const Tab& t, const WS& w, int r, doubl
   // (CE_k = C_k / E_k, in the 1/E array), so k_r prod C^nu'' = k_f Er prod CE.
   const double Er = (w.E[i0] * w.E[i1]) * (w.E[i2] * w.c0p[dn + 2]);
   if (!JAC) {
-    o.q = M * (kf * fma(-Er, w.Einv[j0] * w.Einv[j1] * w.Einv[j2], fwd));
+    const double q = kf * fma(-Er, w.Einv[j0] * w.Einv[j1] * w.Einv[j2], fwd);
+    o.q = PLAIN ? q : M * q;
     return;
   }
   const double kr = kf * (Er * (w.Einv[j0] * w.Einv[j1] * w.Einv[j2]));
   const double rev = w.C[j0] * w.C[j1] * w.C[j2];
   const double base = fma(kf, fwd, -kr * rev);
-  o.q = M * base;
+  o.q = PLAIN ? base : M * base;
   {
     double dlnkf_dT = fma(t.Ta[r], invT, t.b[r]) * invT;
     if (type == 2) dlnkf_dT += w.tro[kTroeSlots * tr + 10];
     const double snh = (w.hh[j0] + w.hh[j1] + w.hh[j2]) - (w.hh[i0] + w.hh[i1] + w.hh[i2]);
     const double dlnKc_dT = (snh - t.nu[dn]) * invT;
-    o.kfw = M * kf;
-    o.krw = M * kr;
-    o.dqdT = M * fma(kf * dlnkf_dT, fwd, -kr * (dlnkf_dT - dlnKc_dT) * rev);
+    const double dq = fma(kf * dlnkf_dT, fwd, -kr * (dlnkf_dT - dlnKc_dT) * rev);
+    o.kfw = PLAIN ? kf : M * kf;
+    o.krw = PLAIN ? kr : M * kr;
+    o.dqdT = PLAIN ? dq : M * dq;
     o.tbs = (type == 1) ? base : ((type == 2) ? w.tro[kTroeSlots * tr + 11] * base : 0.0);
   }
 }
@@ -363,12 +367,18 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     }
   }
   __syncwarp();
-  // two reactions per lane per iteration: independent exponentials interleave
+  // two reactions per lane per iteration: independent exponentials interleave.  The
+  // table groups falloff, then third-body, then plain reactions; with at most 32 of
+  // the first two kinds all of them are first reactions of the first iteration
+  // (r0 < 32, the same for the whole warp), so every other slot takes the plain code.
+  const bool peel = t.n_tb <= 32;
   for (int r0 = lane; r0 < R; r0 += 64) {
     const int r1 = (r0 + 32 < R) ? r0 + 32 : r0;
     RxnOut o0, o1;
-    rxn_eval<JAC>(t, w, r0, lnT, invT, Ctot, o0);
-    rxn_eval<JAC>(t, w, r1, lnT, invT, Ctot, o1);
+    if (peel && r0 >= 32) rxn_eval<JAC, true>(t, w, r0, lnT, invT, Ctot, o0);
+    else rxn_eval<JAC>(t, w, r0, lnT, invT, Ctot, o0);
+    if (peel && r1 >= 32) rxn_eval<JAC, true>(t, w, r1, lnT, invT, Ctot, o1);
+    else rxn_eval<JAC>(t, w, r1, lnT, invT, Ctot, o1);
     w.q[r0] = o0.q;
     if (JAC) { w.kfw[r0] = o0.kfw; w.krw[r0] = o0.krw; w.dqdT[r0] = o0.dqdT; w.tbs[r0] = o0.tbs; }
     if (r1 != r0) {

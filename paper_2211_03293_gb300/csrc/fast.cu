@@ -91,11 +91,18 @@ struct WS {
     piv = reinterpret_cast<int*>(base + o.piv);
     q = base + o.q; kfw = base + o.kfw; krw = base + o.krw; dqdT = base + o.dqdT; tbs = base + o.tbs;
     float* fb = reinterpret_cast<float*>(base + o.f32);
-    const F32Offsets g32 = f32_offsets(L);
+    const F32Offsets g32 = f32_offsets(L, !o.r32);
     M32 = reinterpret_cast<float*>(base + o.M);
     dinv32 = fb + g32.dinv; d32 = fb + g32.d;
     C32 = fb + g32.C; hh32 = fb + g32.hh; cp32 = fb + g32.cp; wd32 = fb + g32.wd; DT32 = fb + g32.DT;
-    DC32 = fb + g32.DC; aux32 = fb + g32.aux; tbk32 = fb + g32.tbk; kfw32 = fb + g32.kfw; krw32 = fb + g32.krw; tbs32 = fb + g32.tbs;
+    DC32 = fb + g32.DC; aux32 = fb + g32.aux; tbk32 = fb + g32.tbk;
+    if (o.r32) {   // in the rates and the falloff scratch, dead when the copies are made
+      kfw32 = reinterpret_cast<float*>(base + o.q);
+      krw32 = kfw32 + L.rv;
+      tbs32 = reinterpret_cast<float*>(base + o.tro);
+    } else {
+      kfw32 = fb + g32.kfw; krw32 = fb + g32.krw; tbs32 = fb + g32.tbs;
+    }
     ld = L.ld;
     nv = round_up(L.n + 1, 2);
   }

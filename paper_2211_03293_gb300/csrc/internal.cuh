@@ -112,6 +112,7 @@ struct WsOffsets {
   int q, kfw, krw, dqdT, tbs;
   int E, Einv, c0p, tro, tbk;
   int f32;     // start of the float region (prec32 only), in doubles
+  int r32;     // prec32: 1 when the FP32 k_f, k_r and third-body scales live in q and tro
   int total;
 };
 
@@ -122,7 +123,9 @@ struct F32Offsets {
   int C, hh, cp, wd, DT, DC, aux, tbk, kfw, krw, tbs, d, dinv, total;
 };
 
-__host__ __device__ inline F32Offsets f32_offsets(const Layout& L) {
+// r_arrays = false: without the per-reaction FP32 arrays (kfw, krw, tbs), which then
+// live elsewhere (WsOffsets::r32).
+__host__ __device__ inline F32Offsets f32_offsets(const Layout& L, bool r_arrays = true) {
   F32Offsets f;
   const int nv = round_up(L.n + 1, 4), ns = round_up(L.nsv, 4), rv = round_up(L.rv, 4);
   int o = 0;
@@ -134,9 +137,12 @@ __host__ __device__ inline F32Offsets f32_offsets(const Layout& L) {
   f.DC = o; o += ns;
   f.aux = o; o += ns;
   f.tbk = o; o += ns;
-  f.kfw = o; o += rv;
-  f.krw = o; o += rv;
-  f.tbs = o; o += rv;
+  f.kfw = f.krw = f.tbs = -1;
+  if (r_arrays) {
+    f.kfw = o; o += rv;
+    f.krw = o; o += rv;
+    f.tbs = o; o += rv;
+  }
   f.d = o; o += nv;
   f.dinv = o; o += nv;
   f.total = round_up(o, 4);
@@ -199,8 +205,17 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = f
   }
   w.tbk = o; o += L.nsv;
   o = round_up(o, 2);
+  // mixed form: the FP32 copies of k_f, k_r and the third-body scales are made after
+  // the Jacobian's rate pass has summed its production rates, when the rates (q, rv
+  // doubles: room for both rv-float copies) and the falloff / partial-sum scratch
+  // (tro) are dead, so they live there when tro holds rv floats
+  {
+    const int ntro = kTroeSlots * (L.n_troe > 0 ? L.n_troe : 1);
+    const int tro_doubles = ntro > L.n_slots ? ntro : L.n_slots;
+    w.r32 = (prec32 && 2 * tro_doubles >= L.rv) ? 1 : 0;
+  }
   w.f32 = o;
-  if (prec32) o += f32_offsets(L).total / 2;
+  if (prec32) o += f32_offsets(L, !w.r32).total / 2;
   w.phi = o; o += K * nv;        // forcing coefficients: sized by the launch's K
   w.total = round_up(o, 2);
   return w;

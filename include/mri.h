@@ -109,7 +109,8 @@ int mri_mech_info(const mri_mech* mech, int* n_species, int* n_reactions);
                                  contraction is slow */
 #define MRI_JAC_LAZY 1        /* the factorised Newton matrix also carries over to the
                                  next substeps of the call while h gamma is unchanged
-                                 (at most 20 substeps); refreshed inside Newton when the
+                                 up to rounding (at most 12 substeps); refreshed inside
+                                 Newton when the
                                  contraction is slow.  The converged stage values do not
                                  depend on the policy, only the cost does. */
 #define MRI_PREC_FP64 0       /* plain path: everything in FP64 */

@@ -989,7 +989,7 @@ struct StageArgs {
   double A[3][3], c[3], gamma;
 };
 
-constexpr int kMaxJacAge = 20;
+constexpr int kMaxJacAge = 12;
 
 __device__ __forceinline__ void substep_geometry(int s, int ramp, double hh, double& tau, double& hk) {
   if (ramp > 0) {
@@ -1209,8 +1209,11 @@ __device__ __forceinline__ void stage_cells(const StageArgs& a, unsigned char* s
       // MRI_JAC_PER_SUBSTEP: Jacobian + LU at every substep start.  MRI_JAC_LAZY: the
       // factorised matrix carries over while h gamma is unchanged and it is younger
       // than kMaxJacAge substeps; poor contraction refreshes it inside Newton.
-      const bool need = (a.jac_policy == MRI_JAC_PER_SUBSTEP) || startup_sub || hg != M_hg ||
-                        M_age >= kMaxJacAge;
+      // "Unchanged" allows rounding: stages of equal substeps compute h from their own
+      // lengths (H/3 / 4 and 5H/12 / 5 differ in the last bit), and a matrix whose h gamma
+      // is off by an ulp is as good a Newton matrix as the exact one.
+      const bool need = (a.jac_policy == MRI_JAC_PER_SUBSTEP) || startup_sub ||
+                        !(fabs(hg - M_hg) <= 1e-12 * hg) || M_age >= kMaxJacAge;
       if (need) {
         if (refresh_matrix<PREC32>(t, w, w.y0, p, hg, a.lu_variant, lane) != 0) { status = MRI_CELL_ENEWTON; break; }
         njac++;

@@ -67,8 +67,9 @@ FLOPS_PER_TRANSCENDENTAL = 20.0
 # Newton-matrix cache in use, from the ncu captures summarised in
 # profiles/stage_fast_fp64_box16.md and profiles/stage_fast_mixed_box16.md (4096-cell
 # launches; traffic grows with the cells processed, so a launch over `cells` moves
-# cells times this).  None: the kernel changed since the capture.
-STAGE_DRAM_BYTES_PER_CELL = {0: (61941760 + 253184) / 4096, 1: (33700352 + 512) / 4096}
+# cells times this).  None: the kernel changed since the capture (the captured figures,
+# 15.1 KB (FP64) and 8.2 KB (mixed) per cell, predate the last workspace change).
+STAGE_DRAM_BYTES_PER_CELL = {0: None, 1: None}
 # forms timed without the Newton-matrix cache (the learned form's comparison: without the
 # cache's f^F no derivative predicts the first SDIRK stage of a call, which is where the
 # network's prediction is used)

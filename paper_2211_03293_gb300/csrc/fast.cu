@@ -71,7 +71,7 @@ struct Tab {
 };
 
 struct WS {
-  double *M, *y0, *Z, *d, *res, *F0, *F1, *Fl, *r, *f, *base, *phi, *C, *g, *hh, *cp, *wd, *DT, *DC, *aux, *dinv;
+  double *M, *y0, *Z, *d, *res, *F0, *F1, *Fl, *r, *f, *base, *phi, *C, *hh, *cp, *wd, *DT, *DC, *aux, *dinv;
   double *E, *Einv, *c0p, *tro, *tbk;
   int* piv;
   double *q, *kfw, *krw, *dqdT, *tbs;
@@ -82,26 +82,34 @@ struct WS {
   __device__ WS(double* base, const Layout& L, bool prec32, int K, bool matrix = true) {
     WsOffsets o = ws_offsets(L, prec32, K, matrix);
     M = base + o.M; y0 = base + o.y0; Z = base + o.Z; d = base + o.d;
-    F0 = base + o.F0; F1 = base + o.F1; Fl = base + o.Fl; r = base + o.r; f = base + o.f; phi = base + o.phi;
+    F0 = base + o.F0; F1 = base + o.F1; Fl = base + o.Fl; r = base + o.r; phi = base + o.phi;
+    f = (o.f >= 0) ? base + o.f : nullptr;
     this->base = base + o.base;
     res = base + o.res;
-    C = base + o.C; g = base + o.g; hh = base + o.hh; cp = base + o.cp; wd = base + o.wd;
+    C = base + o.C; hh = base + o.hh; cp = base + o.cp; wd = base + o.wd;
     DT = base + o.DT; DC = base + o.DC; aux = base + o.aux; dinv = base + o.dinv;
     E = base + o.E; Einv = base + o.Einv; c0p = base + o.c0p; tro = base + o.tro; tbk = base + o.tbk;
     piv = reinterpret_cast<int*>(base + o.piv);
     q = base + o.q; kfw = base + o.kfw; krw = base + o.krw; dqdT = base + o.dqdT; tbs = base + o.tbs;
     float* fb = reinterpret_cast<float*>(base + o.f32);
-    const F32Offsets g32 = f32_offsets(L, !o.r32);
+    const F32Offsets g32 = f32_offsets(L, o.r32 != 0);
     M32 = reinterpret_cast<float*>(base + o.M);
-    dinv32 = fb + g32.dinv; d32 = fb + g32.d;
+    dinv32 = fb + g32.dinv;
     C32 = fb + g32.C; hh32 = fb + g32.hh; cp32 = fb + g32.cp; wd32 = fb + g32.wd; DT32 = fb + g32.DT;
-    DC32 = fb + g32.DC; aux32 = fb + g32.aux; tbk32 = fb + g32.tbk;
-    if (o.r32) {   // in the rates and the falloff scratch, dead when the copies are made
+    tbk32 = fb + g32.tbk;
+    if (o.r32) {
+      // in dead FP64 scratch: the reaction copies in the rates and the falloff scratch
+      // (dead when the copies are made), DC and the column sums in E and 1/E (as in the
+      // FP64 form), the correction in the rates again (no rates are live in a solve)
       kfw32 = reinterpret_cast<float*>(base + o.q);
       krw32 = kfw32 + L.rv;
       tbs32 = reinterpret_cast<float*>(base + o.tro);
+      DC32 = reinterpret_cast<float*>(base + o.E);
+      aux32 = DC32 + round_up(L.nsv, 4);
+      d32 = reinterpret_cast<float*>(base + o.q);
     } else {
       kfw32 = fb + g32.kfw; krw32 = fb + g32.krw; tbs32 = fb + g32.tbs;
+      DC32 = fb + g32.DC; aux32 = fb + g32.aux; d32 = fb + g32.d;
     }
     ld = L.ld;
     nv = round_up(L.n + 1, 2);
@@ -253,11 +261,10 @@ __device__ __forceinline__ void chem_eval(const Tab& t, const WS& w, const doubl
     cpp = fma(zw, cpv, cpp);
     w.cp[k] = cpv;
     w.hh[k] = hv;
-    w.g[k] = g;
     w.E[k] = e;
     w.Einv[k] = JAC ? einv : c * einv;   // 1/E for the Jacobian's k_r, else C/E
   }
-  if (lane == 0) { w.C[Ns] = 1.0; w.g[Ns] = 0.0; w.hh[Ns] = 0.0; w.E[Ns] = 1.0; w.Einv[Ns] = 1.0; }
+  if (lane == 0) { w.C[Ns] = 1.0; w.hh[Ns] = 0.0; w.E[Ns] = 1.0; w.Einv[Ns] = 1.0; }
   if (lane < 5) {
     // (p_atm / (R T))^(-dn) for dn = -2..2 at index dn + 2
     const double C0 = (kPatm / kRu) * invT, iC0 = (kRu / kPatm) * T;

@@ -108,7 +108,7 @@ struct Mech {             // what mri_mech points at
 // prec32 (the mixed-precision form) the Newton matrix and its factors are FP32 and a
 // float region holds FP32 copies of the Jacobian inputs.
 struct WsOffsets {
-  int M, y0, Z, d, res, F0, F1, Fl, r, f, base, phi, C, g, hh, cp, wd, DT, DC, aux, dinv, piv;
+  int M, y0, Z, d, res, F0, F1, Fl, r, f, base, phi, C, hh, cp, wd, DT, DC, aux, dinv, piv;
   int q, kfw, krw, dqdT, tbs;
   int E, Einv, c0p, tro, tbk;
   int f32;     // start of the float region (prec32 only), in doubles
@@ -123,9 +123,10 @@ struct F32Offsets {
   int C, hh, cp, wd, DT, DC, aux, tbk, kfw, krw, tbs, d, dinv, total;
 };
 
-// r_arrays = false: without the per-reaction FP32 arrays (kfw, krw, tbs), which then
-// live elsewhere (WsOffsets::r32).
-__host__ __device__ inline F32Offsets f32_offsets(const Layout& L, bool r_arrays = true) {
+// compact: without the per-reaction FP32 arrays (kfw, krw, tbs), the Jacobian's
+// column vectors (DC, aux) and the FP32 correction (d), which then live in dead FP64
+// scratch (WsOffsets::r32).
+__host__ __device__ inline F32Offsets f32_offsets(const Layout& L, bool compact = false) {
   F32Offsets f;
   const int nv = round_up(L.n + 1, 4), ns = round_up(L.nsv, 4), rv = round_up(L.rv, 4);
   int o = 0;
@@ -134,16 +135,16 @@ __host__ __device__ inline F32Offsets f32_offsets(const Layout& L, bool r_arrays
   f.cp = o; o += ns;
   f.wd = o; o += ns;
   f.DT = o; o += ns;
-  f.DC = o; o += ns;
-  f.aux = o; o += ns;
   f.tbk = o; o += ns;
-  f.kfw = f.krw = f.tbs = -1;
-  if (r_arrays) {
+  f.DC = f.aux = f.kfw = f.krw = f.tbs = f.d = -1;
+  if (!compact) {
+    f.DC = o; o += ns;
+    f.aux = o; o += ns;
     f.kfw = o; o += rv;
     f.krw = o; o += rv;
     f.tbs = o; o += rv;
+    f.d = o; o += nv;
   }
-  f.d = o; o += nv;
   f.dinv = o; o += nv;
   f.total = round_up(o, 4);
   return f;
@@ -166,10 +167,10 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = f
   w.F1 = o; o += nv;
   w.Fl = o; o += nv;
   w.r = o; o += nv;
-  w.f = o; o += nv;
+  w.f = -1;   // f^F of the explicit methods and the per-kernel entries (the stage solve forms it in place)
+  if (!prec32) { w.f = o; o += nv; }
   w.base = o; o += nv;
   w.C = o; o += L.nsv;
-  w.g = o; o += L.nsv;
   w.hh = o; o += L.nsv;
   w.cp = o; o += L.nsv;
   w.wd = o; o += L.nsv;
@@ -208,14 +209,16 @@ __host__ __device__ inline WsOffsets ws_offsets(const Layout& L, bool prec32 = f
   // mixed form: the FP32 copies of k_f, k_r and the third-body scales are made after
   // the Jacobian's rate pass has summed its production rates, when the rates (q, rv
   // doubles: room for both rv-float copies) and the falloff / partial-sum scratch
-  // (tro) are dead, so they live there when tro holds rv floats
+  // (tro) are dead, so they live there when tro holds rv floats; the FP32 Jacobian's
+  // DC and column-sum vectors take E and 1/E as the FP64 ones do, and the FP32 Newton
+  // correction, made while no rates are live, takes q too
   {
     const int ntro = kTroeSlots * (L.n_troe > 0 ? L.n_troe : 1);
     const int tro_doubles = ntro > L.n_slots ? ntro : L.n_slots;
-    w.r32 = (prec32 && 2 * tro_doubles >= L.rv) ? 1 : 0;
+    w.r32 = (prec32 && 2 * tro_doubles >= L.rv && 2 * L.rv >= round_up(L.n + 1, 4)) ? 1 : 0;
   }
   w.f32 = o;
-  if (prec32) o += f32_offsets(L, !w.r32).total / 2;
+  if (prec32) o += f32_offsets(L, w.r32 != 0).total / 2;
   w.phi = o; o += K * nv;        // forcing coefficients: sized by the launch's K
   w.total = round_up(o, 2);
   return w;
